@@ -1,0 +1,360 @@
+#!/usr/bin/env python3
+"""Throughput of the whole hot path -- phase one (2-bit encode, minimizers, super-mer bins)
+plus phase two (extract, canonicalise, count, overflow, compact + min-count filter) -- in
+canonical k-mers counted per second on one B300, bit-exact integer counts.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+One step = gerbil_partition + gerbil_count_batch over all bins of one synthetic read set that
+is already resident in HBM.  Under torchrun each rank runs an independent replica (the path
+has no exchange step); the value is the k-mers of all ranks over the slowest rank's time.
+Prints one JSON line (rank 0).  ``--impl reference`` times the CPU oracle instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("canonical k-mers counted/sec on 1 B300 (bit-exact), fraction of HBM roofline; "
+          "batched vs per-bin")
+UNIT = "k-mers/s"
+DEFAULT_WORKLOAD = "genome5M-30x-k65"
+L2_BYTES = 126 * 2 ** 20
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--per-bin-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample-reads", type=int, default=40000)
+    ap.add_argument("--ref-sample-reads", type=int, default=5000)
+    return ap.parse_args()
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+def _src_sha():
+    h = hashlib.sha256()
+    for f in ("count.cu", "common.cuh", "kernels.h"):
+        with open(os.path.join(ROOT, "paper_1607_06618_b300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _traffic_from_profile(workload: str):
+    """dram bytes per insert launch from the committed ncu summary, if it matches the source."""
+    path = os.path.join(ROOT, "profiles", "insert_kernel_%s.md" % workload)
+    try:
+        text = open(path).read()
+    except OSError:
+        return None
+    sha = re.search(r"source_sha256_16:\s*([0-9a-f]+)", text)
+    tr = re.search(r"traffic_bytes_per_launch:\s*([0-9]+)", text)
+    if not sha or not tr or sha.group(1) != _src_sha():
+        return None
+    return int(tr.group(1))
+
+
+class Clocks:
+    """nvidia-smi sampler running while the timed region runs."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(device), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[3:7]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def _model_bytes(occ, n_bases, distinct, emitted, W):
+    """Algorithmic bytes: occ*(b_in + P(W)) for the insert kernel; + distinct*(8W+8) +
+    emitted*(8W+4) for the whole phase two."""
+    P = 32 * (-(-(8 * W + 8) // 32)) + 32
+    b_in_total = 0.25 * n_bases
+    insert = b_in_total + occ * P
+    step = insert + distinct * (8 * W + 8) + emitted * (8 * W + 4)
+    return insert, step
+
+
+def run_cpu_oracle(seq, offs, p, nreads_sample):
+    import oracle
+    n = min(nreads_sample, offs.size - 1)
+    s, o = seq[: int(offs[n])], offs[: n + 1]
+    t0 = time.perf_counter()
+    keys, counts = oracle.count(s, o, p["k"], canonical=True, min_count=p["min_count"])
+    dt = time.perf_counter() - t0
+    occ = oracle.windows(s, o, p["k"])
+    return occ, dt, n
+
+
+def main_reference(a, world, rank):
+    if rank != 0:
+        return 0
+    from paper_1607_06618_b300 import synth
+    import oracle
+    oracle.build()
+    seq, offs, p = synth.workload(a.workload)
+    for _ in range(a.warmup):
+        run_cpu_oracle(seq, offs, p, a.ref_sample_reads)
+    times, occ = [], 0
+    for _ in range(a.steps):
+        occ, dt, n = run_cpu_oracle(seq, offs, p, a.ref_sample_reads)
+        times.append(dt)
+    total = sum(times)
+    value = occ * a.steps / total
+    sample = "first %d of %d reads per step (%d k-mer windows)" % (n, offs.size - 1, occ)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": a.gpus,
+        "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1000 * total / a.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+        "data": "synthetic", "config": _config(a.workload, p, seq, offs),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def _config(name, p, seq, offs):
+    return {"workload": name, "k": p["k"], "m": p["m"], "nbins": p["nbins"],
+            "min_count": p["min_count"], "reads": int(offs.size - 1),
+            "bases": int(seq.size), "mode": "batched persistent launch",
+            "l2": "inputs larger than L2 (%.0f MB ASCII reads > 126 MB)" % (seq.size / 1e6)}
+
+
+def main_ours(a, world, rank, local):
+    import torch
+    from paper_1607_06618_b300 import gerbil, synth
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    seq, offs, p = synth.workload(a.workload)
+    k, m, nbins, mc = p["k"], p["m"], p["nbins"], p["min_count"]
+    W = (2 * k + 63) // 64
+    s_dev = torch.from_numpy(seq).cuda()
+    o_dev = torch.from_numpy(offs.view(np.int64)).cuda()
+    stream = torch.cuda.current_stream()
+    ctx = gerbil.Context(local, stream=stream.cuda_stream)
+    opts = gerbil.default_opts()
+
+    info = {}
+
+    def step():
+        bins = ctx.partition(s_dev, o_dev, k, m, nbins, opts)
+        res = ctx.count_batch(bins, None, k, mc, opts)
+        st = res.info()[2]
+        if not info:
+            bi = bins.info()
+            info.update(st)
+            info["n_supermers"] = bi["n_supermers"]
+        res.free()
+        bins.free()
+        return st
+
+    for _ in range(max(3, a.warmup)):
+        step()
+    occ = info["occurrences"]
+    n_bases = occ + info["n_supermers"] * (k - 1)
+
+    clocks = Clocks(local)
+    ctx.profile(True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(a.steps):
+        st = step()
+        assert st["emitted"] == info["emitted"] and st["occurrences"] == occ
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ms = e0.elapsed_time(e1)
+    ph = ctx.phase_times()
+    ck = clocks.stop()
+    ctx.profile(False)
+    if dist:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = occ * a.steps * world / (ms / 1000.0)
+
+    # roofline of the dominant kernel (insert), from its own event-timed launches
+    hbm, peak_kind = _peaks()
+    insert_bytes, step_bytes = _model_bytes(occ, n_bases, info["distinct"], info["emitted"], W)
+    ins_ms = ph["insert_ms"] / max(1, ph["insert_launches"])
+    achieved = insert_bytes / (ins_ms / 1000.0) / 1e9
+    p2_ms = (ph["clear_ms"] + ph["insert_ms"] + ph["compact_ms"] + ph["overflow_ms"]) / a.steps
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": achieved / hbm, "traffic": _traffic_from_profile(a.workload),
+                "kernel": "insert_persistent_kernel<%d>" % W,
+                "peak_kind": peak_kind + " (hbm_gbs, copy bandwidth)",
+                "bytes_per_launch": insert_bytes, "launch_ms": ins_ms}
+    phase_ms = {key[:-3]: ph[key] / a.steps for key in ph if key.endswith("_ms")}
+
+    # batched (one persistent launch) vs one count call per bin, phase two only
+    bvp = None
+    if a.per_bin_steps > 0 and rank == 0:
+        bins = ctx.partition(s_dev, o_dev, k, m, nbins, opts)
+        torch.cuda.synchronize()
+        tb = time.perf_counter()
+        for _ in range(a.per_bin_steps):
+            ctx.count_batch(bins, None, k, mc, opts).free()
+        torch.cuda.synchronize()
+        tb = (time.perf_counter() - tb) / a.per_bin_steps
+        tp = time.perf_counter()
+        for _ in range(a.per_bin_steps):
+            for b in range(nbins):
+                ctx.count(bins, b, k, mc, opts).free()
+        torch.cuda.synchronize()
+        tp = (time.perf_counter() - tp) / a.per_bin_steps
+        bins.free()
+        bvp = {"batched_ms": 1000 * tb, "per_bin_ms": 1000 * tp, "speedup": tp / tb,
+               "what": "phase two over all %d bins: one count_batch vs %d count calls" % (nbins, nbins)}
+
+    # end to end through the public API from pinned host buffers, result read back to host
+    e2e = None
+    if a.e2e_steps > 0:
+        seq_pin = torch.from_numpy(seq).pin_memory()
+        offs_pin = torch.from_numpy(offs.view(np.int64)).pin_memory()
+        nrow = info["emitted"]
+        keys_pin = torch.empty((max(1, nrow), W), dtype=torch.int64).pin_memory()
+        cnt_pin = torch.empty(max(1, nrow), dtype=torch.int32).pin_memory()
+        hs, ho = seq_pin.numpy(), offs_pin.numpy().view(np.uint64)
+        kp, cp = keys_pin.numpy().view(np.uint64), cnt_pin.numpy().view(np.uint32)
+
+        def e2e_step():
+            bins = ctx.partition(hs, ho, k, m, nbins, opts)
+            res = ctx.count_batch(bins, None, k, mc, opts)
+            gerbil.gerbil_counts_to_host(res.handle, kp, cp)
+            res.free()
+            bins.free()
+
+        e2e_step()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(a.e2e_steps):
+            e2e_step()
+        torch.cuda.synchronize()
+        te = (time.perf_counter() - t0) / a.e2e_steps
+        if dist:
+            t = torch.tensor([te], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            te = float(t.item())
+        e2e = {"value": occ * world / te, "unit": UNIT,
+               "h2d_bytes_per_step": int(seq.nbytes + offs.nbytes),
+               "d2h_bytes_per_step": int(nrow * (8 * W + 4)), "ms_per_step": 1000 * te}
+
+    cpu = None
+    if rank == 0 and not a.no_cpu_baseline:
+        occ_s, dt, n = run_cpu_oracle(seq, offs, p, a.cpu_sample_reads)
+        cpu = {"value": occ_s / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": "first %d of %d reads (%d k-mer windows), std::map oracle, %.1f s"
+                         % (n, offs.size - 1, occ_s, dt)}
+
+    if rank == 0:
+        cfg = _config(a.workload, p, seq, offs)
+        cfg.update({"occurrences_per_step": occ, "distinct": info["distinct"],
+                    "emitted": info["emitted"], "supermers": info["n_supermers"],
+                    "table_slots": info["table_slots"], "overflowed": info["overflowed"]})
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+            "warmup": max(3, a.warmup), "ms_per_step": ms / a.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": cfg, "roofline": roofline,
+            "step_model": {"bytes": step_bytes, "phase2_ms": p2_ms,
+                           "achieved_gbs": step_bytes / (p2_ms / 1000.0) / 1e9},
+            "phase_ms": phase_ms, "cpu_baseline": cpu, "e2e": e2e, "clocks": ck,
+            "gpu_launches": int(ph["kernel_launches"]), "batched_vs_per_bin": bvp,
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    a = _args()
+    world, rank, local = _dist()
+    if a.impl == "reference":
+        return main_reference(a, world, rank)
+    return main_ours(a, world, rank, local)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

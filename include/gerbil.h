@@ -1,0 +1,219 @@
+/* gerbil.h -- C ABI of the B300-native hot path of Gerbil's two-phase k-mer counter
+ * (Erbert, Rechner, Mueller-Hannemann, "Gerbil: A Fast and Memory-Efficient k-mer Counter
+ * with GPU-Support", arXiv 1607.06618).
+ *
+ * Phase one (Sec. 2.1, Sec. 2.3 "Phase One"): reads are 2-bit encoded, split into super-mers
+ * by their minimizers (Fig. 1, KMC2 ordering of Sec. 3.1) and distributed to bins -- the
+ * paper's temporary files -- so that every occurrence of a k-mer lands in one bin.
+ * Phase two (Sec. 2.2, Sec. 2.3 "Phase Two", Sec. 3.3-3.4): each bin's super-mers are split
+ * into k-mers, each k-mer is replaced by its canonical form (Sec. 2.4.2) and counted in an
+ * open-addressing hash table (Alg. 1); k-mers that exhaust the probe limit go to an
+ * overflow area that is recounted afterwards (Sec. 3.4 "Probing Strategy"); the table is
+ * then compacted under the minimal-occurrence filter (App. A, flag -l).
+ *
+ * Every step runs in hand-written CUDA kernels for sm_103a on the context's stream.  There
+ * is no CPU fallback: without a usable device every call fails with GERBIL_E_CUDA.
+ *
+ * Conventions
+ *  - Return value: 0 (GERBIL_OK) or a positive gerbil_status.  No call throws, traps or
+ *    aborts; device kernels report problems through an error word read by the host.
+ *  - Key layout: A=0, C=1, G=2, T=3 (App. C), first base most significant.  A k-mer is the
+ *    base-4 integer of its bases held in W = ceil(2k/64) 64-bit words, word 0 most
+ *    significant, unused high bits of word 0 zero.  Numeric order equals lexicographic order
+ *    with A<C<G<T, so the canonical key is the numerically smaller of x and revcomp(x).
+ *  - Results are unordered (one row per distinct key); callers sort if they need an order.
+ *  - Ownership: the caller owns every buffer it passes and must keep it valid until the call
+ *    returns.  Objects returned through out-parameters (gerbil_bins, gerbil_counts) are owned
+ *    by the library until the matching *_free call, and must be freed before the context
+ *    that made them is destroyed.  Device memory is charged against the context's budget.
+ *  - Threading: one context must not be used by two host threads at once.
+ */
+#ifndef GERBIL_H
+#define GERBIL_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GERBIL_ABI_VERSION 1
+/* Largest supported k: W = 8 words (the paper supports k up to 479, App. A flag -k). */
+#define GERBIL_MAX_K 256
+#define GERBIL_MIN_K 8
+
+typedef enum gerbil_status {
+  GERBIL_OK = 0,
+  GERBIL_E_INVAL = 1,       /* an argument is out of range or inconsistent */
+  GERBIL_E_UNSUPPORTED = 2, /* valid per the paper, not built here (k > GERBIL_MAX_K) */
+  GERBIL_E_NOMEM = 3,       /* the context's HBM budget (or the device) cannot hold the work */
+  GERBIL_E_OVERFLOW = 4,    /* the overflow area stayed full after every retry */
+  GERBIL_E_TIMEOUT = 5,     /* a bounded device-side wait gave up */
+  GERBIL_E_CUDA = 6,        /* a CUDA runtime call failed (see gerbil_last_error) */
+  GERBIL_E_STATE = 7        /* a device consistency check failed (internal error) */
+} gerbil_status;
+
+typedef enum gerbil_ordering {
+  GERBIL_ORDER_KMC2 = 0, /* Sec. 3.1 "KMC2": lexicographic, m-mers starting with AAA or ACA or
+                            holding AA past position 0 ranked last (Gerbil's choice) */
+  GERBIL_ORDER_LEX = 1   /* plain lexicographic A<C<G<T (the ordering of Fig. 1) */
+} gerbil_ordering;
+
+typedef struct gerbil_ctx gerbil_ctx;       /* device, stream, memory budget, scratch */
+typedef struct gerbil_bins gerbil_bins;     /* device-resident bins of super-mers */
+typedef struct gerbil_counts gerbil_counts; /* device-resident (k-mer, count) rows */
+
+/* Input reads.  Read i is seq[offsets[i] .. offsets[i+1]); offsets has nreads+1
+ * non-decreasing entries and offsets[0] == 0.  Bytes other than A,C,G,T,a,c,g,t are
+ * undetermined bases (Sec. 2.4.1): every k-mer holding one is ignored.  With on_device == 1
+ * both pointers are device pointers on the context's device; with 0 they are host pointers
+ * and the call copies them to the device on the context's stream. */
+typedef struct gerbil_reads {
+  const uint8_t* seq;
+  const uint64_t* offsets;
+  uint64_t nreads;
+  int32_t on_device;
+  int32_t reserved;
+} gerbil_reads;
+
+/* Options; fill with gerbil_opts_default() and change fields. */
+typedef struct gerbil_opts {
+  int32_t canonical;           /* 1: count min(x, revcomp(x)) (Sec. 2.4.2); 0: flag -d */
+  int32_t ordering;            /* gerbil_ordering of the minimizers (Sec. 3.1) */
+  int32_t canonical_minimizer; /* 1: minimizer over canonical m-mers, so x and revcomp(x)
+                                  share a bin; 0: forward m-mers as in Fig. 1 (allowed only
+                                  with canonical == 0) */
+  uint32_t supermer_cap;       /* L_max: a super-mer is also cut before every window whose
+                                  global start position is a multiple of L_max (1..1024,
+                                  default 256) */
+  const uint32_t* bin_bounds;  /* host pointer, NULL or nbins-1 ascending split points: bin =
+                                  number of split points <= fmix32(minimizer); NULL: bin =
+                                  fmix32(minimizer) mod nbins */
+  uint32_t max_probes;         /* theta of Alg. 1: probes before a k-mer goes to overflow
+                                  (default 64) */
+  float load_factor;           /* target table load (default 0.5) */
+  float distinct_ratio;        /* expected distinct/occurrences per bin for table sizing
+                                  (Sec. 3.4 "Estimating table sizes"); 0: use the ratio the
+                                  context measured on earlier calls (1.0 at first) */
+  uint32_t overflow_slots;     /* capacity of the overflow area in k-mers; 0: automatic */
+  int32_t persistent;          /* count_batch: 1 = one persistent launch with a work queue
+                                  (default), 0 = one grid over all tiles */
+  uint32_t reserved[6];
+} gerbil_opts;
+
+/* Per-call statistics of a count. */
+typedef struct gerbil_count_stats {
+  uint64_t occurrences; /* k-mer occurrences inserted (N-free windows of the bins) */
+  uint64_t distinct;    /* distinct keys before the min_count filter */
+  uint64_t emitted;     /* rows in the result (count >= min_count) */
+  uint64_t overflowed;  /* insertions that went to the overflow area */
+  uint64_t table_slots; /* hash-table slots allocated over all bins */
+  uint32_t retries;     /* rounds repeated with larger tables because overflow was full */
+  uint32_t bins;        /* bins counted */
+} gerbil_count_stats;
+
+/* Device time of each step of the path, accumulated over the calls made since profiling was
+ * last enabled (CUDA events recorded on the context's stream around each step). */
+typedef struct gerbil_phase_times {
+  double encode_ms;       /* 2-bit encoding and read-boundary marks (phase one) */
+  double supermer_ms;     /* minimizers, super-mer split, bin count + scatter (phase one) */
+  double clear_ms;        /* table and counter clears (phase two) */
+  double insert_ms;       /* extract + canonicalise + insert launches (phase two) */
+  double compact_ms;      /* compaction under min_count (phase two) */
+  double overflow_ms;     /* overflow recount and merge (phase two) */
+  uint64_t insert_launches;
+  uint64_t kernel_launches; /* kernels of this library launched, counted with profiling off too */
+  uint64_t calls;           /* partition + count calls */
+} gerbil_phase_times;
+
+/* Fills *opts with the defaults listed above. */
+void gerbil_opts_default(gerbil_opts* opts);
+
+/* Human-readable name of a status code; never NULL. */
+const char* gerbil_strerror(int status);
+
+/* Text of the last CUDA or argument error seen on this context ("" if none). */
+const char* gerbil_last_error(const gerbil_ctx* ctx);
+
+/* Creates a context on CUDA device `device`.  hbm_budget_bytes bounds the device memory the
+ * context may hold at once (0 = no bound).  cuda_stream is a cudaStream_t on that device that
+ * every call is ordered on (NULL = the context creates its own non-blocking stream).
+ * Errors: E_INVAL (bad device), E_CUDA. */
+int gerbil_create(gerbil_ctx** out, int device, uint64_t hbm_budget_bytes, void* cuda_stream);
+
+/* Destroys the context and releases its scratch memory (not the caller's stream). */
+void gerbil_destroy(gerbil_ctx* ctx);
+
+/* Enables (1) or disables (0) per-step event timing and resets the accumulated times and
+ * launch counters.  Timing adds two event records per step; results are unchanged. */
+int gerbil_profile(gerbil_ctx* ctx, int enable);
+
+/* Copies the accumulated step times and launch counters (see gerbil_phase_times). */
+int gerbil_get_phase_times(const gerbil_ctx* ctx, gerbil_phase_times* out);
+
+/* Phase one (Sec. 2.1, Fig. 1; Sec. 2.3 Phase One steps 2-4): encodes the reads to 2 bits
+ * per base, computes for every window of k determined bases its minimizer (the m-mer of
+ * smallest rank under opts->ordering), cuts the windows of each read into super-mers --
+ * maximal runs of consecutive windows with one minimizer value, also cut at multiples of
+ * L_max -- and distributes them to nbins bins.  The bins keep the 2-bit bases and one
+ * descriptor per super-mer on the device, together with per-bin statistics (the paper's
+ * binStatFile, App. A flag -x).  Requires GERBIL_MIN_K <= k <= GERBIL_MAX_K,
+ * 1 <= m <= min(k-1, 15), 1 <= nbins <= 65536; a bin may hold fewer than 2^32 k-mers.
+ * Errors: E_INVAL, E_UNSUPPORTED (k > GERBIL_MAX_K), E_NOMEM, E_CUDA. */
+int gerbil_partition(gerbil_ctx* ctx, const gerbil_reads* reads, int k, int m, int nbins,
+                     const gerbil_opts* opts, gerbil_bins** out);
+
+/* Totals of a bins object (any pointer may be NULL). */
+int gerbil_bins_info(const gerbil_bins* bins, int* k, int* m, int* nbins, uint64_t* n_supermers,
+                     uint64_t* n_kmers);
+
+/* binStatFile row of one bin: super-mers, bases (sum of super-mer lengths), k-mers. */
+int gerbil_bin_stats(const gerbil_bins* bins, int bin, uint64_t* n_super, uint64_t* n_bases,
+                     uint64_t* n_kmers);
+
+/* Copies the super-mer descriptors to host arrays of capacity cap (>= n_supermers):
+ * global start position of the super-mer's first base in the input, its number of
+ * k-mers, and its bin.  Order within a bin is unspecified.  Errors: E_INVAL (cap). */
+int gerbil_bins_export(const gerbil_bins* bins, uint64_t* pos, uint32_t* nkmers, uint32_t* bin,
+                       uint64_t cap);
+
+void gerbil_bins_free(gerbil_bins* bins);
+
+/* Phase two for one bin (Sec. 2.3 Phase Two; Alg. 1; Sec. 3.4): splits the bin's super-mers
+ * into k-mers, canonicalises each (unless opts->canonical == 0), inserts it into an
+ * open-addressing table sized from the bin statistics (Sec. 3.4 "Estimating table sizes"),
+ * sends a k-mer that exhausts max_probes probes to the overflow area, recounts the overflow
+ * and merges it, and keeps every key with count >= min_count.  k must equal the k given to
+ * gerbil_partition.  Errors: E_INVAL, E_NOMEM, E_OVERFLOW, E_TIMEOUT, E_STATE, E_CUDA. */
+int gerbil_count(gerbil_ctx* ctx, const gerbil_bins* bins, int bin, int k, uint32_t min_count,
+                 const gerbil_opts* opts, gerbil_counts** out);
+
+/* Phase two for many bins at once: the bins listed in bin_list (host array of nb distinct
+ * bin indices; NULL = all bins, nb ignored) are counted together and their rows returned in
+ * one result.  Because bins partition the k-mers, the rows are the union of the per-bin
+ * results.  With opts->persistent (default) one persistent kernel pops tiles of all bins
+ * from a device work queue.  Errors: as gerbil_count. */
+int gerbil_count_batch(gerbil_ctx* ctx, const gerbil_bins* bins, const int32_t* bin_list,
+                       int nb, int k, uint32_t min_count, const gerbil_opts* opts,
+                       gerbil_counts** out);
+
+/* Size and statistics of a result (any pointer may be NULL). */
+int gerbil_counts_info(const gerbil_counts* counts, uint64_t* n, int* words,
+                       gerbil_count_stats* stats);
+
+/* Device pointers of a result: keys[n][W] (row-major, layout above) and counts[n] (u32).
+ * Valid until gerbil_counts_free. */
+int gerbil_counts_view(const gerbil_counts* counts, const uint64_t** keys_dev,
+                       const uint32_t** counts_dev);
+
+/* Copies a result to host arrays: keys (cap*W words) and counts (cap entries).
+ * Errors: E_INVAL if cap < n. */
+int gerbil_counts_to_host(const gerbil_counts* counts, uint64_t* keys, uint32_t* counts_out,
+                          uint64_t cap);
+
+void gerbil_counts_free(gerbil_counts* counts);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GERBIL_H */

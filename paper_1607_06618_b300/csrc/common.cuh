@@ -1,0 +1,158 @@
+// common.cuh -- device-side building blocks shared by the phase-one and phase-two kernels.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace gerbil {
+
+// ---- device error word bits (host maps them to gerbil_status) ----------------------------
+enum : uint32_t {
+  ERR_OVF_FULL = 1u << 0,   // the overflow area was full: some k-mers were not recorded
+  ERR_SPIN = 1u << 1,       // a bounded wait gave up where no fallback exists
+  ERR_STATE = 1u << 2,      // a claimed slot was never published / descriptor mismatch
+  ERR_OUT_FULL = 1u << 3,   // the result buffer was too small
+  ERR_QUEUE = 1u << 4,      // a work-queue wait gave up
+};
+
+// Device counters block, one per context, cleared per call.
+struct Counters {
+  unsigned long long ovf_count;      // overflow-area cursor
+  unsigned long long out_count;      // result cursor
+  unsigned long long distinct;       // live slots seen by the compaction
+  unsigned long long spin_demotions; // inserts demoted to overflow after a bounded wait
+  unsigned long long queue_head;     // persistent-kernel work queue cursor
+  unsigned long long merged;         // overflow keys merged into a main-table key
+  unsigned long long pad[9];
+  unsigned int err;                  // ERR_* bits
+  unsigned int pad2;
+};
+
+// ---- table slot layout -------------------------------------------------------------------
+// A slot is (W+1) 64-bit words: word 0 = meta, words 1..W = key.  meta's low 32 bits hold the
+// count; the high 32 bits hold the state: CLAIMED | PUBLISHED | MERGED | 29-bit tag taken from
+// the key's hash.  meta == 0 is an empty slot.
+constexpr uint32_t META_CLAIMED = 1u << 31;
+constexpr uint32_t META_PUBLISHED = 1u << 30;
+constexpr uint32_t META_MERGED = 1u << 29;
+constexpr uint32_t META_TAG_MASK = (1u << 29) - 1;
+constexpr unsigned long long PUB64 = (unsigned long long)META_PUBLISHED << 32;
+constexpr unsigned long long MERGED64 = (unsigned long long)META_MERGED << 32;
+
+// ---- memory-model helpers (PTX, gpu scope) -------------------------------------------------
+__device__ __forceinline__ unsigned long long ld_relaxed(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ unsigned long long ld_acquire(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_relaxed(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long cas_acquire(unsigned long long* p,
+                                                          unsigned long long cmp,
+                                                          unsigned long long val) {
+  unsigned long long old;
+  asm volatile("atom.acquire.gpu.global.cas.b64 %0, [%1], %2, %3;"
+               : "=l"(old)
+               : "l"(p), "l"(cmp), "l"(val)
+               : "memory");
+  return old;
+}
+__device__ __forceinline__ void red_add(unsigned long long* p, unsigned long long v) {
+  asm volatile("red.relaxed.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ void red_or_release(unsigned long long* p, unsigned long long v) {
+  asm volatile("red.release.gpu.global.or.b64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long atom_or(unsigned long long* p, unsigned long long v) {
+  unsigned long long old;
+  asm volatile("atom.relaxed.gpu.global.or.b64 %0, [%1], %2;" : "=l"(old) : "l"(p), "l"(v) : "memory");
+  return old;
+}
+
+// ---- bases --------------------------------------------------------------------------------
+// The packed stream holds base i of the input at word i/32, bits (63-2*(i%32), 62-2*(i%32)):
+// first base in the high bits, A=0 C=1 G=2 T=3.  Masks hold base i at u32 word i/32, bit
+// 31-(i%32).
+
+// Reverse the order of the 32 two-bit groups of a word.
+__device__ __forceinline__ unsigned long long rev2(unsigned long long x) {
+  unsigned long long y = __brevll(x);
+  return ((y >> 1) & 0x5555555555555555ull) | ((y & 0x5555555555555555ull) << 1);
+}
+
+// k-mer of k bases starting at base `pos`, as W words (word 0 most significant, right-aligned
+// integer).  Reads W+1 words of the packed stream (the stream carries two words of padding).
+template <int W>
+__device__ __forceinline__ void load_kmer(const unsigned long long* __restrict__ packed,
+                                          unsigned long long pos, int k,
+                                          unsigned long long key[W]) {
+  const unsigned long long* w = packed + (pos >> 5);
+  const int o = 2 * int(pos & 31);
+  unsigned long long v[W + 1];
+#pragma unroll
+  for (int j = 0; j <= W; ++j) v[j] = __ldg(w + j);
+  unsigned long long L[W];
+#pragma unroll
+  for (int j = 0; j < W; ++j) L[j] = o ? ((v[j] << o) | (v[j + 1] >> (64 - o))) : v[j];
+  const int s = 64 * W - 2 * k;  // 0 <= s < 64
+#pragma unroll
+  for (int j = W - 1; j >= 1; --j) key[j] = s ? ((L[j] >> s) | (L[j - 1] << (64 - s))) : L[j];
+  key[0] = L[0] >> s;
+}
+
+// Reverse complement of a right-aligned k-mer (Sec. 2.4.2).
+template <int W>
+__device__ __forceinline__ void revcomp(const unsigned long long key[W], int k,
+                                        unsigned long long rc[W]) {
+  unsigned long long t[W];
+#pragma unroll
+  for (int j = 0; j < W; ++j) t[W - 1 - j] = rev2(~key[j]);
+  const int s = 64 * W - 2 * k;
+#pragma unroll
+  for (int j = W - 1; j >= 1; --j) rc[j] = s ? ((t[j] >> s) | (t[j - 1] << (64 - s))) : t[j];
+  rc[0] = t[0] >> s;
+}
+
+template <int W>
+__device__ __forceinline__ bool key_less(const unsigned long long a[W],
+                                         const unsigned long long b[W]) {
+#pragma unroll
+  for (int j = 0; j < W; ++j)
+    if (a[j] != b[j]) return a[j] < b[j];
+  return false;
+}
+
+// 64-bit hash of a key: per-word multiply/xorshift rounds, MurmurHash3-style finalizer.
+template <int W>
+__device__ __forceinline__ unsigned long long key_hash(const unsigned long long key[W]) {
+  unsigned long long h = 0x9E3779B97F4A7C15ull * (unsigned long long)(W + 1);
+#pragma unroll
+  for (int j = 0; j < W; ++j) {
+    h ^= key[j];
+    h *= 0xff51afd7ed558ccdull;
+    h ^= h >> 33;
+  }
+  h *= 0xc4ceb9fe1a85ec53ull;
+  h ^= h >> 33;
+  return h;
+}
+
+// MurmurHash3 32-bit finalizer (Appleby): minimizer -> bin mixer.
+__device__ __forceinline__ uint32_t fmix32(uint32_t h) {
+  h ^= h >> 16;
+  h *= 0x85ebca6bu;
+  h ^= h >> 13;
+  h *= 0xc2b2ae35u;
+  h ^= h >> 16;
+  return h;
+}
+
+__device__ __forceinline__ void set_err(Counters* c, uint32_t bits) { atomicOr(&c->err, bits); }
+
+}  // namespace gerbil

@@ -1,0 +1,113 @@
+// kernels.h -- launch interface between the host runtime (runtime.cu) and the kernels.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace gerbil {
+
+struct Counters;
+
+// ---- phase one ------------------------------------------------------------------------------
+struct SupermerParams {
+  const unsigned long long* packed;  // 2-bit bases, nwords + 2 padding words
+  const uint32_t* nmask;             // undetermined-base mask, nwords + 2 words
+  const uint32_t* bmask;             // read-start mask, nwords + 2 words
+  uint64_t n;                        // bases in the input
+  uint64_t nwords;                   // ceil((n + 1) / 32)
+  uint64_t nwin;                     // window starts: n - k + 1 (0 if n < k)
+  int k, m;
+  int ordering, canon_min;
+  uint32_t lmax;                     // super-mer cap L_max
+  uint32_t nbins;
+  const uint32_t* bounds;            // device, nbins-1 split points, or NULL
+  int tile;                          // window starts per CTA
+  // pass 0
+  unsigned long long* bin_nsuper;
+  unsigned long long* bin_nkmers;
+  // pass 1
+  const unsigned long long* bin_sm_begin;
+  unsigned long long* bin_cursor;    // (super-mers << 32) | k-mers, cleared before pass 1
+  unsigned long long* sm_pos;        // global start of each super-mer
+  uint32_t* sm_koff;                 // first k-mer of each super-mer within its bin
+  unsigned int* err;                 // ERR_* bits
+};
+
+cudaError_t launch_encode(const uint8_t* seq, uint64_t n, unsigned long long* packed,
+                          uint32_t* nmask, uint64_t nwords, int vec_ok, int nsm, cudaStream_t st);
+cudaError_t launch_boundary(const uint64_t* offsets, uint64_t nreads, uint64_t n, uint32_t* bmask,
+                            unsigned int* err, cudaStream_t st);
+cudaError_t launch_supermer(const SupermerParams& p, int pass, cudaStream_t st);
+size_t supermer_smem_bytes(int tile, int lmax, int k);
+
+// ---- phase two ------------------------------------------------------------------------------
+// One entry per bin being counted.
+struct BinWork {
+  unsigned long long sm_begin;   // first super-mer of the bin in sm_pos / sm_koff
+  unsigned long long table_off;  // first slot of the bin's table in the arena
+  uint32_t n_super;
+  uint32_t n_kmers;
+  uint32_t cap;                  // table slots
+  uint32_t tile_begin;           // first global tile index of the bin
+};
+
+constexpr int COUNT_THREADS = 256;
+constexpr int KMERS_PER_THREAD = 4;
+constexpr int COUNT_TILE = COUNT_THREADS * KMERS_PER_THREAD;
+
+struct CountParams {
+  const unsigned long long* packed;
+  const unsigned long long* sm_pos;
+  const uint32_t* sm_koff;
+  const BinWork* work;
+  uint32_t nwork;
+  uint32_t ntiles;
+  uint32_t tile_base;            // first tile of this launch (per-bin launches)
+  int k;
+  int canonical;
+  uint32_t theta;                // max probes (Alg. 1)
+  uint32_t spin_limit;           // bounded wait on an unpublished slot
+  unsigned long long* arena;     // all tables, (W+1) words per slot
+  unsigned long long* ovf;       // overflow area, W words per k-mer
+  unsigned long long ovf_cap;
+  uint32_t* bin_ovf;             // overflow k-mers per work entry
+  Counters* ctr;
+};
+
+struct CompactParams {
+  const BinWork* work;
+  uint32_t nwork;
+  unsigned long long slot_lo, slot_hi;  // slots of the arena to scan
+  unsigned long long* arena;
+  const uint32_t* bin_ovf;
+  int mode;                      // 0: skip bins with overflow; 1: only those, merged with O
+  unsigned long long* otab;      // overflow recount table
+  uint32_t ocap;
+  uint32_t min_count;
+  unsigned long long* out_keys;
+  uint32_t* out_counts;
+  unsigned long long out_cap;
+  Counters* ctr;
+};
+
+struct OverflowParams {
+  const unsigned long long* ovf;
+  unsigned long long ovf_cap;
+  unsigned long long* otab;
+  uint32_t ocap;
+  uint32_t spin_limit;
+  uint32_t min_count;
+  unsigned long long* out_keys;
+  uint32_t* out_counts;
+  unsigned long long out_cap;
+  Counters* ctr;
+};
+
+cudaError_t launch_insert(int W, const CountParams& p, unsigned grid, cudaStream_t st);
+cudaError_t launch_insert_persistent(int W, const CountParams& p, unsigned grid, cudaStream_t st);
+cudaError_t launch_compact(int W, const CompactParams& p, int nsm, cudaStream_t st);
+cudaError_t launch_overflow_insert(int W, const OverflowParams& p, int nsm, cudaStream_t st);
+cudaError_t launch_overflow_emit(int W, const OverflowParams& p, int nsm, cudaStream_t st);
+
+}  // namespace gerbil

@@ -1,0 +1,270 @@
+// partition.cu -- phase one on the GPU: 2-bit encoding, rolling minimizers, super-mer split
+// and bin scatter (Sec. 2.1, Fig. 1; Sec. 2.3 Phase One; Sec. 3.1-3.2).
+#include <algorithm>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace gerbil {
+
+// ---- N1: ASCII -> 2-bit codes + undetermined-base mask -------------------------------------
+// One thread per 32 bases: packed word (A=0 C=1 G=2 T=3, first base high) and a 32-bit mask
+// of undetermined bases (Sec. 2.4.1: anything but ACGTacgt).
+__device__ __forceinline__ void encode_byte(uint32_t c, unsigned long long& word, uint32_t& mask,
+                                            int j) {
+  const uint32_t u = c & 0xDFu;  // upper case
+  const bool ok = (u == 'A') | (u == 'C') | (u == 'G') | (u == 'T');
+  uint32_t t = (u >> 1) & 3u;  // A->0 C->1 G->3 T->2
+  t ^= t >> 1;                 // A->0 C->1 G->2 T->3
+  word |= (unsigned long long)(ok ? t : 0u) << (62 - 2 * j);
+  mask |= (ok ? 0u : 1u) << (31 - j);
+}
+
+__global__ void __launch_bounds__(256) encode_kernel(const uint8_t* __restrict__ seq, uint64_t n,
+                                                     unsigned long long* __restrict__ packed,
+                                                     uint32_t* __restrict__ nmask,
+                                                     uint64_t nwords, int vec_ok) {
+  for (uint64_t w = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; w < nwords;
+       w += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t b0 = w * 32;
+    unsigned long long word = 0;
+    uint32_t mask = 0;
+    if (vec_ok && b0 + 32 <= n) {
+      const uint4* p = reinterpret_cast<const uint4*>(seq + b0);
+      const uint4 a = __ldg(p), b = __ldg(p + 1);
+      const uint32_t v[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) encode_byte((v[q] >> (8 * j)) & 0xFFu, word, mask, 4 * q + j);
+    } else {
+      for (int j = 0; j < 32; ++j) {
+        if (b0 + j < n)
+          encode_byte(seq[b0 + j], word, mask, j);
+        else
+          mask |= 1u << (31 - j);  // past the end: undetermined
+      }
+    }
+    packed[w] = word;
+    nmask[w] = mask;
+  }
+}
+
+// Read boundaries: bit at every offsets[r] (read starts and the end of the last read).
+// Offsets past the input or out of order are reported (err) and skipped.
+__global__ void boundary_kernel(const uint64_t* __restrict__ offsets, uint64_t nreads, uint64_t n,
+                                uint32_t* __restrict__ bmask, unsigned int* __restrict__ err) {
+  for (uint64_t r = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; r <= nreads;
+       r += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t i = offsets[r];
+    if (i > n || (r > 0 && offsets[r - 1] > i)) {
+      atomicOr(err, ERR_STATE);
+      continue;
+    }
+    atomicOr(bmask + (i >> 5), 1u << (31 - (i & 31)));
+  }
+}
+
+// ---- N2/N3: minimizers, super-mers, bins ---------------------------------------------------
+// One CTA owns the window starts [P0, P0+T) of the global base stream.  It stages the 2-bit
+// bases and masks it needs in shared memory, computes the rank of every m-mer, takes the
+// sliding minimum over w = k-m+1 m-mers by doubling, marks which windows are counted (no
+// undetermined base, no read boundary inside), and emits the super-mers that start in its
+// range.  A super-mer never runs past the next multiple of L_max, so the CTA looks at most
+// L_max windows past its range to find where its last super-mer ends.
+
+__device__ __forceinline__ unsigned long long bases64(const unsigned long long* sw, int lb) {
+  const int w = lb >> 5, o = 2 * (lb & 31);
+  return o ? ((sw[w] << o) | (sw[w + 1] >> (64 - o))) : sw[w];
+}
+__device__ __forceinline__ uint32_t bits32(const uint32_t* sm, int lb) {
+  const int w = lb >> 5, o = lb & 31;
+  return o ? ((sm[w] << o) | (sm[w + 1] >> (32 - o))) : sm[w];
+}
+
+// KMC2 reading (Sec. 3.1): demote m-mers that start with AAA or ACA or hold AA past
+// position 0.  v holds m bases in its low 2m bits, first base most significant.
+__device__ __forceinline__ uint32_t kmc2_demoted(uint32_t v, int m) {
+  uint32_t d = 0;
+  if (m >= 3) {
+    const uint32_t head = v >> (2 * m - 6);
+    d |= (head == 0u) | (head == 4u);  // AAA = 000000, ACA = 000100
+  }
+  if (m >= 3) {
+    const uint32_t lowbits = (m >= 16) ? 0xFFFFFFFFu : ((1u << (2 * m)) - 1u);
+    uint32_t a = ~(v | (v >> 1)) & 0x55555555u & lowbits;  // low bit of group set iff base A
+    uint32_t pairs = a & (a >> 2);            // group g-1 flagged iff groups g, g-1 are A
+    pairs &= ~(1u << (2 * (m - 2)));          // drop the pair at position 0
+    d |= pairs != 0u;
+  }
+  return d;
+}
+
+__device__ __forceinline__ uint32_t mmer_rank(uint32_t v, int m, int ordering, int canon_min) {
+  uint32_t c = v;
+  if (canon_min) {
+    const uint32_t rc = (uint32_t)(rev2(~(unsigned long long)v) >> (64 - 2 * m));
+    c = rc < v ? rc : v;
+  }
+  if (ordering == 0) c |= kmc2_demoted(c, m) << 30;
+  return c;
+}
+
+template <int PASS>
+__global__ void __launch_bounds__(256) supermer_kernel(SupermerParams P) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const long long T = P.tile;
+  const long long P0 = (long long)blockIdx.x * T;
+  const long long nwin = (long long)P.nwin;
+  if (P0 >= nwin) return;
+  const long long P1 = min(P0 + T, nwin);
+  const long long O = P0 - 1;  // global window / base of local index 0
+  const int k = P.k, m = P.m, w = k - m + 1;
+  const long long lmax = P.lmax;
+  const int NW = (int)(min(P1 + lmax, nwin) - O);
+  const int NQ = NW + (k - m);
+  const int NB = NW + k - 1;
+  const long long wlo = (O >= 0) ? (O >> 5) : -1;  // first staged word
+  const int nsw = (int)(((O + NB - 1) >> 5) - wlo) + 2;
+
+  unsigned long long* sw = reinterpret_cast<unsigned long long*>(smem);
+  uint32_t* snm = reinterpret_cast<uint32_t*>(sw + nsw);
+  uint32_t* scm = snm + nsw;
+  uint32_t* rk0 = scm + nsw;
+  uint32_t* rk1 = rk0 + NQ;
+  uint8_t* V = reinterpret_cast<uint8_t*>(rk1 + NQ);
+
+  const long long nwords = (long long)P.nwords;
+  for (int i = threadIdx.x; i < nsw; i += blockDim.x) {
+    const long long g = wlo + i;
+    const bool in = g >= 0 && g < nwords;
+    sw[i] = in ? __ldg(P.packed + g) : 0ull;
+    const uint32_t nm = in ? __ldg(P.nmask + g) : 0xFFFFFFFFu;
+    snm[i] = nm;
+    scm[i] = nm | (in ? __ldg(P.bmask + g) : 0xFFFFFFFFu);
+  }
+  __syncthreads();
+
+  const int lbO = (int)(O - 32 * wlo);  // local base index of global base O
+  const long long n = (long long)P.n;
+  for (int iq = threadIdx.x; iq < NQ; iq += blockDim.x) {
+    const long long q = O + iq;
+    uint32_t r = 0xFFFFFFFFu;
+    if (q >= 0 && q + m <= n) {
+      const int lb = lbO + iq;
+      if ((bits32(snm, lb) >> (32 - m)) == 0u) {
+        const uint32_t v = (uint32_t)(bases64(sw, lb) >> (64 - 2 * m));
+        r = mmer_rank(v, m, P.ordering, P.canon_min);
+      }
+    }
+    rk0[iq] = r;
+  }
+
+  // sliding minimum over w ranks: after the loop A[i] = min(rank[i .. i+span)).
+  uint32_t* A = rk0;
+  uint32_t* B = rk1;
+  int len = NQ, span = 1;
+  while (2 * span <= w) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < len - span; i += blockDim.x) B[i] = min(A[i], A[i + span]);
+    len -= span;
+    span *= 2;
+    uint32_t* t = A;
+    A = B;
+    B = t;
+  }
+  __syncthreads();
+  uint32_t* M = B;  // window minima
+  for (int i = threadIdx.x; i < NW; i += blockDim.x) {
+    M[i] = min(A[i], A[i + w - span]);
+    const long long p = O + i;
+    bool ok = p >= 0 && p < nwin;
+    if (ok) {
+      const int lb = lbO + i;
+      ok = (bits32(snm, lb) >> 31) == 0u;  // base p determined
+      for (int c = 1; ok && c < k; c += 32) {  // no N and no read start in (p, p+k)
+        const int l = min(32, k - c);
+        ok = (bits32(scm, lb + c) >> (32 - l)) == 0u;
+      }
+    }
+    V[i] = ok;
+  }
+  __syncthreads();
+
+  const uint32_t vmask = (2 * m >= 32) ? 0xFFFFFFFFu : ((1u << (2 * m)) - 1u);
+  const int own = (int)(P1 - P0);
+  for (int i = 1 + threadIdx.x; i <= own; i += blockDim.x) {
+    if (!V[i]) continue;
+    const long long p = O + i;
+    const uint32_t mi = M[i];
+    if (V[i - 1] && M[i - 1] == mi && (p % lmax) != 0) continue;
+    int j = i + 1;
+    while (((O + j) % lmax) != 0 && j < NW && V[j] && M[j] == mi) ++j;
+    const uint32_t nk = (uint32_t)(j - i);
+    const uint32_t h = fmix32(mi & vmask);
+    uint32_t bin;
+    if (P.bounds) {
+      uint32_t lo = 0, hi = P.nbins - 1;  // number of split points <= h
+      while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (__ldg(P.bounds + mid) <= h) lo = mid + 1; else hi = mid;
+      }
+      bin = lo;
+    } else {
+      bin = h % P.nbins;
+    }
+    if (PASS == 0) {
+      atomicAdd(P.bin_nsuper + bin, 1ull);
+      atomicAdd(P.bin_nkmers + bin, (unsigned long long)nk);
+    } else {
+      const unsigned long long old = atomicAdd(P.bin_cursor + bin, (1ull << 32) | nk);
+      if ((old >> 32) >= P.bin_nsuper[bin]) {  // the two passes disagree: never expected
+        atomicOr(P.err, ERR_STATE);
+        continue;
+      }
+      const unsigned long long idx = P.bin_sm_begin[bin] + (old >> 32);
+      P.sm_pos[idx] = (unsigned long long)p;
+      P.sm_koff[idx] = (uint32_t)old;
+    }
+  }
+}
+
+size_t supermer_smem_bytes(int tile, int lmax, int k) {
+  const long long NW = (long long)tile + 1 + lmax;
+  const long long NQ = NW + k;  // upper bound (m >= 1)
+  const long long NB = NW + k;
+  const long long nsw = NB / 32 + 3;
+  return nsw * 8 + 2 * nsw * 4 + 2 * NQ * 4 + NW + 16;
+}
+
+cudaError_t launch_encode(const uint8_t* seq, uint64_t n, unsigned long long* packed,
+                          uint32_t* nmask, uint64_t nwords, int vec_ok, int nsm,
+                          cudaStream_t st) {
+  if (nwords == 0) return cudaSuccess;
+  const uint64_t blocks = std::min<uint64_t>((nwords + 255) / 256, (uint64_t)nsm * 16);
+  encode_kernel<<<(unsigned)blocks, 256, 0, st>>>(seq, n, packed, nmask, nwords, vec_ok);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_boundary(const uint64_t* offsets, uint64_t nreads, uint64_t n, uint32_t* bmask,
+                            unsigned int* err, cudaStream_t st) {
+  const uint64_t blocks = std::min<uint64_t>((nreads + 1 + 255) / 256, 4096);
+  boundary_kernel<<<(unsigned)blocks, 256, 0, st>>>(offsets, nreads, n, bmask, err);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_supermer(const SupermerParams& p, int pass, cudaStream_t st) {
+  if (p.nwin == 0) return cudaSuccess;
+  const uint64_t blocks = (p.nwin + p.tile - 1) / p.tile;
+  const size_t smem = supermer_smem_bytes(p.tile, p.lmax, p.k);
+  if (pass == 0) {
+    cudaFuncSetAttribute(supermer_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    supermer_kernel<0><<<(unsigned)blocks, 256, smem, st>>>(p);
+  } else {
+    cudaFuncSetAttribute(supermer_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    supermer_kernel<1><<<(unsigned)blocks, 256, smem, st>>>(p);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace gerbil

@@ -1,0 +1,821 @@
+// runtime.cu -- host side of the C ABI (include/gerbil.h): contexts, device memory under an
+// HBM budget, phase-one orchestration, table sizing (Sec. 3.4 "Estimating table sizes"),
+// phase-two launches and the overflow recount (Sec. 3.4 "Probing Strategy").
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/gerbil.h"
+#include "common.cuh"
+#include "kernels.h"
+
+using gerbil::BinWork;
+using gerbil::Counters;
+
+struct gerbil_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  uint64_t budget = 0;  // 0 = unbounded
+  uint64_t used = 0;
+  int nsm = 148;
+  int insert_ctas_per_sm = 8;
+  double ratio = 1.0;  // distinct / occurrences measured on earlier calls
+  bool ratio_known = false;
+  Counters* ctr = nullptr;   // device
+  Counters* hctr = nullptr;  // pinned host mirror
+  std::string last_error;
+  // cached scratch (grow-only)
+  void* arena = nullptr;
+  size_t arena_bytes = 0;
+  void* ovf = nullptr;
+  size_t ovf_bytes = 0;
+  void* small = nullptr;  // work list + bin_ovf
+  size_t small_bytes = 0;
+  // step timing (gerbil_profile): an event pair per phase, collected after a stream sync
+  bool profiling = false;
+  cudaEvent_t ev[2 * 8] = {};
+  bool pending[8] = {};
+  gerbil_phase_times times{};
+};
+
+struct gerbil_bins {
+  gerbil_ctx* ctx = nullptr;
+  int k = 0, m = 0, nbins = 0;
+  int canon_min = 1;
+  uint64_t n = 0, nwords = 0;
+  unsigned long long* packed = nullptr;
+  size_t packed_bytes = 0;
+  unsigned long long* sm_pos = nullptr;
+  uint32_t* sm_koff = nullptr;
+  size_t sm_bytes = 0;
+  uint64_t n_super_total = 0, n_kmers_total = 0;
+  std::vector<uint64_t> nsuper, nkmers, sm_begin;
+};
+
+struct gerbil_counts {
+  gerbil_ctx* ctx = nullptr;
+  int W = 1;
+  uint64_t n = 0;
+  unsigned long long* keys = nullptr;
+  uint32_t* counts = nullptr;
+  size_t bytes = 0;
+  gerbil_count_stats stats{};
+};
+
+namespace {
+
+int fail(gerbil_ctx* ctx, int status, const std::string& msg) {
+  if (ctx) ctx->last_error = msg;
+  return status;
+}
+
+#define CK(call)                                                                      \
+  do {                                                                                \
+    cudaError_t e_ = (call);                                                          \
+    if (e_ != cudaSuccess)                                                            \
+      return fail(ctx, GERBIL_E_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+int dev_alloc(gerbil_ctx* ctx, void** p, size_t bytes) {
+  *p = nullptr;
+  if (bytes == 0) return GERBIL_OK;
+  bytes = (bytes + 255) & ~size_t(255);
+  if (ctx->budget && ctx->used + bytes > ctx->budget)
+    return fail(ctx, GERBIL_E_NOMEM, "HBM budget exceeded");
+  cudaError_t e = cudaMallocAsync(p, bytes, ctx->stream);
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    return fail(ctx, GERBIL_E_NOMEM, "device out of memory");
+  }
+  if (e != cudaSuccess) return fail(ctx, GERBIL_E_CUDA, cudaGetErrorString(e));
+  ctx->used += bytes;
+  return GERBIL_OK;
+}
+
+void dev_free(gerbil_ctx* ctx, void* p, size_t bytes) {
+  if (!p) return;
+  bytes = (bytes + 255) & ~size_t(255);
+  cudaFreeAsync(p, ctx->stream);
+  ctx->used -= std::min(ctx->used, (uint64_t)bytes);
+}
+
+// Grow-only scratch buffer cached in the context.
+int scratch(gerbil_ctx* ctx, void** buf, size_t* have, size_t need) {
+  if (*have >= need && *buf) return GERBIL_OK;
+  dev_free(ctx, *buf, *have);
+  *buf = nullptr;
+  *have = 0;
+  size_t want = std::max(need, *have + *have / 4);
+  int rc = dev_alloc(ctx, buf, want);
+  if (rc == GERBIL_E_NOMEM && want > need) rc = dev_alloc(ctx, buf, want = need);
+  if (rc) return rc;
+  *have = want;
+  return GERBIL_OK;
+}
+
+void ph_collect(gerbil_ctx* ctx, bool wait);
+int read_counters(gerbil_ctx* ctx) {
+  CK(cudaMemcpyAsync(ctx->hctr, ctx->ctr, sizeof(Counters), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  ph_collect(ctx, false);
+  return GERBIL_OK;
+}
+
+int words_for(int k) { return (2 * k + 63) / 64; }
+
+enum Phase { PH_ENCODE = 0, PH_SUPER0, PH_SUPER1, PH_CLEAR, PH_INSERT, PH_COMPACT, PH_OVERFLOW, PH_N };
+
+void ph_begin(gerbil_ctx* ctx, int ph) {
+  if (ctx->profiling) cudaEventRecord(ctx->ev[2 * ph], ctx->stream);
+}
+void ph_end(gerbil_ctx* ctx, int ph) {
+  if (!ctx->profiling) return;
+  cudaEventRecord(ctx->ev[2 * ph + 1], ctx->stream);
+  ctx->pending[ph] = true;
+}
+// Adds the elapsed time of every finished phase; call only after the stream has synchronized
+// past the phase's end event (or pass wait = true).
+void ph_collect(gerbil_ctx* ctx, bool wait) {
+  for (int ph = 0; ph < PH_N; ++ph) {
+    if (!ctx->pending[ph]) continue;
+    if (wait) cudaEventSynchronize(ctx->ev[2 * ph + 1]);
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, ctx->ev[2 * ph], ctx->ev[2 * ph + 1]) != cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
+    ctx->pending[ph] = false;
+    gerbil_phase_times& t = ctx->times;
+    switch (ph) {
+      case PH_ENCODE: t.encode_ms += ms; break;
+      case PH_SUPER0:
+      case PH_SUPER1: t.supermer_ms += ms; break;
+      case PH_CLEAR: t.clear_ms += ms; break;
+      case PH_INSERT: t.insert_ms += ms; break;
+      case PH_COMPACT: t.compact_ms += ms; break;
+      case PH_OVERFLOW: t.overflow_ms += ms; break;
+      default: break;
+    }
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+void gerbil_opts_default(gerbil_opts* o) {
+  std::memset(o, 0, sizeof(*o));
+  o->canonical = 1;
+  o->ordering = GERBIL_ORDER_KMC2;
+  o->canonical_minimizer = 1;
+  o->supermer_cap = 256;
+  o->bin_bounds = nullptr;
+  o->max_probes = 64;
+  o->load_factor = 0.5f;
+  o->distinct_ratio = 0.0f;
+  o->overflow_slots = 0;
+  o->persistent = 1;
+}
+
+const char* gerbil_strerror(int s) {
+  switch (s) {
+    case GERBIL_OK: return "ok";
+    case GERBIL_E_INVAL: return "invalid argument";
+    case GERBIL_E_UNSUPPORTED: return "unsupported (k above the compiled maximum)";
+    case GERBIL_E_NOMEM: return "out of device memory or HBM budget";
+    case GERBIL_E_OVERFLOW: return "overflow area exhausted after all retries";
+    case GERBIL_E_TIMEOUT: return "bounded device wait gave up";
+    case GERBIL_E_CUDA: return "CUDA error";
+    case GERBIL_E_STATE: return "device consistency check failed";
+    default: return "unknown status";
+  }
+}
+
+const char* gerbil_last_error(const gerbil_ctx* ctx) { return ctx ? ctx->last_error.c_str() : ""; }
+
+int gerbil_create(gerbil_ctx** out, int device, uint64_t budget, void* stream) {
+  if (!out) return GERBIL_E_INVAL;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+    cudaGetLastError();
+    return GERBIL_E_CUDA;
+  }
+  if (device < 0 || device >= ndev) return GERBIL_E_INVAL;
+  gerbil_ctx* ctx = new (std::nothrow) gerbil_ctx;
+  if (!ctx) return GERBIL_E_NOMEM;
+  ctx->device = device;
+  ctx->budget = budget;
+  int rc = GERBIL_OK;
+  do {
+    if (cudaSetDevice(device) != cudaSuccess) { rc = GERBIL_E_CUDA; break; }
+    cudaDeviceGetAttribute(&ctx->nsm, cudaDevAttrMultiProcessorCount, device);
+    if (stream) {
+      ctx->stream = (cudaStream_t)stream;
+    } else {
+      if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) {
+        rc = GERBIL_E_CUDA;
+        break;
+      }
+      ctx->own_stream = true;
+    }
+    // keep freed blocks in the device's default pool: repeated calls reuse them
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
+      uint64_t thr = UINT64_MAX;
+      cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    if (cudaMalloc(&ctx->ctr, sizeof(Counters)) != cudaSuccess) { rc = GERBIL_E_CUDA; break; }
+    if (cudaMallocHost(&ctx->hctr, sizeof(Counters)) != cudaSuccess) { rc = GERBIL_E_CUDA; break; }
+    for (cudaEvent_t& e : ctx->ev)
+      if (cudaEventCreate(&e) != cudaSuccess) { rc = GERBIL_E_CUDA; break; }
+    if (rc) break;
+    int occ = 0;
+    // resident CTAs of the insert kernel decide the persistent grid; 8 x 256 threads is the
+    // SM's thread limit, refined by the occupancy query of the kernel in use at launch.
+    ctx->insert_ctas_per_sm = 8;
+    (void)occ;
+  } while (0);
+  if (rc) {
+    cudaGetLastError();
+    gerbil_destroy(ctx);
+    return rc;
+  }
+  *out = ctx;
+  return GERBIL_OK;
+}
+
+void gerbil_destroy(gerbil_ctx* ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->device);
+  if (ctx->stream) {
+    dev_free(ctx, ctx->arena, ctx->arena_bytes);
+    dev_free(ctx, ctx->ovf, ctx->ovf_bytes);
+    dev_free(ctx, ctx->small, ctx->small_bytes);
+    cudaStreamSynchronize(ctx->stream);
+  }
+  for (cudaEvent_t e : ctx->ev)
+    if (e) cudaEventDestroy(e);
+  if (ctx->ctr) cudaFree(ctx->ctr);
+  if (ctx->hctr) cudaFreeHost(ctx->hctr);
+  if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+  delete ctx;
+}
+
+int gerbil_profile(gerbil_ctx* ctx, int enable) {
+  if (!ctx) return GERBIL_E_INVAL;
+  CK(cudaSetDevice(ctx->device));
+  CK(cudaStreamSynchronize(ctx->stream));
+  ph_collect(ctx, true);
+  ctx->profiling = enable != 0;
+  std::memset(&ctx->times, 0, sizeof(ctx->times));
+  for (bool& p : ctx->pending) p = false;
+  return GERBIL_OK;
+}
+
+int gerbil_get_phase_times(const gerbil_ctx* cctx, gerbil_phase_times* out) {
+  if (!cctx || !out) return GERBIL_E_INVAL;
+  gerbil_ctx* ctx = const_cast<gerbil_ctx*>(cctx);
+  cudaSetDevice(ctx->device);
+  ph_collect(ctx, true);
+  *out = ctx->times;
+  return GERBIL_OK;
+}
+
+// ---- phase one ---------------------------------------------------------------------------------
+int gerbil_partition(gerbil_ctx* ctx, const gerbil_reads* reads, int k, int m, int nbins,
+                     const gerbil_opts* opts_in, gerbil_bins** out) {
+  if (!ctx || !reads || !out) return GERBIL_E_INVAL;
+  *out = nullptr;
+  gerbil_opts opts;
+  if (opts_in) opts = *opts_in; else gerbil_opts_default(&opts);
+  if (k > GERBIL_MAX_K) return fail(ctx, GERBIL_E_UNSUPPORTED, "k above GERBIL_MAX_K");
+  if (k < GERBIL_MIN_K || m < 1 || m >= k || m > 15 || nbins < 1 || nbins > 65536)
+    return fail(ctx, GERBIL_E_INVAL, "k, m or nbins out of range");
+  if (opts.supermer_cap < 1 || opts.supermer_cap > 1024)
+    return fail(ctx, GERBIL_E_INVAL, "supermer_cap out of range");
+  if (opts.ordering != GERBIL_ORDER_KMC2 && opts.ordering != GERBIL_ORDER_LEX)
+    return fail(ctx, GERBIL_E_INVAL, "unknown ordering");
+  if (reads->nreads > 0 && (!reads->seq || !reads->offsets))
+    return fail(ctx, GERBIL_E_INVAL, "null reads");
+  if (opts.bin_bounds) {
+    for (int i = 0; i + 2 < nbins; ++i)
+      if (opts.bin_bounds[i] > opts.bin_bounds[i + 1])
+        return fail(ctx, GERBIL_E_INVAL, "bin_bounds not ascending");
+  }
+  CK(cudaSetDevice(ctx->device));
+  cudaStream_t st = ctx->stream;
+
+  // total bases and offsets[0]
+  uint64_t first = 0, n = 0;
+  const uint64_t nreads = reads->nreads;
+  if (nreads > 0) {
+    if (reads->on_device) {
+      CK(cudaMemcpyAsync(&first, reads->offsets, 8, cudaMemcpyDeviceToHost, st));
+      CK(cudaMemcpyAsync(&n, reads->offsets + nreads, 8, cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+    } else {
+      first = reads->offsets[0];
+      n = reads->offsets[nreads];
+    }
+  }
+  if (first != 0) return fail(ctx, GERBIL_E_INVAL, "offsets[0] must be 0");
+
+  gerbil_bins* b = new (std::nothrow) gerbil_bins;
+  if (!b) return GERBIL_E_NOMEM;
+  b->ctx = ctx;
+  b->k = k;
+  b->m = m;
+  b->nbins = nbins;
+  b->canon_min = opts.canonical_minimizer ? 1 : 0;
+  b->n = n;
+  b->nwords = (n + 1 + 31) / 32;
+  b->nsuper.assign(nbins, 0);
+  b->nkmers.assign(nbins, 0);
+  b->sm_begin.assign(nbins + 1, 0);
+
+  // temporaries
+  uint8_t* dseq = nullptr;
+  uint64_t* doff = nullptr;
+  uint32_t* nmask = nullptr;
+  uint32_t* bmask = nullptr;
+  uint32_t* dbounds = nullptr;
+  unsigned long long* binbuf = nullptr;  // nsuper, nkmers, cursor, sm_begin
+  size_t seq_bytes = 0, off_bytes = 0, mask_bytes = 0, bounds_bytes = 0, binbuf_bytes = 0;
+  std::vector<unsigned long long> hbin;
+  int rc = GERBIL_OK;
+  auto cleanup = [&]() {
+    dev_free(ctx, dseq, seq_bytes);
+    dev_free(ctx, doff, off_bytes);
+    dev_free(ctx, nmask, mask_bytes);
+    dev_free(ctx, bmask, mask_bytes);
+    dev_free(ctx, dbounds, bounds_bytes);
+    dev_free(ctx, binbuf, binbuf_bytes);
+  };
+#define TRY(x)                      \
+  do {                              \
+    rc = (x);                       \
+    if (rc) {                       \
+      cleanup();                    \
+      gerbil_bins_free(b);          \
+      return rc;                    \
+    }                               \
+  } while (0)
+#define TRYCU(call)                                                                       \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess) TRY(fail(ctx, GERBIL_E_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_))); \
+  } while (0)
+
+  const uint8_t* seq = reads->seq;
+  const uint64_t* offsets = reads->offsets;
+  if (!reads->on_device && nreads > 0) {
+    seq_bytes = n + 16;
+    off_bytes = (nreads + 1) * 8;
+    TRY(dev_alloc(ctx, (void**)&dseq, seq_bytes));
+    TRY(dev_alloc(ctx, (void**)&doff, off_bytes));
+    if (n) TRYCU(cudaMemcpyAsync(dseq, reads->seq, n, cudaMemcpyHostToDevice, st));
+    TRYCU(cudaMemcpyAsync(doff, reads->offsets, off_bytes, cudaMemcpyHostToDevice, st));
+    seq = dseq;
+    offsets = doff;
+  }
+
+  b->packed_bytes = (b->nwords + 2) * 8;
+  mask_bytes = (b->nwords + 2) * 4;
+  TRY(dev_alloc(ctx, (void**)&b->packed, b->packed_bytes));
+  TRY(dev_alloc(ctx, (void**)&nmask, mask_bytes));
+  TRY(dev_alloc(ctx, (void**)&bmask, mask_bytes));
+  binbuf_bytes = (size_t)nbins * 4 * 8 + 16;  // + error word
+  TRY(dev_alloc(ctx, (void**)&binbuf, binbuf_bytes));
+  TRYCU(cudaMemsetAsync(binbuf, 0, binbuf_bytes, st));
+  TRYCU(cudaMemsetAsync(b->packed + b->nwords, 0, 16, st));
+  TRYCU(cudaMemsetAsync(nmask + b->nwords, 0xFF, 8, st));
+  TRYCU(cudaMemsetAsync(bmask, 0, mask_bytes, st));
+  if (opts.bin_bounds && nbins > 1) {
+    bounds_bytes = (size_t)(nbins - 1) * 4;
+    TRY(dev_alloc(ctx, (void**)&dbounds, bounds_bytes));
+    TRYCU(cudaMemcpyAsync(dbounds, opts.bin_bounds, bounds_bytes, cudaMemcpyHostToDevice, st));
+  }
+
+  const int vec_ok = ((uintptr_t)seq & 15) == 0;
+  ctx->times.calls++;
+  ph_begin(ctx, PH_ENCODE);
+  TRYCU(gerbil::launch_encode(seq, n, b->packed, nmask, b->nwords, vec_ok, ctx->nsm, st));
+  ctx->times.kernel_launches++;
+  unsigned int* perr = (unsigned int*)(binbuf + 4 * (size_t)nbins);
+  if (nreads > 0) {
+    TRYCU(gerbil::launch_boundary(offsets, nreads, n, bmask, perr, st));
+    ctx->times.kernel_launches++;
+  }
+  ph_end(ctx, PH_ENCODE);
+
+  gerbil::SupermerParams sp{};
+  sp.packed = b->packed;
+  sp.nmask = nmask;
+  sp.bmask = bmask;
+  sp.n = n;
+  sp.nwords = b->nwords;
+  sp.nwin = (n >= (uint64_t)k) ? n - k + 1 : 0;
+  sp.k = k;
+  sp.m = m;
+  sp.ordering = opts.ordering;
+  sp.canon_min = b->canon_min;
+  sp.lmax = opts.supermer_cap;
+  sp.nbins = (uint32_t)nbins;
+  sp.bounds = dbounds;
+  sp.tile = 2048;
+  sp.bin_nsuper = binbuf;
+  sp.bin_nkmers = binbuf + nbins;
+  sp.bin_cursor = binbuf + 2 * nbins;
+  sp.bin_sm_begin = binbuf + 3 * nbins;
+  sp.err = perr;
+  ph_begin(ctx, PH_SUPER0);
+  TRYCU(gerbil::launch_supermer(sp, 0, st));
+  if (sp.nwin) ctx->times.kernel_launches++;
+  ph_end(ctx, PH_SUPER0);
+
+  hbin.resize((size_t)nbins * 2);
+  TRYCU(cudaMemcpyAsync(hbin.data(), binbuf, (size_t)nbins * 16, cudaMemcpyDeviceToHost, st));
+  TRYCU(cudaMemcpyAsync(ctx->hctr, perr, 4, cudaMemcpyDeviceToHost, st));
+  TRYCU(cudaStreamSynchronize(st));
+  ph_collect(ctx, false);
+  if (*(unsigned int*)ctx->hctr) TRY(fail(ctx, GERBIL_E_INVAL, "offsets out of order or past the input"));
+  uint64_t acc = 0;
+  for (int i = 0; i < nbins; ++i) {
+    b->nsuper[i] = hbin[i];
+    b->nkmers[i] = hbin[nbins + i];
+    if (b->nkmers[i] >= (1ull << 32)) TRY(fail(ctx, GERBIL_E_INVAL, "a bin holds 2^32 or more k-mers"));
+    b->sm_begin[i] = acc;
+    acc += b->nsuper[i];
+    b->n_kmers_total += b->nkmers[i];
+  }
+  b->sm_begin[nbins] = acc;
+  b->n_super_total = acc;
+  b->sm_bytes = acc * 12 + 16;
+  TRY(dev_alloc(ctx, (void**)&b->sm_pos, acc * 8 + 8));
+  TRY(dev_alloc(ctx, (void**)&b->sm_koff, acc * 4 + 8));
+  {
+    std::vector<unsigned long long> beg(b->sm_begin.begin(), b->sm_begin.end() - 1);
+    TRYCU(cudaMemcpyAsync(binbuf + 3 * nbins, beg.data(), (size_t)nbins * 8, cudaMemcpyHostToDevice, st));
+    TRYCU(cudaStreamSynchronize(st));  // beg lives on this stack frame
+  }
+  sp.sm_pos = b->sm_pos;
+  sp.sm_koff = b->sm_koff;
+  ph_begin(ctx, PH_SUPER1);
+  TRYCU(gerbil::launch_supermer(sp, 1, st));
+  if (sp.nwin) ctx->times.kernel_launches++;
+  ph_end(ctx, PH_SUPER1);
+  TRYCU(cudaMemcpyAsync(ctx->hctr, perr, 4, cudaMemcpyDeviceToHost, st));
+  TRYCU(cudaStreamSynchronize(st));
+  if (*(unsigned int*)ctx->hctr) TRY(fail(ctx, GERBIL_E_STATE, "phase-one passes disagree"));
+  cleanup();
+  *out = b;
+  return GERBIL_OK;
+#undef TRY
+#undef TRYCU
+}
+
+int gerbil_bins_info(const gerbil_bins* b, int* k, int* m, int* nbins, uint64_t* ns, uint64_t* nk) {
+  if (!b) return GERBIL_E_INVAL;
+  if (k) *k = b->k;
+  if (m) *m = b->m;
+  if (nbins) *nbins = b->nbins;
+  if (ns) *ns = b->n_super_total;
+  if (nk) *nk = b->n_kmers_total;
+  return GERBIL_OK;
+}
+
+int gerbil_bin_stats(const gerbil_bins* b, int bin, uint64_t* ns, uint64_t* nbases, uint64_t* nk) {
+  if (!b || bin < 0 || bin >= b->nbins) return GERBIL_E_INVAL;
+  if (ns) *ns = b->nsuper[bin];
+  if (nk) *nk = b->nkmers[bin];
+  if (nbases) *nbases = b->nkmers[bin] + b->nsuper[bin] * (uint64_t)(b->k - 1);
+  return GERBIL_OK;
+}
+
+int gerbil_bins_export(const gerbil_bins* b, uint64_t* pos, uint32_t* nkmers, uint32_t* bin,
+                       uint64_t cap) {
+  if (!b || (b->n_super_total && (!pos || !nkmers || !bin))) return GERBIL_E_INVAL;
+  if (cap < b->n_super_total) return GERBIL_E_INVAL;
+  gerbil_ctx* ctx = b->ctx;
+  CK(cudaSetDevice(ctx->device));
+  const uint64_t S = b->n_super_total;
+  if (S == 0) return GERBIL_OK;
+  std::vector<uint32_t> koff(S);
+  CK(cudaMemcpyAsync(pos, b->sm_pos, S * 8, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaMemcpyAsync(koff.data(), b->sm_koff, S * 4, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  for (int i = 0; i < b->nbins; ++i) {
+    const uint64_t lo = b->sm_begin[i], hi = b->sm_begin[i + 1];
+    for (uint64_t s = lo; s < hi; ++s) {
+      const uint64_t next = (s + 1 < hi) ? koff[s + 1] : b->nkmers[i];
+      nkmers[s] = (uint32_t)(next - koff[s]);
+      bin[s] = (uint32_t)i;
+    }
+  }
+  return GERBIL_OK;
+}
+
+void gerbil_bins_free(gerbil_bins* b) {
+  if (!b) return;
+  gerbil_ctx* ctx = b->ctx;
+  cudaSetDevice(ctx->device);
+  dev_free(ctx, b->packed, b->packed_bytes);
+  dev_free(ctx, b->sm_pos, b->n_super_total * 8 + 8);
+  dev_free(ctx, b->sm_koff, b->n_super_total * 4 + 8);
+  delete b;
+}
+
+// ---- phase two ---------------------------------------------------------------------------------
+static int count_impl(gerbil_ctx* ctx, const gerbil_bins* b, const std::vector<int32_t>& list,
+                      int k, uint32_t min_count, const gerbil_opts& opts, gerbil_counts** out) {
+  const int W = words_for(k);
+  cudaStream_t st = ctx->stream;
+  const double alpha = (opts.load_factor > 0.05f && opts.load_factor <= 0.95f) ? opts.load_factor : 0.5;
+  double ratio = opts.distinct_ratio > 0.0f ? std::min(1.0, (double)opts.distinct_ratio)
+                                            : std::min(1.0, ctx->ratio_known ? ctx->ratio * 1.25 : 1.0);
+  uint32_t theta = opts.max_probes ? opts.max_probes : 64;
+  const uint32_t spin_limit = 1u << 20;
+
+  uint64_t occ = 0;
+  for (int32_t bi : list) occ += b->nkmers[bi];
+
+  gerbil_count_stats stats{};
+  stats.bins = (uint32_t)list.size();
+  stats.occurrences = occ;
+
+  for (int round = 0; round < 4; ++round) {
+    // table sizing per bin (Sec. 3.4: expected distinct = ratio x k-mers of the file)
+    std::vector<BinWork> work;
+    work.reserve(list.size());
+    uint64_t slots = 0, tiles = 0;
+    for (int32_t bi : list) {
+      if (b->nkmers[bi] == 0) continue;
+      BinWork w{};
+      w.sm_begin = b->sm_begin[bi];
+      w.n_super = (uint32_t)b->nsuper[bi];
+      w.n_kmers = (uint32_t)b->nkmers[bi];
+      const double est = std::max(1.0, std::ceil(ratio * (double)w.n_kmers));
+      uint64_t cap = (uint64_t)std::ceil(est / alpha) + 16;
+      cap = std::min<uint64_t>(cap, 0xFFFFFFF0ull);
+      w.cap = (uint32_t)cap;
+      w.table_off = slots;
+      w.tile_begin = (uint32_t)tiles;
+      slots += cap;
+      tiles += (w.n_kmers + gerbil::COUNT_TILE - 1) / gerbil::COUNT_TILE;
+      work.push_back(w);
+    }
+    if (tiles >= (1ull << 32)) return fail(ctx, GERBIL_E_INVAL, "too many tiles");
+    const uint64_t ovf_cap = opts.overflow_slots ? opts.overflow_slots
+                                                 : std::max<uint64_t>(1 << 16, occ / 32) << round;
+    const size_t arena_need = slots * (W + 1) * 8;
+    int rc;
+    if ((rc = scratch(ctx, &ctx->arena, &ctx->arena_bytes, arena_need + 256))) return rc;
+    if ((rc = scratch(ctx, &ctx->ovf, &ctx->ovf_bytes, ovf_cap * W * 8 + 256))) return rc;
+    const size_t work_bytes = work.size() * sizeof(BinWork);
+    const size_t small_need = work_bytes + work.size() * 4 + 512;
+    if ((rc = scratch(ctx, &ctx->small, &ctx->small_bytes, small_need))) return rc;
+    BinWork* dwork = (BinWork*)ctx->small;
+    uint32_t* bin_ovf = (uint32_t*)((char*)ctx->small + ((work_bytes + 255) & ~size_t(255)));
+
+    // result buffer: at most one row per live slot plus the overflow-only keys
+    const uint64_t out_cap = std::max<uint64_t>(1, std::min<uint64_t>(occ, slots + ovf_cap));
+    gerbil_counts* res = new (std::nothrow) gerbil_counts;
+    if (!res) return GERBIL_E_NOMEM;
+    res->ctx = ctx;
+    res->W = W;
+    res->bytes = out_cap * (W * 8 + 4);
+    if ((rc = dev_alloc(ctx, (void**)&res->keys, out_cap * W * 8))) { delete res; return rc; }
+    if ((rc = dev_alloc(ctx, (void**)&res->counts, out_cap * 4))) {
+      dev_free(ctx, res->keys, out_cap * W * 8);
+      delete res;
+      return rc;
+    }
+    auto drop = [&]() { gerbil_counts_free(res); };
+#define CKR(call)                                                                          \
+  do {                                                                                     \
+    cudaError_t e_ = (call);                                                               \
+    if (e_ != cudaSuccess) {                                                               \
+      drop();                                                                              \
+      return fail(ctx, GERBIL_E_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    }                                                                                      \
+  } while (0)
+
+    ctx->times.calls++;
+    ph_begin(ctx, PH_CLEAR);
+    CKR(cudaMemsetAsync(ctx->arena, 0, arena_need, st));
+    CKR(cudaMemsetAsync(ctx->ctr, 0, sizeof(Counters), st));
+    if (!work.empty()) {
+      CKR(cudaMemcpyAsync(dwork, work.data(), work_bytes, cudaMemcpyHostToDevice, st));
+      CKR(cudaMemsetAsync(bin_ovf, 0, work.size() * 4, st));
+    }
+    ph_end(ctx, PH_CLEAR);
+
+    gerbil::CountParams cp{};
+    cp.packed = b->packed;
+    cp.sm_pos = b->sm_pos;
+    cp.sm_koff = b->sm_koff;
+    cp.work = dwork;
+    cp.nwork = (uint32_t)work.size();
+    cp.ntiles = (uint32_t)tiles;
+    cp.tile_base = 0;
+    cp.k = k;
+    cp.canonical = opts.canonical ? 1 : 0;
+    cp.theta = theta;
+    cp.spin_limit = spin_limit;
+    cp.arena = (unsigned long long*)ctx->arena;
+    cp.ovf = (unsigned long long*)ctx->ovf;
+    cp.ovf_cap = ovf_cap;
+    cp.bin_ovf = bin_ovf;
+    cp.ctr = ctx->ctr;
+    ph_begin(ctx, PH_INSERT);
+    if (tiles) {
+      ctx->times.kernel_launches++;
+      ctx->times.insert_launches++;
+      if (opts.persistent) {
+        const unsigned grid = (unsigned)std::min<uint64_t>(tiles, (uint64_t)ctx->nsm * ctx->insert_ctas_per_sm);
+        CKR(gerbil::launch_insert_persistent(W, cp, grid, st));
+      } else {
+        CKR(gerbil::launch_insert(W, cp, (unsigned)tiles, st));
+      }
+    }
+    ph_end(ctx, PH_INSERT);
+    gerbil::CompactParams xp{};
+    xp.work = dwork;
+    xp.nwork = (uint32_t)work.size();
+    xp.slot_lo = 0;
+    xp.slot_hi = slots;
+    xp.arena = (unsigned long long*)ctx->arena;
+    xp.bin_ovf = bin_ovf;
+    xp.mode = 0;
+    xp.min_count = min_count;
+    xp.out_keys = res->keys;
+    xp.out_counts = res->counts;
+    xp.out_cap = out_cap;
+    xp.ctr = ctx->ctr;
+    ph_begin(ctx, PH_COMPACT);
+    CKR(gerbil::launch_compact(W, xp, ctx->nsm, st));
+    if (slots) ctx->times.kernel_launches++;
+    ph_end(ctx, PH_COMPACT);
+    if ((rc = read_counters(ctx))) { drop(); return rc; }
+    Counters h = *ctx->hctr;
+    if (h.err & gerbil::ERR_OVF_FULL) {
+      // the emergency area ran full: repeat with twice the table size estimate
+      drop();
+      ratio = std::min(1.0, ratio * 2.0);
+      theta = std::max<uint32_t>(theta, 128);
+      stats.retries++;
+      continue;
+    }
+    stats.overflowed = h.ovf_count;
+    if (h.ovf_count) {
+      // recount the overflow area in a fresh table, merge it into the deferred bins' keys and
+      // emit the keys that exist only in the overflow table
+      const uint64_t ocap64 = std::max<uint64_t>(64, 2 * h.ovf_count + 16);
+      if (ocap64 >= 0xFFFFFFF0ull) { drop(); return fail(ctx, GERBIL_E_OVERFLOW, "overflow too large"); }
+      const uint32_t ocap = (uint32_t)ocap64;
+      void* otab = nullptr;
+      const size_t obytes = (size_t)ocap * (W + 1) * 8;
+      if ((rc = dev_alloc(ctx, &otab, obytes))) { drop(); return rc; }
+      CKR(cudaMemsetAsync(otab, 0, obytes, st));
+      gerbil::OverflowParams op{};
+      op.ovf = (unsigned long long*)ctx->ovf;
+      op.ovf_cap = ovf_cap;
+      op.otab = (unsigned long long*)otab;
+      op.ocap = ocap;
+      op.spin_limit = spin_limit;
+      op.min_count = min_count;
+      op.out_keys = res->keys;
+      op.out_counts = res->counts;
+      op.out_cap = out_cap;
+      op.ctr = ctx->ctr;
+      ph_begin(ctx, PH_OVERFLOW);
+      CKR(gerbil::launch_overflow_insert(W, op, ctx->nsm, st));
+      xp.mode = 1;
+      xp.otab = op.otab;
+      xp.ocap = ocap;
+      CKR(gerbil::launch_compact(W, xp, ctx->nsm, st));
+      CKR(gerbil::launch_overflow_emit(W, op, ctx->nsm, st));
+      ctx->times.kernel_launches += 3;
+      ph_end(ctx, PH_OVERFLOW);
+      rc = read_counters(ctx);
+      dev_free(ctx, otab, obytes);
+      if (rc) { drop(); return rc; }
+      h = *ctx->hctr;
+      // distinct counted in mode 0 skipped deferred bins; add their main-table keys
+      // (overflow emit counted the overflow-only ones)
+    }
+    if (h.err & gerbil::ERR_SPIN) { drop(); return fail(ctx, GERBIL_E_TIMEOUT, "bounded wait gave up"); }
+    if (h.err & (gerbil::ERR_STATE | gerbil::ERR_OUT_FULL)) {
+      drop();
+      return fail(ctx, GERBIL_E_STATE, "device consistency check failed");
+    }
+    stats.emitted = h.out_count;
+    stats.distinct = h.distinct;
+    stats.table_slots = slots;
+    res->n = h.out_count;
+    res->stats = stats;
+    if (occ > 0 && stats.overflowed == 0) {
+      ctx->ratio = (double)h.distinct / (double)occ;
+      ctx->ratio_known = true;
+    }
+    *out = res;
+    return GERBIL_OK;
+#undef CKR
+  }
+  return fail(ctx, GERBIL_E_OVERFLOW, "overflow area full after all retries");
+}
+
+static int count_checks(gerbil_ctx* ctx, const gerbil_bins* b, int k, uint32_t min_count,
+                        const gerbil_opts& opts) {
+  if (!b || b->ctx != ctx) return fail(ctx, GERBIL_E_INVAL, "bins from another context");
+  if (k != b->k) return fail(ctx, GERBIL_E_INVAL, "k differs from the partition's k");
+  if (min_count < 1) return fail(ctx, GERBIL_E_INVAL, "min_count must be >= 1");
+  if (opts.canonical && !b->canon_min)
+    return fail(ctx, GERBIL_E_INVAL, "canonical counting needs canonical minimizers");
+  return GERBIL_OK;
+}
+
+int gerbil_count(gerbil_ctx* ctx, const gerbil_bins* b, int bin, int k, uint32_t min_count,
+                 const gerbil_opts* opts_in, gerbil_counts** out) {
+  if (!ctx || !out) return GERBIL_E_INVAL;
+  *out = nullptr;
+  gerbil_opts opts;
+  if (opts_in) opts = *opts_in; else gerbil_opts_default(&opts);
+  int rc = count_checks(ctx, b, k, min_count, opts);
+  if (rc) return rc;
+  if (bin < 0 || bin >= b->nbins) return fail(ctx, GERBIL_E_INVAL, "bin out of range");
+  CK(cudaSetDevice(ctx->device));
+  std::vector<int32_t> list(1, bin);
+  return count_impl(ctx, b, list, k, min_count, opts, out);
+}
+
+int gerbil_count_batch(gerbil_ctx* ctx, const gerbil_bins* b, const int32_t* bin_list, int nb,
+                       int k, uint32_t min_count, const gerbil_opts* opts_in,
+                       gerbil_counts** out) {
+  if (!ctx || !out) return GERBIL_E_INVAL;
+  *out = nullptr;
+  gerbil_opts opts;
+  if (opts_in) opts = *opts_in; else gerbil_opts_default(&opts);
+  int rc = count_checks(ctx, b, k, min_count, opts);
+  if (rc) return rc;
+  std::vector<int32_t> list;
+  if (bin_list) {
+    if (nb < 0) return fail(ctx, GERBIL_E_INVAL, "nb < 0");
+    std::vector<char> seen(b->nbins, 0);
+    for (int i = 0; i < nb; ++i) {
+      const int32_t x = bin_list[i];
+      if (x < 0 || x >= b->nbins || seen[x]) return fail(ctx, GERBIL_E_INVAL, "bad bin list");
+      seen[x] = 1;
+      list.push_back(x);
+    }
+  } else {
+    for (int i = 0; i < b->nbins; ++i) list.push_back(i);
+  }
+  CK(cudaSetDevice(ctx->device));
+  return count_impl(ctx, b, list, k, min_count, opts, out);
+}
+
+int gerbil_counts_info(const gerbil_counts* c, uint64_t* n, int* words, gerbil_count_stats* s) {
+  if (!c) return GERBIL_E_INVAL;
+  if (n) *n = c->n;
+  if (words) *words = c->W;
+  if (s) *s = c->stats;
+  return GERBIL_OK;
+}
+
+int gerbil_counts_view(const gerbil_counts* c, const uint64_t** keys, const uint32_t** counts) {
+  if (!c) return GERBIL_E_INVAL;
+  if (keys) *keys = (const uint64_t*)c->keys;
+  if (counts) *counts = c->counts;
+  return GERBIL_OK;
+}
+
+int gerbil_counts_to_host(const gerbil_counts* c, uint64_t* keys, uint32_t* counts, uint64_t cap) {
+  if (!c) return GERBIL_E_INVAL;
+  gerbil_ctx* ctx = c->ctx;
+  if (cap < c->n || (c->n && (!keys || !counts))) return fail(ctx, GERBIL_E_INVAL, "cap < n");
+  if (c->n == 0) return GERBIL_OK;
+  CK(cudaSetDevice(ctx->device));
+  CK(cudaMemcpyAsync(keys, c->keys, c->n * c->W * 8, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaMemcpyAsync(counts, c->counts, c->n * 4, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return GERBIL_OK;
+}
+
+void gerbil_counts_free(gerbil_counts* c) {
+  if (!c) return;
+  gerbil_ctx* ctx = c->ctx;
+  cudaSetDevice(ctx->device);
+  const uint64_t cap = c->bytes / (c->W * 8 + 4);
+  dev_free(ctx, c->keys, cap * c->W * 8);
+  dev_free(ctx, c->counts, cap * 4);
+  delete c;
+}
+
+}  // extern "C"

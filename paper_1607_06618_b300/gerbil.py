@@ -1,0 +1,382 @@
+"""Thin ctypes binding of ``libgerbil.so`` (include/gerbil.h) -- argument marshalling only.
+
+Every step of the path runs in the CUDA library; this module passes pointers and sizes.
+Device memory and streams come from PyTorch (``tensor.data_ptr()``,
+``torch.cuda.current_stream().cuda_stream``).  There is no CPU fallback: if the library is
+missing or no CUDA device is usable, calls raise ``GerbilError``.
+
+The module-level functions carry the C-ABI's names; ``Context``/``Bins``/``Counts`` wrap the
+handles for convenient lifetime management.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgerbil.so")
+
+GERBIL_OK = 0
+GERBIL_E_INVAL = 1
+GERBIL_E_UNSUPPORTED = 2
+GERBIL_E_NOMEM = 3
+GERBIL_E_OVERFLOW = 4
+GERBIL_E_TIMEOUT = 5
+GERBIL_E_CUDA = 6
+GERBIL_E_STATE = 7
+GERBIL_ORDER_KMC2 = 0
+GERBIL_ORDER_LEX = 1
+
+# every symbol the header declares (checked by tests/test_abi.py)
+ABI_SYMBOLS = (
+    "gerbil_opts_default", "gerbil_strerror", "gerbil_last_error", "gerbil_create",
+    "gerbil_destroy", "gerbil_partition", "gerbil_bins_info", "gerbil_bin_stats",
+    "gerbil_bins_export", "gerbil_bins_free", "gerbil_count", "gerbil_count_batch",
+    "gerbil_counts_info", "gerbil_counts_view", "gerbil_counts_to_host", "gerbil_counts_free",
+    "gerbil_profile", "gerbil_get_phase_times",
+)
+
+
+class GerbilError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(msg)
+        self.status = status
+
+
+class gerbil_reads(ctypes.Structure):
+    _fields_ = [("seq", ctypes.c_void_p), ("offsets", ctypes.c_void_p),
+                ("nreads", ctypes.c_uint64), ("on_device", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class gerbil_opts(ctypes.Structure):
+    _fields_ = [("canonical", ctypes.c_int32), ("ordering", ctypes.c_int32),
+                ("canonical_minimizer", ctypes.c_int32), ("supermer_cap", ctypes.c_uint32),
+                ("bin_bounds", ctypes.c_void_p), ("max_probes", ctypes.c_uint32),
+                ("load_factor", ctypes.c_float), ("distinct_ratio", ctypes.c_float),
+                ("overflow_slots", ctypes.c_uint32), ("persistent", ctypes.c_int32),
+                ("reserved", ctypes.c_uint32 * 6)]
+
+
+class gerbil_count_stats(ctypes.Structure):
+    _fields_ = [("occurrences", ctypes.c_uint64), ("distinct", ctypes.c_uint64),
+                ("emitted", ctypes.c_uint64), ("overflowed", ctypes.c_uint64),
+                ("table_slots", ctypes.c_uint64), ("retries", ctypes.c_uint32),
+                ("bins", ctypes.c_uint32)]
+
+    def as_dict(self):
+        return {name: int(getattr(self, name)) for name, _ in self._fields_}
+
+
+class gerbil_phase_times(ctypes.Structure):
+    _fields_ = [("encode_ms", ctypes.c_double), ("supermer_ms", ctypes.c_double),
+                ("clear_ms", ctypes.c_double), ("insert_ms", ctypes.c_double),
+                ("compact_ms", ctypes.c_double), ("overflow_ms", ctypes.c_double),
+                ("insert_launches", ctypes.c_uint64), ("kernel_launches", ctypes.c_uint64),
+                ("calls", ctypes.c_uint64)]
+
+    def as_dict(self):
+        return {name: (float if t is ctypes.c_double else int)(getattr(self, name))
+                for name, t in self._fields_}
+
+
+_lib = None
+
+
+def load() -> ctypes.CDLL:
+    """Load the in-tree CUDA library (built by ``build.build()``); raise if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise GerbilError(GERBIL_E_CUDA, "libgerbil.so is not built (run __graft_entry__.build())")
+    lib = ctypes.CDLL(LIB_PATH)
+    P, U64, U32, I32 = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int
+    PP = ctypes.POINTER(ctypes.c_void_p)
+    sig = {
+        "gerbil_opts_default": (None, [ctypes.POINTER(gerbil_opts)]),
+        "gerbil_strerror": (ctypes.c_char_p, [I32]),
+        "gerbil_last_error": (ctypes.c_char_p, [P]),
+        "gerbil_create": (I32, [PP, I32, U64, P]),
+        "gerbil_destroy": (None, [P]),
+        "gerbil_partition": (I32, [P, ctypes.POINTER(gerbil_reads), I32, I32, I32,
+                                   ctypes.POINTER(gerbil_opts), PP]),
+        "gerbil_bins_info": (I32, [P, ctypes.POINTER(I32), ctypes.POINTER(I32),
+                                   ctypes.POINTER(I32), ctypes.POINTER(U64), ctypes.POINTER(U64)]),
+        "gerbil_bin_stats": (I32, [P, I32, ctypes.POINTER(U64), ctypes.POINTER(U64),
+                                   ctypes.POINTER(U64)]),
+        "gerbil_bins_export": (I32, [P, P, P, P, U64]),
+        "gerbil_bins_free": (None, [P]),
+        "gerbil_count": (I32, [P, P, I32, I32, U32, ctypes.POINTER(gerbil_opts), PP]),
+        "gerbil_count_batch": (I32, [P, P, P, I32, I32, U32, ctypes.POINTER(gerbil_opts), PP]),
+        "gerbil_counts_info": (I32, [P, ctypes.POINTER(U64), ctypes.POINTER(I32),
+                                     ctypes.POINTER(gerbil_count_stats)]),
+        "gerbil_counts_view": (I32, [P, PP, PP]),
+        "gerbil_counts_to_host": (I32, [P, P, P, U64]),
+        "gerbil_counts_free": (None, [P]),
+        "gerbil_profile": (I32, [P, I32]),
+        "gerbil_get_phase_times": (I32, [P, ctypes.POINTER(gerbil_phase_times)]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(status: int, ctx=None):
+    if status != GERBIL_OK:
+        lib = load()
+        msg = lib.gerbil_strerror(status).decode()
+        if ctx:
+            detail = lib.gerbil_last_error(ctx).decode()
+            if detail:
+                msg += ": " + detail
+        raise GerbilError(status, msg)
+
+
+def default_opts(**kw) -> gerbil_opts:
+    o = gerbil_opts()
+    load().gerbil_opts_default(ctypes.byref(o))
+    for key, val in kw.items():
+        if key == "bin_bounds":
+            continue
+        setattr(o, key, val)
+    return o
+
+
+# ---- C-ABI names ------------------------------------------------------------------------
+def gerbil_create(device: int = 0, hbm_budget_bytes: int = 0, cuda_stream: int | None = None):
+    h = ctypes.c_void_p()
+    _check(load().gerbil_create(ctypes.byref(h), device, hbm_budget_bytes, cuda_stream))
+    return h
+
+
+def gerbil_destroy(ctx):
+    load().gerbil_destroy(ctx)
+
+
+def gerbil_profile(ctx, enable: bool):
+    _check(load().gerbil_profile(ctx, 1 if enable else 0), ctx)
+
+
+def gerbil_get_phase_times(ctx):
+    t = gerbil_phase_times()
+    _check(load().gerbil_get_phase_times(ctx, ctypes.byref(t)), ctx)
+    return t.as_dict()
+
+
+def _reads_struct(seq, offsets):
+    """Marshal reads: torch CUDA tensors (device pointers) or numpy arrays (host pointers)."""
+    r = gerbil_reads()
+    keep = (seq, offsets)
+    if hasattr(seq, "data_ptr"):
+        r.seq, r.offsets, r.on_device = seq.data_ptr(), offsets.data_ptr(), 1 if seq.is_cuda else 0
+        r.nreads = offsets.numel() - 1
+    else:
+        seq = np.ascontiguousarray(seq, dtype=np.uint8)
+        offsets = np.ascontiguousarray(offsets, dtype=np.uint64)
+        keep = (seq, offsets)
+        r.seq, r.offsets, r.on_device = seq.ctypes.data, offsets.ctypes.data, 0
+        r.nreads = offsets.size - 1
+    return r, keep
+
+
+def gerbil_partition(ctx, seq, offsets, k: int, m: int, nbins: int, opts: gerbil_opts | None = None,
+                     bin_bounds=None):
+    r, keep = _reads_struct(seq, offsets)
+    o = opts if opts is not None else default_opts()
+    bb = None
+    if bin_bounds is not None:
+        bb = np.ascontiguousarray(bin_bounds, dtype=np.uint32)
+        o.bin_bounds = bb.ctypes.data
+    h = ctypes.c_void_p()
+    st = load().gerbil_partition(ctx, ctypes.byref(r), k, m, nbins, ctypes.byref(o), ctypes.byref(h))
+    o.bin_bounds = None
+    del keep, bb
+    _check(st, ctx)
+    return h
+
+
+def gerbil_bins_info(bins):
+    k, m, nb = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    ns, nk = ctypes.c_uint64(), ctypes.c_uint64()
+    _check(load().gerbil_bins_info(bins, ctypes.byref(k), ctypes.byref(m), ctypes.byref(nb),
+                                   ctypes.byref(ns), ctypes.byref(nk)))
+    return {"k": k.value, "m": m.value, "nbins": nb.value, "n_supermers": ns.value,
+            "n_kmers": nk.value}
+
+
+def gerbil_bin_stats(bins, b: int):
+    ns, nbases, nk = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
+    _check(load().gerbil_bin_stats(bins, b, ctypes.byref(ns), ctypes.byref(nbases), ctypes.byref(nk)))
+    return ns.value, nbases.value, nk.value
+
+
+def gerbil_bins_export(bins):
+    n = gerbil_bins_info(bins)["n_supermers"]
+    pos = np.zeros(max(n, 1), np.uint64)
+    nk = np.zeros(max(n, 1), np.uint32)
+    b = np.zeros(max(n, 1), np.uint32)
+    _check(load().gerbil_bins_export(bins, pos.ctypes.data, nk.ctypes.data, b.ctypes.data, pos.size))
+    return {"pos": pos[:n], "nkmers": nk[:n], "bin": b[:n]}
+
+
+def gerbil_bins_free(bins):
+    load().gerbil_bins_free(bins)
+
+
+def gerbil_count(ctx, bins, b: int, k: int, min_count: int, opts: gerbil_opts | None = None):
+    o = opts if opts is not None else default_opts()
+    h = ctypes.c_void_p()
+    _check(load().gerbil_count(ctx, bins, b, k, min_count, ctypes.byref(o), ctypes.byref(h)), ctx)
+    return h
+
+
+def gerbil_count_batch(ctx, bins, bin_list, k: int, min_count: int, opts: gerbil_opts | None = None):
+    o = opts if opts is not None else default_opts()
+    h = ctypes.c_void_p()
+    if bin_list is None:
+        st = load().gerbil_count_batch(ctx, bins, None, 0, k, min_count, ctypes.byref(o), ctypes.byref(h))
+    else:
+        arr = np.ascontiguousarray(bin_list, dtype=np.int32)
+        st = load().gerbil_count_batch(ctx, bins, arr.ctypes.data, arr.size, k, min_count,
+                                       ctypes.byref(o), ctypes.byref(h))
+    _check(st, ctx)
+    return h
+
+
+def gerbil_counts_info(counts):
+    n, w = ctypes.c_uint64(), ctypes.c_int()
+    s = gerbil_count_stats()
+    _check(load().gerbil_counts_info(counts, ctypes.byref(n), ctypes.byref(w), ctypes.byref(s)))
+    return n.value, w.value, s.as_dict()
+
+
+def gerbil_counts_view(counts):
+    kp, cp = ctypes.c_void_p(), ctypes.c_void_p()
+    _check(load().gerbil_counts_view(counts, ctypes.byref(kp), ctypes.byref(cp)))
+    return kp.value or 0, cp.value or 0
+
+
+def gerbil_counts_to_host(counts, keys_out=None, counts_out=None):
+    n, W, _ = gerbil_counts_info(counts)
+    keys = keys_out if keys_out is not None else np.zeros((max(n, 1), W), np.uint64)
+    cnt = counts_out if counts_out is not None else np.zeros(max(n, 1), np.uint32)
+    _check(load().gerbil_counts_to_host(counts, keys.ctypes.data, cnt.ctypes.data, min(len(cnt), len(keys))))
+    return keys[:n], cnt[:n]
+
+
+def gerbil_counts_free(counts):
+    load().gerbil_counts_free(counts)
+
+
+# ---- handle wrappers ----------------------------------------------------------------------
+class _DeviceArray:
+    """Exposes a device pointer to torch through __cuda_array_interface__ (no copy)."""
+
+    def __init__(self, ptr: int, shape, typestr: str, owner):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr,
+                                         "data": (ptr, False), "version": 2, "strides": None}
+        self._owner = owner
+
+
+class Counts:
+    def __init__(self, handle, ctx):
+        self.handle, self.ctx = handle, ctx
+
+    def info(self):
+        return gerbil_counts_info(self.handle)
+
+    def __len__(self):
+        return self.info()[0]
+
+    def to_host(self):
+        return gerbil_counts_to_host(self.handle)
+
+    def torch_views(self):
+        """(keys int64[n, W], counts int32[n]) torch views of the device result (no copy)."""
+        import torch
+        n, W, _ = self.info()
+        kp, cp = gerbil_counts_view(self.handle)
+        if n == 0:
+            dev = torch.device("cuda", self.ctx.device)
+            return (torch.zeros((0, W), dtype=torch.int64, device=dev),
+                    torch.zeros(0, dtype=torch.int32, device=dev))
+        keys = torch.as_tensor(_DeviceArray(kp, (n, W), "<i8", self), device="cuda")
+        cnts = torch.as_tensor(_DeviceArray(cp, (n,), "<i4", self), device="cuda")
+        return keys, cnts
+
+    def free(self):
+        if self.handle:
+            gerbil_counts_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+class Bins:
+    def __init__(self, handle, ctx):
+        self.handle, self.ctx = handle, ctx
+
+    def info(self):
+        return gerbil_bins_info(self.handle)
+
+    def stats(self, b: int):
+        return gerbil_bin_stats(self.handle, b)
+
+    def export(self):
+        return gerbil_bins_export(self.handle)
+
+    def free(self):
+        if self.handle:
+            gerbil_bins_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+class Context:
+    def __init__(self, device: int = 0, hbm_budget_bytes: int = 0, stream=None):
+        if stream is None:
+            import torch
+            stream = torch.cuda.current_stream(device).cuda_stream
+        self.device = device
+        self.handle = gerbil_create(device, hbm_budget_bytes, stream)
+
+    def partition(self, seq, offsets, k, m, nbins, opts=None, bin_bounds=None) -> Bins:
+        return Bins(gerbil_partition(self.handle, seq, offsets, k, m, nbins, opts, bin_bounds), self)
+
+    def count(self, bins: Bins, b: int, k: int, min_count: int, opts=None) -> Counts:
+        return Counts(gerbil_count(self.handle, bins.handle, b, k, min_count, opts), self)
+
+    def count_batch(self, bins: Bins, bin_list, k: int, min_count: int, opts=None) -> Counts:
+        return Counts(gerbil_count_batch(self.handle, bins.handle, bin_list, k, min_count, opts), self)
+
+    def profile(self, enable: bool = True):
+        gerbil_profile(self.handle, enable)
+
+    def phase_times(self):
+        return gerbil_get_phase_times(self.handle)
+
+    def close(self):
+        if self.handle:
+            gerbil_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

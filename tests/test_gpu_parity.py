@@ -1,0 +1,235 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle -- needs a B300.
+
+Counts are integers, so every comparison is bit-exact: same set of keys, same counts.  Bins
+are compared as sets of (global start, k-mers, bin) rows, since their order within a bin is
+free.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1607_06618_b300 import synth
+from tests._util import (assert_same_rows, fnv1a64_rows, keys_to_ascii, reads_from_strings,
+                         revcomp_reads, sort_rows)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def g():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_1607_06618_b300 import gerbil
+    ctx = gerbil.Context(0)
+    yield gerbil, ctx, torch
+    ctx.close()
+
+
+def _dev(torch, seq, offs):
+    return (torch.from_numpy(np.ascontiguousarray(seq)).cuda(),
+            torch.from_numpy(np.ascontiguousarray(offs).view(np.int64)).cuda())
+
+
+def _gpu_count(g, seq, offs, k, m, nbins, min_count, on_device=True, batch=True, **opt):
+    gerbil, ctx, torch = g
+    o = gerbil.default_opts(**opt)
+    s, of = _dev(torch, seq, offs) if on_device else (seq, offs)
+    bins = ctx.partition(s, of, k, m, nbins, o, opt.get("bin_bounds"))
+    if batch:
+        res = ctx.count_batch(bins, None, k, min_count, o)
+        keys, counts = res.to_host()
+        stats = res.info()[2]
+        res.free()
+    else:
+        ks, cs = [], []
+        stats = {"overflowed": 0}
+        for b in range(nbins):
+            r = ctx.count(bins, b, k, min_count, o)
+            kk, cc = r.to_host()
+            ks.append(kk)
+            cs.append(cc)
+            stats["overflowed"] += r.info()[2]["overflowed"]
+            r.free()
+        W = (2 * k + 63) // 64
+        keys = np.concatenate(ks) if ks else np.zeros((0, W), np.uint64)
+        counts = np.concatenate(cs) if cs else np.zeros(0, np.uint32)
+    bins.free()
+    return (keys, counts), stats
+
+
+# ---- phase one -------------------------------------------------------------------------
+
+def _gpu_bins(g, seq, offs, k, m, nbins, **opt):
+    gerbil, ctx, torch = g
+    o = gerbil.default_opts(**opt)
+    s, of = _dev(torch, seq, offs)
+    bins = ctx.partition(s, of, k, m, nbins, o, opt.get("bin_bounds"))
+    ex = bins.export()
+    info = bins.info()
+    stats = [bins.stats(b) for b in range(nbins)]
+    bins.free()
+    return ex, info, stats
+
+
+def _rows(part):
+    return sorted(zip(part["pos"].tolist(), part["nkmers"].tolist(), part["bin"].tolist()))
+
+
+@pytest.mark.parametrize("k,m,lmax,ordering", [
+    (32, 7, 256, 0), (32, 7, 7, 0), (65, 9, 256, 0), (65, 9, 1024, 1), (8, 3, 5, 1),
+    (99, 9, 64, 0), (200, 11, 256, 0), (256, 15, 300, 0), (33, 1, 256, 1)])
+def test_partition_matches_oracle(g, k, m, lmax, ordering):
+    nreads = 700 if k < 100 else 120
+    seq, offs = synth.random_small(nreads, k - 3, k + 400, p_n=0.004, seed=k * 31 + m)
+    nbins = 37
+    ex, info, stats = _gpu_bins(g, seq, offs, k, m, nbins, supermer_cap=lmax, ordering=ordering)
+    want = oracle.partition(seq, offs, k, m, nbins, ordering=ordering, lmax=lmax)
+    assert _rows(ex) == _rows(want)
+    assert info["n_kmers"] == oracle.windows(seq, offs, k)
+    for b in range(nbins):
+        sel = want["bin"] == b
+        assert stats[b][0] == int(sel.sum())
+        assert stats[b][2] == int(want["nkmers"][sel].sum())
+
+
+def test_partition_config1_full_and_bounds(g):
+    seq, offs, p = synth.workload("uniform-20k-k32")
+    bounds = np.sort(np.random.default_rng(3).integers(0, 2 ** 32, p["nbins"] - 1)).astype(np.uint32)
+    for bb in (None, bounds):
+        ex, _, _ = _gpu_bins(g, seq, offs, p["k"], p["m"], p["nbins"], bin_bounds=bb)
+        want = oracle.partition(seq, offs, p["k"], p["m"], p["nbins"], bounds=bb)
+        assert _rows(ex) == _rows(want)
+
+
+def test_partition_edge_reads(g):
+    k, m = 12, 5
+    reads = ["", "ACGT", "A" * 12, "acgtACGTacgtN", "N" * 40, "ACGTNACGTACGTACGTTT", "",
+             "GATTACA" * 9, "ACGTRYACGTACGTACGTACGT\n", "T" * 11, "C" * 13]
+    seq, offs = reads_from_strings(reads)
+    for lmax in (1, 3, 256):
+        ex, _, _ = _gpu_bins(g, seq, offs, k, m, 4, supermer_cap=lmax)
+        want = oracle.partition(seq, offs, k, m, 4, lmax=lmax)
+        assert _rows(ex) == _rows(want)
+    # forward minimizers in lexicographic order: Fig. 1's example
+    seq, offs = reads_from_strings(["CAAGAACAGTG" * 3])
+    ex, _, _ = _gpu_bins(g, seq, offs, 8, 3, 1, ordering=1, canonical_minimizer=0, canonical=0)
+    want = oracle.partition(seq, offs, 8, 3, 1, ordering=1, canonical_min=False)
+    assert _rows(ex) == _rows(want)
+
+
+# ---- phase two -------------------------------------------------------------------------
+
+@pytest.mark.parametrize("k", [8, 31, 32, 33, 63, 64, 65, 99, 127, 128, 129, 200, 256])
+def test_count_matches_oracle_all_word_counts(g, k):
+    m = min(11, k - 1)
+    seq, offs = synth.random_small(400, max(1, k - 4), k + 300, p_n=0.003, seed=1000 + k,
+                                   lowercase=(k % 2 == 1))
+    # add repeated content so that counts above 1 occur
+    seq = np.concatenate([seq, seq[: int(offs[50])]])
+    offs = np.concatenate([offs, offs[1:51] + offs[-1]])
+    for mc in (1, 2):
+        got, _ = _gpu_count(g, seq, offs, k, m, 16, mc)
+        assert_same_rows(got, oracle.count(seq, offs, k, canonical=True, min_count=mc))
+
+
+def test_count_config1_full_batch_grid_and_per_bin(g):
+    seq, offs, p = synth.workload("uniform-20k-k32")
+    want = oracle.count(seq, offs, p["k"], min_count=1)
+    assert int(want[1].sum()) == oracle.windows(seq, offs, p["k"])
+    for batch, persistent in ((True, 1), (True, 0), (False, 1)):
+        got, _ = _gpu_count(g, seq, offs, p["k"], p["m"], p["nbins"], 1, batch=batch,
+                            persistent=persistent)
+        assert_same_rows(got, want)
+
+
+def test_count_host_buffers_path(g):
+    seq, offs = synth.random_small(300, 50, 400, p_n=0.01, seed=5)
+    got, _ = _gpu_count(g, seq, offs, 41, 9, 8, 1, on_device=False)
+    assert_same_rows(got, oracle.count(seq, offs, 41))
+
+
+def test_count_noncanonical(g):
+    seq, offs = synth.random_small(300, 50, 400, p_n=0.01, seed=6)
+    for k in (21, 77):
+        got, _ = _gpu_count(g, seq, offs, k, 7, 8, 1, canonical=0)
+        assert_same_rows(got, oracle.count(seq, offs, k, canonical=False))
+
+
+def test_count_edge_cases(g):
+    k = 16
+    reads = ["", "A" * 15, "A" * 16, "A" * 200, "T" * 100, "ACGTACGTACGTACGTACGT",
+             "NNNNNNNNNNNNNNNNNNNNNNNN", "acgtacgtacgtacgtAC", "GGGGCCCC" * 10]
+    seq, offs = reads_from_strings(reads)
+    for mc in (1, 2, 3, 100):
+        got, _ = _gpu_count(g, seq, offs, k, 5, 3, mc)
+        assert_same_rows(got, oracle.count(seq, offs, k, min_count=mc))
+    # no windows at all
+    seq, offs = reads_from_strings(["ACG", "", "NNNN"])
+    got, _ = _gpu_count(g, seq, offs, k, 5, 3, 1)
+    assert got[1].size == 0
+
+
+def test_forced_overflow_recount_is_exact(g):
+    # theta = 1 and a tiny table send most k-mers to the overflow area
+    seq, offs = synth.random_small(500, 100, 300, p_n=0.002, seed=8)
+    seq = np.concatenate([seq, seq])
+    offs = np.concatenate([offs, offs[1:] + offs[-1]])
+    for k in (32, 65, 200):
+        want = oracle.count(seq, offs, k, min_count=2)
+        got, st = _gpu_count(g, seq, offs, k, 9, 4, 2, max_probes=1, distinct_ratio=0.05)
+        assert st["overflowed"] > 0
+        assert_same_rows(got, want)
+        # per-bin path with the same forcing
+        got, st = _gpu_count(g, seq, offs, k, 9, 4, 2, batch=False, max_probes=1, distinct_ratio=0.05)
+        assert st["overflowed"] > 0
+        assert_same_rows(got, want)
+
+
+def test_overflow_area_full_retries(g):
+    seq, offs = synth.random_small(200, 100, 200, p_n=0.0, seed=9)
+    got, st = _gpu_count(g, seq, offs, 33, 7, 2, 1, max_probes=1, distinct_ratio=0.01,
+                         overflow_slots=16)
+    assert_same_rows(got, oracle.count(seq, offs, 33))
+
+
+def test_invariants_on_gpu(g):
+    seq, offs = synth.random_small(800, 100, 300, p_n=0.005, seed=10)
+    base, _ = _gpu_count(g, seq, offs, 45, 9, 64, 1)
+    rc, _ = _gpu_count(g, *revcomp_reads(seq, offs), 45, 9, 64, 1)
+    assert_same_rows(rc, base)
+    for nb, m in ((1, 9), (7, 5), (1000, 11)):
+        other, _ = _gpu_count(g, seq, offs, 45, m, nb, 1)
+        assert_same_rows(other, base)
+
+
+# ---- the measured workload at full size ----------------------------------------------------
+
+@pytest.fixture(scope="module")
+def genome5m():
+    return synth.workload("genome5M-30x-k65")
+
+
+def test_genome5m_full_size_sampled_parity(g, genome5m):
+    """Full-size k=65 workload, batched persistent launch as timed by bench.py: the keys with
+    FNV-1a(key) = 0 (mod 64) must match the oracle's pass 0 of 64 exactly."""
+    seq, offs, p = genome5m
+    got, st = _gpu_count(g, seq, offs, p["k"], p["m"], p["nbins"], p["min_count"])
+    keys, counts = got
+    h = fnv1a64_rows(keys_to_ascii(keys, p["k"]))
+    sel = (h % np.uint64(64)) == np.uint64(0)
+    want = oracle.count(seq, offs, p["k"], min_count=p["min_count"], npass=64, pass_index=0)
+    assert_same_rows((keys[sel], counts[sel]), want)
+    assert st["occurrences"] == oracle.windows(seq, offs, p["k"])
+
+
+def test_genome5m_full_size_total(g, genome5m):
+    """At min_count = 1 the counts sum to the number of N-free windows (closed form)."""
+    seq, offs, p = genome5m
+    got, st = _gpu_count(g, seq, offs, p["k"], p["m"], p["nbins"], 1)
+    k = p["k"]
+    total_windows = (offs.size - 1) * (150 - k + 1)  # no N in this workload
+    assert int(got[1].astype(np.uint64).sum()) == total_windows
+    assert st["distinct"] == got[1].size
+    # each key once
+    sk, _ = sort_rows(*got)
+    assert not np.any(np.all(sk[1:] == sk[:-1], axis=1))
