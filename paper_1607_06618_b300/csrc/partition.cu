@@ -191,16 +191,52 @@ __global__ void __launch_bounds__(256) supermer_kernel(SupermerParams P) {
   }
   __syncthreads();
 
+  // super-mer starts and boundaries as bit masks (one ballot per 32 windows): window i starts
+  // a super-mer if it is counted and its predecessor is not, or has another minimizer, or i
+  // sits on a multiple of L_max; a boundary is a start or an uncounted window.
+  const int nbw = (NW + 31) >> 5;
+  uint32_t* SB = reinterpret_cast<uint32_t*>(V + ((NW + 15) & ~15));
+  uint32_t* BB = SB + nbw;
+  {
+    const long long Omod = ((O % lmax) + lmax) % lmax;
+    const uint32_t lm = (uint32_t)lmax;
+    const bool pow2 = (lm & (lm - 1)) == 0;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    for (int w0 = warp * 32; w0 < nbw * 32; w0 += nwarp * 32) {
+      const int i = w0 + lane;
+      bool st = false, bd = true;
+      if (i >= 1 && i < NW) {
+        const uint32_t r = (uint32_t)Omod + (uint32_t)i;
+        const bool cut = pow2 ? ((r & (lm - 1)) == 0u) : (r % lm == 0u);
+        st = V[i] && (!V[i - 1] || M[i - 1] != M[i] || cut);
+        bd = !V[i] || st;
+      }
+      const uint32_t sb = __ballot_sync(0xFFFFFFFFu, st);
+      const uint32_t bb = __ballot_sync(0xFFFFFFFFu, bd);
+      if (lane == 0) {
+        SB[w0 >> 5] = sb;
+        BB[w0 >> 5] = bb;
+      }
+    }
+  }
+  __syncthreads();
+
   const uint32_t vmask = (2 * m >= 32) ? 0xFFFFFFFFu : ((1u << (2 * m)) - 1u);
   const int own = (int)(P1 - P0);
   for (int i = 1 + threadIdx.x; i <= own; i += blockDim.x) {
-    if (!V[i]) continue;
+    if (!((SB[i >> 5] >> (i & 31)) & 1u)) continue;
     const long long p = O + i;
     const uint32_t mi = M[i];
-    if (V[i - 1] && M[i - 1] == mi && (p % lmax) != 0) continue;
-    int j = i + 1;
-    while (((O + j) % lmax) != 0 && j < NW && V[j] && M[j] == mi) ++j;
-    const uint32_t nk = (uint32_t)(j - i);
+    // end = first boundary after i (a cut every L_max windows bounds the search)
+    int j = i + 1, end = NW;
+    for (int wj = j >> 5; wj < nbw; ++wj) {
+      const uint32_t bits = BB[wj] & (wj == (j >> 5) ? (0xFFFFFFFFu << (j & 31)) : 0xFFFFFFFFu);
+      if (bits) {
+        end = min(NW, (wj << 5) + __ffs(bits) - 1);
+        break;
+      }
+    }
+    const uint32_t nk = (uint32_t)(end - i);
     const uint32_t h = fmix32(mi & vmask);
     uint32_t bin;
     if (P.bounds) {
@@ -234,7 +270,8 @@ size_t supermer_smem_bytes(int tile, int lmax, int k) {
   const long long NQ = NW + k;  // upper bound (m >= 1)
   const long long NB = NW + k;
   const long long nsw = NB / 32 + 3;
-  return nsw * 8 + 2 * nsw * 4 + 2 * NQ * 4 + NW + 16;
+  const long long nbw = (NW + 31) / 32;
+  return nsw * 8 + 2 * nsw * 4 + 2 * NQ * 4 + ((NW + 15) & ~15LL) + 2 * nbw * 4 + 16;
 }
 
 cudaError_t launch_encode(const uint8_t* seq, uint64_t n, unsigned long long* packed,

@@ -571,8 +571,10 @@ static int count_impl(gerbil_ctx* ctx, const gerbil_bins* b, const std::vector<i
       work.push_back(w);
     }
     if (tiles >= (1ull << 32)) return fail(ctx, GERBIL_E_INVAL, "too many tiles");
-    const uint64_t ovf_cap = opts.overflow_slots ? opts.overflow_slots
-                                                 : std::max<uint64_t>(1 << 16, occ / 32) << round;
+    // the overflow area grows 4x per retry (a caller-given size is the starting size)
+    const uint64_t ovf_cap = (opts.overflow_slots ? (uint64_t)opts.overflow_slots
+                                                  : std::max<uint64_t>(1 << 16, occ / 32))
+                             << (2 * round);
     const size_t arena_need = slots * (W + 1) * 8;
     int rc;
     if ((rc = scratch(ctx, &ctx->arena, &ctx->arena_bytes, arena_need + 256))) return rc;
@@ -665,10 +667,11 @@ static int count_impl(gerbil_ctx* ctx, const gerbil_bins* b, const std::vector<i
     if ((rc = read_counters(ctx))) { drop(); return rc; }
     Counters h = *ctx->hctr;
     if (h.err & gerbil::ERR_OVF_FULL) {
-      // the emergency area ran full: repeat with twice the table size estimate
+      // the emergency area ran full: repeat with the largest table estimate (every k-mer
+      // distinct) and a long probe limit, which leaves almost nothing to the overflow area
       drop();
-      ratio = std::min(1.0, ratio * 2.0);
-      theta = std::max<uint32_t>(theta, 128);
+      ratio = 1.0;
+      theta = std::max<uint32_t>(theta, 1024);
       stats.retries++;
       continue;
     }

@@ -12,6 +12,7 @@ from __future__ import annotations
 
 import ctypes
 import os
+import weakref
 
 import numpy as np
 
@@ -287,6 +288,7 @@ class _DeviceArray:
 class Counts:
     def __init__(self, handle, ctx):
         self.handle, self.ctx = handle, ctx
+        ctx._children.add(self)
 
     def info(self):
         return gerbil_counts_info(self.handle)
@@ -311,9 +313,10 @@ class Counts:
         return keys, cnts
 
     def free(self):
-        if self.handle:
+        # a context frees its children before it is destroyed (include/gerbil.h ownership)
+        if self.handle and self.ctx.handle:
             gerbil_counts_free(self.handle)
-            self.handle = None
+        self.handle = None
 
     def __del__(self):
         try:
@@ -325,6 +328,7 @@ class Counts:
 class Bins:
     def __init__(self, handle, ctx):
         self.handle, self.ctx = handle, ctx
+        ctx._children.add(self)
 
     def info(self):
         return gerbil_bins_info(self.handle)
@@ -336,9 +340,9 @@ class Bins:
         return gerbil_bins_export(self.handle)
 
     def free(self):
-        if self.handle:
+        if self.handle and self.ctx.handle:
             gerbil_bins_free(self.handle)
-            self.handle = None
+        self.handle = None
 
     def __del__(self):
         try:
@@ -353,6 +357,7 @@ class Context:
             import torch
             stream = torch.cuda.current_stream(device).cuda_stream
         self.device = device
+        self._children = weakref.WeakSet()
         self.handle = gerbil_create(device, hbm_budget_bytes, stream)
 
     def partition(self, seq, offsets, k, m, nbins, opts=None, bin_bounds=None) -> Bins:
@@ -372,6 +377,8 @@ class Context:
 
     def close(self):
         if self.handle:
+            for child in list(self._children):
+                child.free()
             gerbil_destroy(self.handle)
             self.handle = None
 

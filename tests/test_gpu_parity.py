@@ -42,13 +42,14 @@ def _gpu_count(g, seq, offs, k, m, nbins, min_count, on_device=True, batch=True,
         res.free()
     else:
         ks, cs = [], []
-        stats = {"overflowed": 0}
+        stats = {"overflowed": 0, "retries": 0}
         for b in range(nbins):
             r = ctx.count(bins, b, k, min_count, o)
             kk, cc = r.to_host()
             ks.append(kk)
             cs.append(cc)
             stats["overflowed"] += r.info()[2]["overflowed"]
+            stats["retries"] += r.info()[2]["retries"]
             r.free()
         W = (2 * k + 63) // 64
         keys = np.concatenate(ks) if ks else np.zeros((0, W), np.uint64)
@@ -176,11 +177,12 @@ def test_forced_overflow_recount_is_exact(g):
     offs = np.concatenate([offs, offs[1:] + offs[-1]])
     for k in (32, 65, 200):
         want = oracle.count(seq, offs, k, min_count=2)
-        got, st = _gpu_count(g, seq, offs, k, 9, 4, 2, max_probes=1, distinct_ratio=0.05)
-        assert st["overflowed"] > 0
+        kw = dict(max_probes=1, distinct_ratio=0.05, overflow_slots=1 << 22)
+        got, st = _gpu_count(g, seq, offs, k, 9, 4, 2, **kw)
+        assert st["overflowed"] > 0 and st["retries"] == 0
         assert_same_rows(got, want)
         # per-bin path with the same forcing
-        got, st = _gpu_count(g, seq, offs, k, 9, 4, 2, batch=False, max_probes=1, distinct_ratio=0.05)
+        got, st = _gpu_count(g, seq, offs, k, 9, 4, 2, batch=False, **kw)
         assert st["overflowed"] > 0
         assert_same_rows(got, want)
 
@@ -189,6 +191,7 @@ def test_overflow_area_full_retries(g):
     seq, offs = synth.random_small(200, 100, 200, p_n=0.0, seed=9)
     got, st = _gpu_count(g, seq, offs, 33, 7, 2, 1, max_probes=1, distinct_ratio=0.01,
                          overflow_slots=16)
+    assert st["retries"] > 0
     assert_same_rows(got, oracle.count(seq, offs, 33))
 
 
