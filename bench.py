@@ -259,7 +259,7 @@ def main_ours(a, world, rank, local):
     p2_ms = (ph["clear_ms"] + ph["insert_ms"] + ph["compact_ms"] + ph["overflow_ms"]) / a.steps
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                 "frac": achieved / hbm, "traffic": _traffic_from_profile(a.workload),
-                "kernel": "insert_persistent_kernel<%d>" % W,
+                "kernel": "insert_kernel<%d,%d>" % (W, (2 * k + 62) // 63),
                 "peak_kind": peak_kind + " (hbm_gbs, copy bandwidth)",
                 "bytes_per_launch": insert_bytes, "launch_ms": ins_ms}
     phase_ms = {key[:-3]: ph[key] / a.steps for key in ph if key.endswith("_ms")}

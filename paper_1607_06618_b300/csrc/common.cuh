@@ -29,15 +29,71 @@ struct Counters {
 };
 
 // ---- table slot layout -------------------------------------------------------------------
-// A slot is (W+1) 64-bit words: word 0 = meta, words 1..W = key.  meta's low 32 bits hold the
-// count; the high 32 bits hold the state: CLAIMED | PUBLISHED | MERGED | 29-bit tag taken from
-// the key's hash.  meta == 0 is an empty slot.
+// A slot is SW = even(WS+1) 64-bit words: word 0 = meta, words 1..WS = the stored key.  meta's
+// low 32 bits hold the count; the high 32 bits hold CLAIMED | MERGED | 30-bit tag taken from
+// the key's hash; meta == 0 is an empty slot.  The stored key is the 2k-bit key cut into
+// WS = ceil(2k/63) chunks of 63 bits, each with bit 63 set as a "written" marker.  A cleared
+// word (0) can therefore never be mistaken for a written one: a reader that sees every
+// marker set has read the final key, word by word, with relaxed loads and no ordering.
 constexpr uint32_t META_CLAIMED = 1u << 31;
-constexpr uint32_t META_PUBLISHED = 1u << 30;
-constexpr uint32_t META_MERGED = 1u << 29;
-constexpr uint32_t META_TAG_MASK = (1u << 29) - 1;
-constexpr unsigned long long PUB64 = (unsigned long long)META_PUBLISHED << 32;
+constexpr uint32_t META_MERGED = 1u << 30;
+constexpr uint32_t META_TAG_MASK = (1u << 30) - 1;
 constexpr unsigned long long MERGED64 = (unsigned long long)META_MERGED << 32;
+constexpr unsigned long long MARK = 1ull << 63;
+constexpr unsigned long long MASK63 = MARK - 1;
+
+__host__ __device__ constexpr int slot_words(int WS) { return (WS + 2) & ~1; }
+
+// key (W words, word 0 most significant) -> WS marked 63-bit chunks, chunk 0 least significant
+template <int W, int WS>
+__device__ __forceinline__ void to_stored(const unsigned long long key[W], unsigned long long st[WS]) {
+#pragma unroll
+  for (int c = 0; c < WS; ++c) {
+    const int L = 63 * c, r = L >> 6, sh = L & 63;  // r counts words from the least significant
+    unsigned long long v = 0;
+    if (r < W) v = key[W - 1 - r] >> sh;
+    if (sh >= 2 && r + 1 < W) v |= key[W - 2 - r] << (64 - sh);
+    st[c] = MARK | (v & MASK63);
+  }
+}
+
+template <int W, int WS>
+__device__ __forceinline__ void from_stored(const unsigned long long st[WS], unsigned long long key[W]) {
+#pragma unroll
+  for (int j = 0; j < W; ++j) key[j] = 0;
+#pragma unroll
+  for (int c = 0; c < WS; ++c) {
+    const unsigned long long v = st[c] & MASK63;
+    const int L = 63 * c, r = L >> 6, sh = L & 63;
+    if (r < W) key[W - 1 - r] |= v << sh;
+    if (sh >= 2 && r + 1 < W) key[W - 2 - r] |= v >> (64 - sh);
+  }
+}
+
+__device__ __forceinline__ void ld_relaxed_v2(const unsigned long long* p, unsigned long long& a,
+                                              unsigned long long& b) {
+  asm volatile("ld.relaxed.gpu.global.v2.u64 {%0, %1}, [%2];" : "=l"(a), "=l"(b) : "l"(p) : "memory");
+}
+__device__ __forceinline__ void st_relaxed_v2(unsigned long long* p, unsigned long long a,
+                                              unsigned long long b) {
+  asm volatile("st.relaxed.gpu.global.v2.u64 [%0], {%1, %2};" ::"l"(p), "l"(a), "l"(b) : "memory");
+}
+__device__ __forceinline__ unsigned long long cas_relaxed(unsigned long long* p, unsigned long long cmp,
+                                                          unsigned long long val) {
+  unsigned long long old;
+  asm volatile("atom.relaxed.gpu.global.cas.b64 %0, [%1], %2, %3;"
+               : "=l"(old)
+               : "l"(p), "l"(cmp), "l"(val)
+               : "memory");
+  return old;
+}
+
+// All SW words of a slot with relaxed 16-byte loads (slots are 16-byte aligned).
+template <int SW>
+__device__ __forceinline__ void load_slot(const unsigned long long* slot, unsigned long long v[SW]) {
+#pragma unroll
+  for (int i = 0; i < SW; i += 2) ld_relaxed_v2(slot + i, v[i], v[i + 1]);
+}
 
 // ---- memory-model helpers (PTX, gpu scope) -------------------------------------------------
 __device__ __forceinline__ unsigned long long ld_relaxed(const unsigned long long* p) {

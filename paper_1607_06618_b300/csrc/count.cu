@@ -10,44 +10,60 @@ namespace gerbil {
 
 // ---- table insert (Alg. 1) -------------------------------------------------------------------
 // Probe sequence: slot0 = fastrange(hash), then linear steps, at most theta probes (Alg. 1's
-// trial limit).  A slot is claimed by CAS on its meta word (empty -> CLAIMED|tag, count 1);
-// the claimer writes the key words and publishes with a release OR.  A prober whose tag
-// matches waits (bounded) for PUBLISHED, then compares the full key (acquire ordering makes
-// the key words visible).  Returns 0 on success, 1 if theta probes found no room, 2 if a
-// bounded wait gave up -- both of the latter send the k-mer to the overflow area, which is
-// always correct because overflow counts are added to table counts before filtering.
-template <int W>
+// trial limit).  Each probe reads the whole slot with relaxed 16-byte loads.  An empty slot is
+// claimed by CAS on its meta word (0 -> CLAIMED|tag, count 1); the claimer then writes the
+// marked key words.  A prober whose tag matches compares the key once every word carries its
+// marker (bounded wait otherwise) and adds 1 to the count.  Returns 0 on success, 1 if theta
+// probes found no room, 2 if a bounded wait gave up -- both send the k-mer to the overflow
+// area, which is always correct because overflow counts are added to table counts before
+// the min_count filter.
+template <int WS>
 __device__ __forceinline__ int table_insert(unsigned long long* __restrict__ tab, uint32_t cap,
-                                            const unsigned long long key[W], unsigned long long h,
+                                            const unsigned long long st[WS], unsigned long long h,
                                             uint32_t theta, uint32_t spin_limit) {
+  constexpr int SW = slot_words(WS);
   uint32_t s = (uint32_t)(((h & 0xFFFFFFFFull) * (unsigned long long)cap) >> 32);
-  const uint32_t tagw = META_CLAIMED | (uint32_t)((h >> 35) & META_TAG_MASK);
+  const uint32_t tagw = META_CLAIMED | (uint32_t)((h >> 34) & META_TAG_MASK);
   const unsigned long long claim = ((unsigned long long)tagw << 32) | 1ull;
   for (uint32_t t = 0; t < theta; ++t) {
-    unsigned long long* slot = tab + (unsigned long long)s * (W + 1);
-    unsigned long long mt = ld_acquire(slot);
-    if (mt == 0ull) {
-      mt = cas_acquire(slot, 0ull, claim);
-      if (mt == 0ull) {
+    unsigned long long* slot = tab + (unsigned long long)s * SW;
+    unsigned long long v[SW];
+    load_slot<SW>(slot, v);
+    if (v[0] == 0ull) {
+      const unsigned long long old = cas_relaxed(slot, 0ull, claim);
+      if (old == 0ull) {
+        // word 1 sits at byte 8 of the 16-byte aligned slot: store it alone, then aligned
+        // pairs (slot + 2, slot + 4, ...)
+        st_relaxed(slot + 1, st[0]);
 #pragma unroll
-        for (int j = 0; j < W; ++j) st_relaxed(slot + 1 + j, key[j]);
-        red_or_release(slot, PUB64);
+        for (int j = 1; j < WS; j += 2) {
+          if (j + 1 < WS) st_relaxed_v2(slot + 1 + j, st[j], st[j + 1]);
+          else st_relaxed(slot + 1 + j, st[j]);
+        }
         return 0;
       }
+      v[0] = old;
+#pragma unroll
+      for (int j = 1; j < SW; ++j) v[j] = 0ull;  // re-read below
     }
-    if (((uint32_t)(mt >> 32) & ~(META_PUBLISHED | META_MERGED)) == tagw) {
-      uint32_t spins = 0;
-      while (!(mt & PUB64)) {
-        if (++spins > spin_limit) return 2;
-        __nanosleep(64);
-        mt = ld_acquire(slot);
-      }
-      bool eq = true;
+    if (((uint32_t)(v[0] >> 32) & ~META_MERGED) == tagw) {
+      for (uint32_t spins = 0;;) {
+        bool all = true, eq = true;
 #pragma unroll
-      for (int j = 0; j < W; ++j) eq &= (ld_relaxed(slot + 1 + j) == key[j]);
-      if (eq) {
-        red_add(slot, 1ull);
-        return 0;
+        for (int j = 0; j < WS; ++j) {
+          all &= (v[1 + j] & MARK) != 0ull;
+          eq &= v[1 + j] == st[j];
+        }
+        if (all) {
+          if (eq) {
+            red_add(slot, 1ull);
+            return 0;
+          }
+          break;  // another key with the same tag
+        }
+        if (++spins > spin_limit) return 2;
+        if (spins > 1) __nanosleep(32);
+        load_slot<SW>(slot, v);
       }
     }
     s = (s + 1 == cap) ? 0u : s + 1;
@@ -57,20 +73,20 @@ __device__ __forceinline__ int table_insert(unsigned long long* __restrict__ tab
 
 // Lookup in a complete table (no concurrent inserts); marks the slot MERGED and returns its
 // count, or 0 if the key is absent.
-template <int W>
+template <int WS>
 __device__ __forceinline__ uint32_t table_take(unsigned long long* __restrict__ tab, uint32_t cap,
-                                               const unsigned long long key[W],
-                                               unsigned long long h) {
+                                               const unsigned long long st[WS], unsigned long long h) {
+  constexpr int SW = slot_words(WS);
   uint32_t s = (uint32_t)(((h & 0xFFFFFFFFull) * (unsigned long long)cap) >> 32);
-  const uint32_t tagw = META_CLAIMED | (uint32_t)((h >> 35) & META_TAG_MASK);
+  const uint32_t tagw = META_CLAIMED | (uint32_t)((h >> 34) & META_TAG_MASK);
   for (uint32_t t = 0; t < cap; ++t) {
-    unsigned long long* slot = tab + (unsigned long long)s * (W + 1);
+    unsigned long long* slot = tab + (unsigned long long)s * SW;
     const unsigned long long mt = slot[0];
     if (mt == 0ull) return 0;
-    if (((uint32_t)(mt >> 32) & ~(META_PUBLISHED | META_MERGED)) == tagw) {
+    if (((uint32_t)(mt >> 32) & ~META_MERGED) == tagw) {
       bool eq = true;
 #pragma unroll
-      for (int j = 0; j < W; ++j) eq &= (slot[1 + j] == key[j]);
+      for (int j = 0; j < WS; ++j) eq &= (slot[1 + j] == st[j]);
       if (eq) {
         atom_or(slot, MERGED64);
         return (uint32_t)mt;
@@ -95,53 +111,66 @@ __device__ __forceinline__ void to_overflow(const CountParams& P, uint32_t widx,
   atomicAdd(P.bin_ovf + widx, 1u);
 }
 
-// ---- one tile of one bin: extract, canonicalise, insert ----------------------------------------
-struct TileSmem {
-  unsigned long long pos[COUNT_TILE];
-  uint32_t koff[COUNT_TILE];
-  uint32_t widx, tile, s_lo, ns;
-};
+// ---- warp work items: extract, canonicalise, insert --------------------------------------------
+// The k-mers of a bin are cut into items of ITEM_KMERS consecutive k-mers (bin order).  Item i
+// is done by one warp; imap[i] = (work index << 32 | first super-mer of the item), built by
+// item_map_kernel, so a warp starts without searching.  The warp loads the item's super-mer
+// descriptors into its own shared-memory slice; each lane then takes k-mers lane, lane+32, ...
+// of the item, reads its bases through L1 and inserts.  No CTA-wide barrier is involved.
 
-// Last super-mer index s in [lo, hi) with koff[s] <= j (koff ascending within a bin).
-__device__ __forceinline__ uint32_t last_le(const uint32_t* __restrict__ koff, uint32_t lo,
-                                            uint32_t hi, uint32_t j) {
-  while (hi - lo > 1) {
-    const uint32_t mid = (lo + hi) >> 1;
-    if (__ldg(koff + mid) <= j) lo = mid; else hi = mid;
-  }
-  return lo;
-}
-
-template <int W>
-__device__ __forceinline__ void count_tile(const CountParams& P, TileSmem& S) {
-  // thread 0 located the bin (S.widx) and the tile within it (S.tile)
-  const BinWork wk = P.work[S.widx];
-  const uint32_t j0 = S.tile * COUNT_TILE;
-  const uint32_t j1 = min(j0 + (uint32_t)COUNT_TILE, wk.n_kmers);
-  const uint32_t* koff = P.sm_koff + wk.sm_begin;
-  const unsigned long long* spos = P.sm_pos + wk.sm_begin;
-  if (threadIdx.x == 0) {
-    const uint32_t lo = last_le(koff, 0, wk.n_super, j0);
-    const uint32_t hi = last_le(koff, lo, wk.n_super, j1 - 1);
-    S.s_lo = lo;
-    S.ns = hi - lo + 1;
-    if (S.ns > (uint32_t)COUNT_TILE) {  // descriptors out of order: never expected
-      set_err(P.ctr, ERR_STATE);
-      S.ns = 0;
+__global__ void __launch_bounds__(256) item_map_kernel(const BinWork* __restrict__ work, uint32_t nwork,
+                                                      const uint32_t* __restrict__ sm_koff,
+                                                      unsigned long long* __restrict__ imap) {
+  for (uint32_t wi = blockIdx.x; wi < nwork; wi += gridDim.x) {
+    const BinWork wk = work[wi];
+    const uint32_t* koff = sm_koff + wk.sm_begin;
+    for (uint32_t s = threadIdx.x; s < wk.n_super; s += blockDim.x) {
+      const unsigned long long a = koff[s];
+      const unsigned long long b = (s + 1 < wk.n_super) ? koff[s + 1] : wk.n_kmers;
+      for (unsigned long long t = (a + ITEM_KMERS - 1) / ITEM_KMERS; t * ITEM_KMERS < b; ++t)
+        imap[wk.item_begin + t] = ((unsigned long long)wi << 32) | s;
     }
   }
-  __syncthreads();
-  const uint32_t s_lo = S.s_lo, ns = S.ns;
-  for (uint32_t i = threadIdx.x; i < ns; i += blockDim.x) {
-    S.koff[i] = __ldg(koff + s_lo + i);
-    S.pos[i] = __ldg(spos + s_lo + i);
+}
+
+struct WarpSmem {
+  uint32_t koff[ITEM_KMERS];
+  unsigned long long pos[ITEM_KMERS];
+};
+
+template <int W, int WS>
+__device__ __forceinline__ void count_item(const CountParams& P, unsigned long long item,
+                                           unsigned long long entry, WarpSmem& S, int lane) {
+  const uint32_t wi = (uint32_t)(entry >> 32), s_lo = (uint32_t)entry;
+  const BinWork wk = P.work[wi];
+  const uint32_t j0 = (uint32_t)(item - wk.item_begin) * ITEM_KMERS;
+  const uint32_t j1 = min(j0 + (uint32_t)ITEM_KMERS, wk.n_kmers);
+  const uint32_t* koff = P.sm_koff + wk.sm_begin;
+  const unsigned long long* spos = P.sm_pos + wk.sm_begin;
+  // descriptors of the super-mers that hold k-mers [j0, j1): koff ascends, so they are the
+  // ones from s_lo on whose first k-mer is below j1
+  uint32_t ns = 0;
+  for (uint32_t c = 0; c < (uint32_t)ITEM_KMERS; c += 32) {
+    const uint32_t s = s_lo + c + lane;
+    const bool have = s < wk.n_super;
+    const uint32_t ko = have ? __ldg(koff + s) : wk.n_kmers;
+    const unsigned long long po = have ? __ldg(spos + s) : 0ull;
+    const bool in = have && (c + lane == 0 || ko < j1);
+    const uint32_t bal = __ballot_sync(0xFFFFFFFFu, in);
+    if (in) {
+      S.koff[c + lane] = ko;
+      S.pos[c + lane] = po;
+    }
+    const uint32_t cnt = __popc(bal);
+    ns += cnt;
+    if (cnt < 32) break;
   }
-  __syncthreads();
-  unsigned long long* tab = P.arena + wk.table_off * (W + 1);
+  __syncwarp();
+  unsigned long long* tab = P.arena + wk.table_off * slot_words(WS);
 #pragma unroll 1
-  for (int r = 0; r < KMERS_PER_THREAD; ++r) {
-    const uint32_t j = j0 + threadIdx.x + r * COUNT_THREADS;
-    if (j >= j1 || ns == 0) break;
+  for (int r = 0; r < ITEM_KMERS / 32; ++r) {
+    const uint32_t j = j0 + lane + 32 * r;
+    if (j >= j1) break;
     uint32_t lo = 0, hi = ns;
     while (hi - lo > 1) {
       const uint32_t mid = (lo + hi) >> 1;
@@ -159,47 +188,26 @@ __device__ __forceinline__ void count_tile(const CountParams& P, TileSmem& S) {
       }
     }
     const unsigned long long h = key_hash<W>(key);
-    const int res = table_insert<W>(tab, wk.cap, key, h, P.theta, P.spin_limit);
-    if (res) to_overflow<W>(P, S.widx, key, res);
+    unsigned long long st[WS];
+    to_stored<W, WS>(key, st);
+    const int res = table_insert<WS>(tab, wk.cap, st, h, P.theta, P.spin_limit);
+    if (res) to_overflow<W>(P, wi, key, res);
   }
-  __syncthreads();  // S is reused by the next tile
+  __syncwarp();  // S is reused by the next item
 }
 
-__device__ __forceinline__ void locate_tile(const CountParams& P, uint32_t gtile, TileSmem& S) {
-  // last work entry whose tile_begin <= gtile
-  uint32_t lo = 0, hi = P.nwork;
-  while (hi - lo > 1) {
-    const uint32_t mid = (lo + hi) >> 1;
-    if (P.work[mid].tile_begin <= gtile) lo = mid; else hi = mid;
-  }
-  S.widx = lo;
-  S.tile = gtile - P.work[lo].tile_begin;
-}
-
-// Grid form: one CTA per tile.
-template <int W>
-__global__ void __launch_bounds__(COUNT_THREADS) insert_kernel(CountParams P) {
-  __shared__ TileSmem S;
-  if (threadIdx.x == 0) locate_tile(P, P.tile_base + blockIdx.x, S);
-  __syncthreads();
-  count_tile<W>(P, S);
-}
-
-// Persistent form: CTAs pop tile indices from a device work queue (tiles ordered by bin, so
-// the bins in flight at any moment are few and their tables stay hot in L2).
-template <int W>
-__global__ void __launch_bounds__(COUNT_THREADS) insert_persistent_kernel(CountParams P) {
-  __shared__ TileSmem S;
-  __shared__ uint32_t next;
-  for (;;) {
-    if (threadIdx.x == 0) {
-      const unsigned long long t = atomicAdd(&P.ctr->queue_head, 1ull);
-      next = (t < P.ntiles) ? (uint32_t)t : 0xFFFFFFFFu;
-      if (next != 0xFFFFFFFFu) locate_tile(P, next, S);
-    }
-    __syncthreads();
-    if (next == 0xFFFFFFFFu) break;
-    count_tile<W>(P, S);
+// Warps stride over the items in bin order, so the bins in flight at any moment are few and
+// their tables stay hot in L2.  Launched with as many CTAs as fit on the GPU (persistent) or
+// one warp per item.
+template <int W, int WS>
+__global__ void __launch_bounds__(256) insert_kernel(CountParams P) {
+  __shared__ WarpSmem S[8];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const unsigned long long nw = (unsigned long long)gridDim.x * (blockDim.x >> 5);
+  for (unsigned long long item = blockIdx.x * (unsigned long long)(blockDim.x >> 5) + warp;
+       item < P.nitems; item += nw) {
+    const unsigned long long entry = __ldg(P.imap + item);
+    count_item<W, WS>(P, item, entry, S[warp], lane);
   }
 }
 
@@ -214,6 +222,122 @@ __device__ __forceinline__ uint32_t work_of_slot(const BinWork* work, uint32_t n
   return lo;
 }
 
+// CTA-cooperative append: every thread contributes e rows; one atomic per CTA returns the base
+// and an exclusive scan over the CTA gives every thread its first row.
+__device__ __forceinline__ unsigned long long cta_append(uint32_t e, Counters* ctr,
+                                                         uint32_t* wsum, unsigned long long* cbase) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  uint32_t incl = e;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane == 31) wsum[warp] = incl;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t acc = 0;
+    for (int i = 0; i < nwarp; ++i) {
+      const uint32_t t = wsum[i];
+      wsum[i] = acc;
+      acc += t;
+    }
+    *cbase = acc ? atomicAdd(&ctr->out_count, (unsigned long long)acc) : 0ull;
+  }
+  __syncthreads();
+  const unsigned long long first = *cbase + wsum[warp] + incl - e;
+  __syncthreads();  // wsum / cbase are reused by the next call
+  return first;
+}
+
+template <int W, int WS>
+__global__ void __launch_bounds__(256, 3) compact_kernel(CompactParams P) {
+  constexpr int SW = slot_words(WS);
+  constexpr int COMPACT_UNROLL = SW <= 4 ? 4 : 2;
+  __shared__ uint32_t wsum[8];
+  __shared__ unsigned long long cbase;
+  const bool any_ovf = P.ctr->ovf_count != 0ull;
+  unsigned long long ndist = 0;
+  const unsigned long long chunk = (unsigned long long)blockDim.x * COMPACT_UNROLL;
+  for (unsigned long long cb = P.slot_lo + blockIdx.x * chunk; cb < P.slot_hi;
+       cb += (unsigned long long)gridDim.x * chunk) {
+    unsigned long long v[COMPACT_UNROLL][SW];
+#pragma unroll
+    for (int u = 0; u < COMPACT_UNROLL; ++u) {
+      const unsigned long long slot = cb + u * blockDim.x + threadIdx.x;
+      if (slot < P.slot_hi) {
+        const unsigned long long* sp = P.arena + slot * SW;
+#pragma unroll
+        for (int i = 0; i < SW; i += 2) {
+          const ulonglong2 x = *reinterpret_cast<const ulonglong2*>(sp + i);
+          v[u][i] = x.x;
+          v[u][i + 1] = x.y;
+        }
+      } else {
+#pragma unroll
+        for (int i = 0; i < SW; ++i) v[u][i] = 0ull;
+      }
+    }
+    uint32_t cnt[COMPACT_UNROLL];
+    uint32_t e = 0;
+#pragma unroll
+    for (int u = 0; u < COMPACT_UNROLL; ++u) {
+      const unsigned long long slot = cb + u * blockDim.x + threadIdx.x;
+      const unsigned long long mt = v[u][0];
+      bool live = mt != 0ull;
+      if (live) {
+        bool all = true;
+#pragma unroll
+        for (int j = 0; j < WS; ++j) all &= (v[u][1 + j] & MARK) != 0ull;
+        if (!all) {  // a claimed slot whose key was never written: never expected
+          set_err(P.ctr, ERR_STATE);
+          live = false;
+        }
+      }
+      bool take = live && P.mode == 0;
+      if (live && any_ovf) {
+        const uint32_t wi = work_of_slot(P.work, P.nwork, slot);
+        const bool deferred = P.bin_ovf[wi] != 0u;
+        take = (P.mode == 0) ? !deferred : deferred;
+      }
+      uint32_t c = 0;
+      if (take) {
+        ++ndist;
+        c = (uint32_t)mt;
+        if (P.mode == 1) {
+          unsigned long long key[W];
+          from_stored<W, WS>(&v[u][1], key);
+          const uint32_t extra = table_take<WS>(P.otab, P.ocap, &v[u][1], key_hash<W>(key));
+          if (extra) atomicAdd(&P.ctr->merged, 1ull);
+          c += extra;
+        }
+        if (c < P.min_count) c = 0;
+      }
+      cnt[u] = c;
+      e += c ? 1u : 0u;
+    }
+    unsigned long long row = cta_append(e, P.ctr, wsum, &cbase);
+#pragma unroll
+    for (int u = 0; u < COMPACT_UNROLL; ++u) {
+      if (!cnt[u]) continue;
+      if (row < P.out_cap) {
+        unsigned long long key[W];
+        from_stored<W, WS>(&v[u][1], key);
+#pragma unroll
+        for (int j = 0; j < W; ++j) P.out_keys[row * W + j] = key[j];
+        P.out_counts[row] = cnt[u];
+      } else {
+        set_err(P.ctr, ERR_OUT_FULL);
+      }
+      ++row;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) ndist += __shfl_down_sync(0xFFFFFFFFu, ndist, o);
+  if ((threadIdx.x & 31) == 0 && ndist) atomicAdd(&P.ctr->distinct, ndist);
+}
+
+// Warp-cooperative append of the rows whose lane has emit set: one atomic per warp (used by the
+// overflow-only emission, whose table is small).
 template <int W>
 __device__ __forceinline__ void emit_rows(bool emit, const unsigned long long key[W], uint32_t c,
                                          unsigned long long* out_keys, uint32_t* out_counts,
@@ -236,57 +360,9 @@ __device__ __forceinline__ void emit_rows(bool emit, const unsigned long long ke
   }
 }
 
-template <int W>
-__global__ void __launch_bounds__(256) compact_kernel(CompactParams P) {
-  const bool any_ovf = P.ctr->ovf_count != 0ull;
-  const unsigned long long nthreads = (unsigned long long)gridDim.x * blockDim.x;
-  const unsigned long long warp0 = (blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) & ~31ull;
-  const unsigned int lane = threadIdx.x & 31;
-  unsigned long long ndist = 0;
-  for (unsigned long long base = P.slot_lo + warp0; base < P.slot_hi; base += nthreads) {
-    const unsigned long long slot = base + lane;
-    bool emit = false;
-    unsigned long long key[W];
-    uint32_t c = 0;
-    if (slot < P.slot_hi) {
-      const unsigned long long* sp = P.arena + slot * (W + 1);
-      const unsigned long long mt = sp[0];
-      bool live = mt != 0ull;
-      if (live && !(mt & PUB64)) {
-        set_err(P.ctr, ERR_STATE);
-        live = false;
-      }
-      bool take = live;
-      if (live && any_ovf) {
-        const uint32_t wi = work_of_slot(P.work, P.nwork, slot);
-        const bool deferred = P.bin_ovf[wi] != 0u;
-        take = (P.mode == 0) ? !deferred : deferred;
-      } else if (P.mode == 1) {
-        take = false;
-      }
-      if (take) {
-        ++ndist;
-#pragma unroll
-        for (int j = 0; j < W; ++j) key[j] = sp[1 + j];
-        c = (uint32_t)mt;
-        if (P.mode == 1) {
-          const uint32_t extra = table_take<W>(P.otab, P.ocap, key, key_hash<W>(key));
-          if (extra) atomicAdd(&P.ctr->merged, 1ull);
-          c += extra;
-        }
-        emit = c >= P.min_count;
-      }
-    }
-    emit_rows<W>(emit, key, c, P.out_keys, P.out_counts, P.out_cap, P.ctr);
-  }
-  // distinct keys of the main tables (overflow-only keys are added by the overflow emit)
-  for (int o = 16; o > 0; o >>= 1) ndist += __shfl_down_sync(0xFFFFFFFFu, ndist, o);
-  if (lane == 0 && ndist) atomicAdd(&P.ctr->distinct, ndist);
-}
-
 // ---- overflow recount (Sec. 3.4 "Probing Strategy": the emergency area is counted after the
 // file) -- a fresh table sized for all overflow k-mers, probed without a trial limit -----------
-template <int W>
+template <int W, int WS>
 __global__ void __launch_bounds__(256) overflow_insert_kernel(OverflowParams P) {
   const unsigned long long n = min(P.ctr->ovf_count, P.ovf_cap);
   for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
@@ -294,14 +370,17 @@ __global__ void __launch_bounds__(256) overflow_insert_kernel(OverflowParams P) 
     unsigned long long key[W];
 #pragma unroll
     for (int j = 0; j < W; ++j) key[j] = P.ovf[i * W + j];
-    const int res = table_insert<W>(P.otab, P.ocap, key, key_hash<W>(key), P.ocap, P.spin_limit);
+    unsigned long long st[WS];
+    to_stored<W, WS>(key, st);
+    const int res = table_insert<WS>(P.otab, P.ocap, st, key_hash<W>(key), P.ocap, P.spin_limit);
     if (res) set_err(P.ctr, ERR_SPIN);
   }
 }
 
 // Keys that exist only in the overflow table (not merged into a main-table key).
-template <int W>
+template <int W, int WS>
 __global__ void __launch_bounds__(256) overflow_emit_kernel(OverflowParams P) {
+  constexpr int SW = slot_words(WS);
   const unsigned long long nthreads = (unsigned long long)gridDim.x * blockDim.x;
   const unsigned long long warp0 = (blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) & ~31ull;
   const unsigned int lane = threadIdx.x & 31;
@@ -312,12 +391,14 @@ __global__ void __launch_bounds__(256) overflow_emit_kernel(OverflowParams P) {
     unsigned long long key[W];
     uint32_t c = 0;
     if (slot < P.ocap) {
-      const unsigned long long* sp = P.otab + slot * (W + 1);
+      const unsigned long long* sp = P.otab + slot * SW;
       const unsigned long long mt = sp[0];
       if (mt != 0ull && !(mt & MERGED64)) {
         ++ndist;
+        unsigned long long st[WS];
 #pragma unroll
-        for (int j = 0; j < W; ++j) key[j] = sp[1 + j];
+        for (int j = 0; j < WS; ++j) st[j] = sp[1 + j];
+        from_stored<W, WS>(st, key);
         c = (uint32_t)mt;
         emit = c >= P.min_count;
       }
@@ -328,59 +409,90 @@ __global__ void __launch_bounds__(256) overflow_emit_kernel(OverflowParams P) {
   if (lane == 0 && ndist) atomicAdd(&P.ctr->distinct, ndist);
 }
 
-// ---- launchers (W dispatch) ---------------------------------------------------------------------
-#define GERBIL_W_SWITCH(W, CALL)          \
-  switch (W) {                            \
-    case 1: CALL(1); break;               \
-    case 2: CALL(2); break;               \
-    case 3: CALL(3); break;               \
-    case 4: CALL(4); break;               \
-    case 5: CALL(5); break;               \
-    case 6: CALL(6); break;               \
-    case 7: CALL(7); break;               \
-    case 8: CALL(8); break;               \
-    default: return cudaErrorInvalidValue; \
+// ---- launchers: dispatch on (W, WS) ------------------------------------------------------------
+// W = ceil(2k/64) key words; WS = ceil(2k/63) stored words, W or W+1.
+#define GERBIL_KEY_SWITCH(W, WS, CALL)                 \
+  switch (W * 16 + WS) {                               \
+    case 1 * 16 + 1: CALL(1, 1); break;                \
+    case 1 * 16 + 2: CALL(1, 2); break;                \
+    case 2 * 16 + 2: CALL(2, 2); break;                \
+    case 2 * 16 + 3: CALL(2, 3); break;                \
+    case 3 * 16 + 3: CALL(3, 3); break;                \
+    case 3 * 16 + 4: CALL(3, 4); break;                \
+    case 4 * 16 + 4: CALL(4, 4); break;                \
+    case 4 * 16 + 5: CALL(4, 5); break;                \
+    case 5 * 16 + 5: CALL(5, 5); break;                \
+    case 5 * 16 + 6: CALL(5, 6); break;                \
+    case 6 * 16 + 6: CALL(6, 6); break;                \
+    case 6 * 16 + 7: CALL(6, 7); break;                \
+    case 7 * 16 + 7: CALL(7, 7); break;                \
+    case 7 * 16 + 8: CALL(7, 8); break;                \
+    case 8 * 16 + 8: CALL(8, 8); break;                \
+    case 8 * 16 + 9: CALL(8, 9); break;                \
+    default: return cudaErrorInvalidValue;             \
   }
 
-cudaError_t launch_insert(int W, const CountParams& p, unsigned grid, cudaStream_t st) {
-  if (grid == 0) return cudaSuccess;
-#define L_INSERT(w) insert_kernel<w><<<grid, COUNT_THREADS, 0, st>>>(p)
-  GERBIL_W_SWITCH(W, L_INSERT)
+int stored_words(int k) { return (2 * k + 62) / 63; }
+int slot_words_for_k(int k) { return slot_words(stored_words(k)); }
+
+cudaError_t launch_item_map(const CountParams& p, cudaStream_t st) {
+  if (p.nwork == 0) return cudaSuccess;
+  item_map_kernel<<<std::min<unsigned>(p.nwork, 4096u), 256, 0, st>>>(p.work, p.nwork, p.sm_koff,
+                                                                      p.imap);
+  return cudaGetLastError();
+}
+
+// persistent: as many CTAs as are resident at once (occupancy query), each warp striding over
+// the items; otherwise one warp per item.
+cudaError_t launch_insert(int k, const CountParams& p, int persistent, int nsm, cudaStream_t st) {
+  const unsigned long long need = (p.nitems + 7) / 8;
+  if (need == 0) return cudaSuccess;
+  const int W = (2 * k + 63) / 64, WS = stored_words(k);
+#define L_INSERT(w, ws)                                                                          \
+  {                                                                                              \
+    unsigned long long grid = need;                                                              \
+    if (persistent) {                                                                            \
+      int per_sm = 0;                                                                            \
+      cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, insert_kernel<w, ws>, \
+                                                                    COUNT_THREADS, 0);           \
+      if (e != cudaSuccess) return e;                                                            \
+      grid = std::min<unsigned long long>(need, (unsigned long long)nsm * std::max(1, per_sm));  \
+    }                                                                                            \
+    insert_kernel<w, ws><<<(unsigned)grid, COUNT_THREADS, 0, st>>>(p);                          \
+  }
+  GERBIL_KEY_SWITCH(W, WS, L_INSERT)
 #undef L_INSERT
   return cudaGetLastError();
 }
 
-cudaError_t launch_insert_persistent(int W, const CountParams& p, unsigned grid, cudaStream_t st) {
-  if (grid == 0) return cudaSuccess;
-#define L_PINSERT(w) insert_persistent_kernel<w><<<grid, COUNT_THREADS, 0, st>>>(p)
-  GERBIL_W_SWITCH(W, L_PINSERT)
-#undef L_PINSERT
-  return cudaGetLastError();
-}
-
-cudaError_t launch_compact(int W, const CompactParams& p, int nsm, cudaStream_t st) {
+cudaError_t launch_compact(int k, const CompactParams& p, int nsm, cudaStream_t st) {
   const unsigned long long n = p.slot_hi - p.slot_lo;
   if (n == 0) return cudaSuccess;
-  const unsigned grid = (unsigned)std::min<unsigned long long>((n + 255) / 256, (unsigned long long)nsm * 8);
-#define L_COMPACT(w) compact_kernel<w><<<grid, 256, 0, st>>>(p)
-  GERBIL_W_SWITCH(W, L_COMPACT)
+  const int W = (2 * k + 63) / 64, WS = stored_words(k);
+  const unsigned long long per_cta = 256ull * 4;
+  const unsigned grid = (unsigned)std::min<unsigned long long>((n + per_cta - 1) / per_cta,
+                                                               (unsigned long long)nsm * 8);
+#define L_COMPACT(w, ws) compact_kernel<w, ws><<<grid, 256, 0, st>>>(p)
+  GERBIL_KEY_SWITCH(W, WS, L_COMPACT)
 #undef L_COMPACT
   return cudaGetLastError();
 }
 
-cudaError_t launch_overflow_insert(int W, const OverflowParams& p, int nsm, cudaStream_t st) {
+cudaError_t launch_overflow_insert(int k, const OverflowParams& p, int nsm, cudaStream_t st) {
   const unsigned grid = (unsigned)nsm * 4;
-#define L_OINS(w) overflow_insert_kernel<w><<<grid, 256, 0, st>>>(p)
-  GERBIL_W_SWITCH(W, L_OINS)
+  const int W = (2 * k + 63) / 64, WS = stored_words(k);
+#define L_OINS(w, ws) overflow_insert_kernel<w, ws><<<grid, 256, 0, st>>>(p)
+  GERBIL_KEY_SWITCH(W, WS, L_OINS)
 #undef L_OINS
   return cudaGetLastError();
 }
 
-cudaError_t launch_overflow_emit(int W, const OverflowParams& p, int nsm, cudaStream_t st) {
+cudaError_t launch_overflow_emit(int k, const OverflowParams& p, int nsm, cudaStream_t st) {
   const unsigned grid = (unsigned)std::min<unsigned long long>(((unsigned long long)p.ocap + 255) / 256,
-                                                          (unsigned long long)nsm * 8);
-#define L_OEMIT(w) overflow_emit_kernel<w><<<grid, 256, 0, st>>>(p)
-  GERBIL_W_SWITCH(W, L_OEMIT)
+                                                               (unsigned long long)nsm * 8);
+  const int W = (2 * k + 63) / 64, WS = stored_words(k);
+#define L_OEMIT(w, ws) overflow_emit_kernel<w, ws><<<grid, 256, 0, st>>>(p)
+  GERBIL_KEY_SWITCH(W, WS, L_OEMIT)
 #undef L_OEMIT
   return cudaGetLastError();
 }

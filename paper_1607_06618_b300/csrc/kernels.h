@@ -23,10 +23,13 @@ struct SupermerParams {
   uint32_t nbins;
   const uint32_t* bounds;            // device, nbins-1 split points, or NULL
   int tile;                          // window starts per CTA
-  // pass 0
+  // supermer_kernel: per-bin counts and one record per super-mer
   unsigned long long* bin_nsuper;
   unsigned long long* bin_nkmers;
-  // pass 1
+  ulonglong2* rec;                   // (start, bin << 32 | k-mers)
+  unsigned long long rec_cap;
+  unsigned long long* rec_count;     // records produced (may exceed rec_cap: then rerun)
+  // scatter_kernel
   const unsigned long long* bin_sm_begin;
   unsigned long long* bin_cursor;    // (super-mers << 32) | k-mers, cleared before pass 1
   unsigned long long* sm_pos;        // global start of each super-mer
@@ -38,7 +41,8 @@ cudaError_t launch_encode(const uint8_t* seq, uint64_t n, unsigned long long* pa
                           uint32_t* nmask, uint64_t nwords, int vec_ok, int nsm, cudaStream_t st);
 cudaError_t launch_boundary(const uint64_t* offsets, uint64_t nreads, uint64_t n, uint32_t* bmask,
                             unsigned int* err, cudaStream_t st);
-cudaError_t launch_supermer(const SupermerParams& p, int pass, cudaStream_t st);
+cudaError_t launch_supermer(const SupermerParams& p, cudaStream_t st);
+cudaError_t launch_scatter(const SupermerParams& p, unsigned long long nrec, int nsm, cudaStream_t st);
 size_t supermer_smem_bytes(int tile, int lmax, int k);
 
 // ---- phase two ------------------------------------------------------------------------------
@@ -49,12 +53,11 @@ struct BinWork {
   uint32_t n_super;
   uint32_t n_kmers;
   uint32_t cap;                  // table slots
-  uint32_t tile_begin;           // first global tile index of the bin
+  uint32_t item_begin;           // first global work item of the bin
 };
 
 constexpr int COUNT_THREADS = 256;
-constexpr int KMERS_PER_THREAD = 4;
-constexpr int COUNT_TILE = COUNT_THREADS * KMERS_PER_THREAD;
+constexpr int ITEM_KMERS = 128;  // k-mers per warp work item (4 per lane)
 
 struct CountParams {
   const unsigned long long* packed;
@@ -62,13 +65,13 @@ struct CountParams {
   const uint32_t* sm_koff;
   const BinWork* work;
   uint32_t nwork;
-  uint32_t ntiles;
-  uint32_t tile_base;            // first tile of this launch (per-bin launches)
+  unsigned long long nitems;     // warp work items over all bins
+  unsigned long long* imap;      // item -> (work index << 32 | first super-mer of the item)
   int k;
   int canonical;
   uint32_t theta;                // max probes (Alg. 1)
   uint32_t spin_limit;           // bounded wait on an unpublished slot
-  unsigned long long* arena;     // all tables, (W+1) words per slot
+  unsigned long long* arena;     // all tables, slot_words_for_k(k) words per slot
   unsigned long long* ovf;       // overflow area, W words per k-mer
   unsigned long long ovf_cap;
   uint32_t* bin_ovf;             // overflow k-mers per work entry
@@ -104,10 +107,14 @@ struct OverflowParams {
   Counters* ctr;
 };
 
-cudaError_t launch_insert(int W, const CountParams& p, unsigned grid, cudaStream_t st);
-cudaError_t launch_insert_persistent(int W, const CountParams& p, unsigned grid, cudaStream_t st);
-cudaError_t launch_compact(int W, const CompactParams& p, int nsm, cudaStream_t st);
-cudaError_t launch_overflow_insert(int W, const OverflowParams& p, int nsm, cudaStream_t st);
-cudaError_t launch_overflow_emit(int W, const OverflowParams& p, int nsm, cudaStream_t st);
+// Table slots hold the key cut into ceil(2k/63) marked words (see common.cuh); a slot is
+// slot_words_for_k(k) 64-bit words.  Launchers dispatch on k.
+int stored_words(int k);
+int slot_words_for_k(int k);
+cudaError_t launch_item_map(const CountParams& p, cudaStream_t st);
+cudaError_t launch_insert(int k, const CountParams& p, int persistent, int nsm, cudaStream_t st);
+cudaError_t launch_compact(int k, const CompactParams& p, int nsm, cudaStream_t st);
+cudaError_t launch_overflow_insert(int k, const OverflowParams& p, int nsm, cudaStream_t st);
+cudaError_t launch_overflow_emit(int k, const OverflowParams& p, int nsm, cudaStream_t st);
 
 }  // namespace gerbil

@@ -67,11 +67,14 @@ __global__ void boundary_kernel(const uint64_t* __restrict__ offsets, uint64_t n
 
 // ---- N2/N3: minimizers, super-mers, bins ---------------------------------------------------
 // One CTA owns the window starts [P0, P0+T) of the global base stream.  It stages the 2-bit
-// bases and masks it needs in shared memory, computes the rank of every m-mer, takes the
-// sliding minimum over w = k-m+1 m-mers by doubling, marks which windows are counted (no
-// undetermined base, no read boundary inside), and emits the super-mers that start in its
-// range.  A super-mer never runs past the next multiple of L_max, so the CTA looks at most
-// L_max windows past its range to find where its last super-mer ends.
+// bases and masks it needs in shared memory and gives every m-mer a key: 0 if the m-mer holds
+// an undetermined base or straddles a read start, else 1 + its rank.  The sliding minimum of
+// the keys over w = k-m+1 m-mers (by doubling) is then 0 exactly for the windows that are not
+// counted (for m >= 2 every interior read start is straddled by one of the window's m-mers),
+// and 1 + the minimizer's rank otherwise.  Super-mer starts and ends come from two ballot
+// masks; a super-mer never runs past the next multiple of L_max, so the CTA looks at most
+// L_max windows past its range.  Each super-mer becomes one record (start, k-mers, bin),
+// appended with one atomic per warp, and counted into its bin.
 
 __device__ __forceinline__ unsigned long long bases64(const unsigned long long* sw, int lb) {
   const int w = lb >> 5, o = 2 * (lb & 31);
@@ -85,19 +88,14 @@ __device__ __forceinline__ uint32_t bits32(const uint32_t* sm, int lb) {
 // KMC2 reading (Sec. 3.1): demote m-mers that start with AAA or ACA or hold AA past
 // position 0.  v holds m bases in its low 2m bits, first base most significant.
 __device__ __forceinline__ uint32_t kmc2_demoted(uint32_t v, int m) {
-  uint32_t d = 0;
-  if (m >= 3) {
-    const uint32_t head = v >> (2 * m - 6);
-    d |= (head == 0u) | (head == 4u);  // AAA = 000000, ACA = 000100
-  }
-  if (m >= 3) {
-    const uint32_t lowbits = (m >= 16) ? 0xFFFFFFFFu : ((1u << (2 * m)) - 1u);
-    uint32_t a = ~(v | (v >> 1)) & 0x55555555u & lowbits;  // low bit of group set iff base A
-    uint32_t pairs = a & (a >> 2);            // group g-1 flagged iff groups g, g-1 are A
-    pairs &= ~(1u << (2 * (m - 2)));          // drop the pair at position 0
-    d |= pairs != 0u;
-  }
-  return d;
+  if (m < 3) return 0u;
+  const uint32_t head = v >> (2 * m - 6);
+  uint32_t d = (head == 0u) | (head == 4u);  // AAA = 000000, ACA = 000100
+  const uint32_t lowbits = (1u << (2 * m)) - 1u;
+  const uint32_t a = ~(v | (v >> 1)) & 0x55555555u & lowbits;  // low bit of group set iff A
+  uint32_t pairs = a & (a >> 2);    // group g-1 flagged iff groups g and g-1 are A
+  pairs &= ~(1u << (2 * (m - 2)));  // drop the pair at position 0
+  return d | (pairs != 0u);
 }
 
 __device__ __forceinline__ uint32_t mmer_rank(uint32_t v, int m, int ordering, int canon_min) {
@@ -110,7 +108,6 @@ __device__ __forceinline__ uint32_t mmer_rank(uint32_t v, int m, int ordering, i
   return c;
 }
 
-template <int PASS>
 __global__ void __launch_bounds__(256) supermer_kernel(SupermerParams P) {
   extern __shared__ __align__(16) unsigned char smem[];
   const long long T = P.tile;
@@ -129,19 +126,21 @@ __global__ void __launch_bounds__(256) supermer_kernel(SupermerParams P) {
 
   unsigned long long* sw = reinterpret_cast<unsigned long long*>(smem);
   uint32_t* snm = reinterpret_cast<uint32_t*>(sw + nsw);
-  uint32_t* scm = snm + nsw;
-  uint32_t* rk0 = scm + nsw;
+  uint32_t* sbm = snm + nsw;
+  uint32_t* rk0 = sbm + nsw;
   uint32_t* rk1 = rk0 + NQ;
   uint8_t* V = reinterpret_cast<uint8_t*>(rk1 + NQ);
+  const int nbw = (NW + 31) >> 5;
+  uint32_t* SB = reinterpret_cast<uint32_t*>(V + ((NW + 15) & ~15));
+  uint32_t* BB = SB + nbw;
 
   const long long nwords = (long long)P.nwords;
   for (int i = threadIdx.x; i < nsw; i += blockDim.x) {
     const long long g = wlo + i;
     const bool in = g >= 0 && g < nwords;
     sw[i] = in ? __ldg(P.packed + g) : 0ull;
-    const uint32_t nm = in ? __ldg(P.nmask + g) : 0xFFFFFFFFu;
-    snm[i] = nm;
-    scm[i] = nm | (in ? __ldg(P.bmask + g) : 0xFFFFFFFFu);
+    snm[i] = in ? __ldg(P.nmask + g) : 0xFFFFFFFFu;
+    sbm[i] = in ? __ldg(P.bmask + g) : 0xFFFFFFFFu;
   }
   __syncthreads();
 
@@ -149,18 +148,20 @@ __global__ void __launch_bounds__(256) supermer_kernel(SupermerParams P) {
   const long long n = (long long)P.n;
   for (int iq = threadIdx.x; iq < NQ; iq += blockDim.x) {
     const long long q = O + iq;
-    uint32_t r = 0xFFFFFFFFu;
+    uint32_t key = 0u;
     if (q >= 0 && q + m <= n) {
       const int lb = lbO + iq;
-      if ((bits32(snm, lb) >> (32 - m)) == 0u) {
+      bool ok = (bits32(snm, lb) >> (32 - m)) == 0u;
+      if (m >= 2) ok = ok && (bits32(sbm, lb + 1) >> (33 - m)) == 0u;  // no read start inside
+      if (ok) {
         const uint32_t v = (uint32_t)(bases64(sw, lb) >> (64 - 2 * m));
-        r = mmer_rank(v, m, P.ordering, P.canon_min);
+        key = mmer_rank(v, m, P.ordering, P.canon_min) + 1u;
       }
     }
-    rk0[iq] = r;
+    rk0[iq] = key;
   }
 
-  // sliding minimum over w ranks: after the loop A[i] = min(rank[i .. i+span)).
+  // sliding minimum over w keys: after the loop A[i] = min(key[i .. i+span)).
   uint32_t* A = rk0;
   uint32_t* B = rk1;
   int len = NQ, span = 1;
@@ -174,17 +175,17 @@ __global__ void __launch_bounds__(256) supermer_kernel(SupermerParams P) {
     B = t;
   }
   __syncthreads();
-  uint32_t* M = B;  // window minima
+  uint32_t* M = B;  // window minima: 0 = window not counted, else 1 + minimizer rank
   for (int i = threadIdx.x; i < NW; i += blockDim.x) {
-    M[i] = min(A[i], A[i + w - span]);
+    const uint32_t mk = min(A[i], A[i + w - span]);
+    M[i] = mk;
     const long long p = O + i;
-    bool ok = p >= 0 && p < nwin;
-    if (ok) {
+    bool ok = p >= 0 && p < nwin && mk != 0u;
+    if (ok && m == 1) {  // m = 1: no m-mer straddles a read start, test the window itself
       const int lb = lbO + i;
-      ok = (bits32(snm, lb) >> 31) == 0u;  // base p determined
-      for (int c = 1; ok && c < k; c += 32) {  // no N and no read start in (p, p+k)
+      for (int c = 1; ok && c < k; c += 32) {
         const int l = min(32, k - c);
-        ok = (bits32(scm, lb + c) >> (32 - l)) == 0u;
+        ok = (bits32(sbm, lb + c) >> (32 - l)) == 0u;
       }
     }
     V[i] = ok;
@@ -194,14 +195,11 @@ __global__ void __launch_bounds__(256) supermer_kernel(SupermerParams P) {
   // super-mer starts and boundaries as bit masks (one ballot per 32 windows): window i starts
   // a super-mer if it is counted and its predecessor is not, or has another minimizer, or i
   // sits on a multiple of L_max; a boundary is a start or an uncounted window.
-  const int nbw = (NW + 31) >> 5;
-  uint32_t* SB = reinterpret_cast<uint32_t*>(V + ((NW + 15) & ~15));
-  uint32_t* BB = SB + nbw;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
   {
     const long long Omod = ((O % lmax) + lmax) % lmax;
     const uint32_t lm = (uint32_t)lmax;
     const bool pow2 = (lm & (lm - 1)) == 0;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
     for (int w0 = warp * 32; w0 < nbw * 32; w0 += nwarp * 32) {
       const int i = w0 + lane;
       bool st = false, bd = true;
@@ -221,47 +219,70 @@ __global__ void __launch_bounds__(256) supermer_kernel(SupermerParams P) {
   }
   __syncthreads();
 
-  const uint32_t vmask = (2 * m >= 32) ? 0xFFFFFFFFu : ((1u << (2 * m)) - 1u);
+  const uint32_t vmask = (1u << (2 * m)) - 1u;
   const int own = (int)(P1 - P0);
-  for (int i = 1 + threadIdx.x; i <= own; i += blockDim.x) {
-    if (!((SB[i >> 5] >> (i & 31)) & 1u)) continue;
-    const long long p = O + i;
-    const uint32_t mi = M[i];
-    // end = first boundary after i (a cut every L_max windows bounds the search)
-    int j = i + 1, end = NW;
-    for (int wj = j >> 5; wj < nbw; ++wj) {
-      const uint32_t bits = BB[wj] & (wj == (j >> 5) ? (0xFFFFFFFFu << (j & 31)) : 0xFFFFFFFFu);
-      if (bits) {
-        end = min(NW, (wj << 5) + __ffs(bits) - 1);
-        break;
+  for (int base = 0; base < own; base += blockDim.x) {  // uniform trip count (ballots inside)
+    const int i = 1 + base + threadIdx.x;
+    const bool is_start = i <= own && ((SB[i >> 5] >> (i & 31)) & 1u);
+    uint32_t nk = 0, bin = 0;
+    if (is_start) {
+      // end = first boundary after i (a cut every L_max windows bounds the search)
+      const int j = i + 1;
+      int end = NW;
+      for (int wj = j >> 5; wj < nbw; ++wj) {
+        const uint32_t bits = BB[wj] & (wj == (j >> 5) ? (0xFFFFFFFFu << (j & 31)) : 0xFFFFFFFFu);
+        if (bits) {
+          end = min(NW, (wj << 5) + __ffs(bits) - 1);
+          break;
+        }
       }
-    }
-    const uint32_t nk = (uint32_t)(end - i);
-    const uint32_t h = fmix32(mi & vmask);
-    uint32_t bin;
-    if (P.bounds) {
-      uint32_t lo = 0, hi = P.nbins - 1;  // number of split points <= h
-      while (lo < hi) {
-        const uint32_t mid = (lo + hi) >> 1;
-        if (__ldg(P.bounds + mid) <= h) lo = mid + 1; else hi = mid;
+      nk = (uint32_t)(end - i);
+      const uint32_t h = fmix32((M[i] - 1u) & vmask);
+      if (P.bounds) {
+        uint32_t lo = 0, hi = P.nbins - 1;  // number of split points <= h
+        while (lo < hi) {
+          const uint32_t mid = (lo + hi) >> 1;
+          if (__ldg(P.bounds + mid) <= h) lo = mid + 1; else hi = mid;
+        }
+        bin = lo;
+      } else {
+        bin = h % P.nbins;
       }
-      bin = lo;
-    } else {
-      bin = h % P.nbins;
-    }
-    if (PASS == 0) {
       atomicAdd(P.bin_nsuper + bin, 1ull);
       atomicAdd(P.bin_nkmers + bin, (unsigned long long)nk);
-    } else {
-      const unsigned long long old = atomicAdd(P.bin_cursor + bin, (1ull << 32) | nk);
-      if ((old >> 32) >= P.bin_nsuper[bin]) {  // the two passes disagree: never expected
-        atomicOr(P.err, ERR_STATE);
-        continue;
-      }
-      const unsigned long long idx = P.bin_sm_begin[bin] + (old >> 32);
-      P.sm_pos[idx] = (unsigned long long)p;
-      P.sm_koff[idx] = (uint32_t)old;
     }
+    const uint32_t bal = __ballot_sync(0xFFFFFFFFu, is_start);
+    if (bal) {
+      unsigned long long rbase = 0;
+      if (lane == 0) rbase = atomicAdd(P.rec_count, (unsigned long long)__popc(bal));
+      rbase = __shfl_sync(0xFFFFFFFFu, rbase, 0);
+      if (is_start) {
+        const unsigned long long idx = rbase + __popc(bal & ((1u << lane) - 1u));
+        if (idx < P.rec_cap) {
+          P.rec[idx] = make_ulonglong2((unsigned long long)(O + i),
+                                       ((unsigned long long)bin << 32) | nk);
+        }
+      }
+    }
+  }
+}
+
+// Scatter of the records into their bins.  One 64-bit atomic per record takes both the
+// super-mer's index and its first k-mer within the bin, so that within a bin super-mer order
+// and k-mer order agree.
+__global__ void __launch_bounds__(256) scatter_kernel(SupermerParams P, unsigned long long nrec) {
+  for (unsigned long long r = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; r < nrec;
+       r += (unsigned long long)gridDim.x * blockDim.x) {
+    const ulonglong2 rec = P.rec[r];
+    const uint32_t bin = (uint32_t)(rec.y >> 32), nk = (uint32_t)rec.y;
+    const unsigned long long old = atomicAdd(P.bin_cursor + bin, (1ull << 32) | nk);
+    if ((old >> 32) >= P.bin_nsuper[bin]) {  // never expected
+      atomicOr(P.err, ERR_STATE);
+      continue;
+    }
+    const unsigned long long idx = P.bin_sm_begin[bin] + (old >> 32);
+    P.sm_pos[idx] = rec.x;
+    P.sm_koff[idx] = (uint32_t)old;
   }
 }
 
@@ -290,17 +311,21 @@ cudaError_t launch_boundary(const uint64_t* offsets, uint64_t nreads, uint64_t n
   return cudaGetLastError();
 }
 
-cudaError_t launch_supermer(const SupermerParams& p, int pass, cudaStream_t st) {
+cudaError_t launch_supermer(const SupermerParams& p, cudaStream_t st) {
   if (p.nwin == 0) return cudaSuccess;
   const uint64_t blocks = (p.nwin + p.tile - 1) / p.tile;
   const size_t smem = supermer_smem_bytes(p.tile, p.lmax, p.k);
-  if (pass == 0) {
-    cudaFuncSetAttribute(supermer_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    supermer_kernel<0><<<(unsigned)blocks, 256, smem, st>>>(p);
-  } else {
-    cudaFuncSetAttribute(supermer_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    supermer_kernel<1><<<(unsigned)blocks, 256, smem, st>>>(p);
-  }
+  cudaError_t e = cudaFuncSetAttribute(supermer_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  supermer_kernel<<<(unsigned)blocks, 256, smem, st>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scatter(const SupermerParams& p, unsigned long long nrec, int nsm, cudaStream_t st) {
+  if (nrec == 0) return cudaSuccess;
+  const unsigned blocks = (unsigned)std::min<unsigned long long>((nrec + 255) / 256, (unsigned long long)nsm * 8);
+  scatter_kernel<<<blocks, 256, 0, st>>>(p, nrec);
   return cudaGetLastError();
 }
 

@@ -346,6 +346,8 @@ int gerbil_partition(gerbil_ctx* ctx, const gerbil_reads* reads, int k, int m, i
   uint32_t* bmask = nullptr;
   uint32_t* dbounds = nullptr;
   unsigned long long* binbuf = nullptr;  // nsuper, nkmers, cursor, sm_begin
+  unsigned long long* rec = nullptr;     // super-mer records
+  uint64_t rec_cap = 0, nrec = 0;
   size_t seq_bytes = 0, off_bytes = 0, mask_bytes = 0, bounds_bytes = 0, binbuf_bytes = 0;
   std::vector<unsigned long long> hbin;
   int rc = GERBIL_OK;
@@ -356,6 +358,7 @@ int gerbil_partition(gerbil_ctx* ctx, const gerbil_reads* reads, int k, int m, i
     dev_free(ctx, bmask, mask_bytes);
     dev_free(ctx, dbounds, bounds_bytes);
     dev_free(ctx, binbuf, binbuf_bytes);
+    dev_free(ctx, rec, rec_cap * 16);
   };
 #define TRY(x)                      \
   do {                              \
@@ -390,7 +393,7 @@ int gerbil_partition(gerbil_ctx* ctx, const gerbil_reads* reads, int k, int m, i
   TRY(dev_alloc(ctx, (void**)&b->packed, b->packed_bytes));
   TRY(dev_alloc(ctx, (void**)&nmask, mask_bytes));
   TRY(dev_alloc(ctx, (void**)&bmask, mask_bytes));
-  binbuf_bytes = (size_t)nbins * 4 * 8 + 16;  // + error word
+  binbuf_bytes = (size_t)nbins * 4 * 8 + 16;  // + error word + record count
   TRY(dev_alloc(ctx, (void**)&binbuf, binbuf_bytes));
   TRYCU(cudaMemsetAsync(binbuf, 0, binbuf_bytes, st));
   TRYCU(cudaMemsetAsync(b->packed + b->nwords, 0, 16, st));
@@ -408,6 +411,7 @@ int gerbil_partition(gerbil_ctx* ctx, const gerbil_reads* reads, int k, int m, i
   TRYCU(gerbil::launch_encode(seq, n, b->packed, nmask, b->nwords, vec_ok, ctx->nsm, st));
   ctx->times.kernel_launches++;
   unsigned int* perr = (unsigned int*)(binbuf + 4 * (size_t)nbins);
+  unsigned long long* rec_count = binbuf + 4 * (size_t)nbins + 1;
   if (nreads > 0) {
     TRYCU(gerbil::launch_boundary(offsets, nreads, n, bmask, perr, st));
     ctx->times.kernel_launches++;
@@ -434,17 +438,40 @@ int gerbil_partition(gerbil_ctx* ctx, const gerbil_reads* reads, int k, int m, i
   sp.bin_cursor = binbuf + 2 * nbins;
   sp.bin_sm_begin = binbuf + 3 * nbins;
   sp.err = perr;
-  ph_begin(ctx, PH_SUPER0);
-  TRYCU(gerbil::launch_supermer(sp, 0, st));
-  if (sp.nwin) ctx->times.kernel_launches++;
-  ph_end(ctx, PH_SUPER0);
-
-  hbin.resize((size_t)nbins * 2);
-  TRYCU(cudaMemcpyAsync(hbin.data(), binbuf, (size_t)nbins * 16, cudaMemcpyDeviceToHost, st));
-  TRYCU(cudaMemcpyAsync(ctx->hctr, perr, 4, cudaMemcpyDeviceToHost, st));
-  TRYCU(cudaStreamSynchronize(st));
-  ph_collect(ctx, false);
-  if (*(unsigned int*)ctx->hctr) TRY(fail(ctx, GERBIL_E_INVAL, "offsets out of order or past the input"));
+  sp.rec_count = rec_count;
+  // record area: random minimizers give about 2/(w+1) super-mers per window, plus one per
+  // read; four times that, and a rerun with the exact size if it is ever exceeded
+  {
+    const uint64_t w = (uint64_t)(k - m + 1);
+    uint64_t est = sp.nwin * 4 / (w + 1) + 2 * nreads + 65536;
+    rec_cap = std::min<uint64_t>(est, sp.nwin + 1);
+  }
+  TRY(dev_alloc(ctx, (void**)&rec, rec_cap * 16));
+  hbin.resize((size_t)nbins * 2 + 2);
+  for (int attempt = 0;; ++attempt) {
+    sp.rec = (ulonglong2*)rec;
+    sp.rec_cap = rec_cap;
+    ph_begin(ctx, PH_SUPER0);
+    TRYCU(gerbil::launch_supermer(sp, st));
+    if (sp.nwin) ctx->times.kernel_launches++;
+    ph_end(ctx, PH_SUPER0);
+    TRYCU(cudaMemcpyAsync(hbin.data(), binbuf, (size_t)nbins * 16, cudaMemcpyDeviceToHost, st));
+    TRYCU(cudaMemcpyAsync(hbin.data() + 2 * (size_t)nbins, binbuf + 4 * (size_t)nbins, 16,
+                          cudaMemcpyDeviceToHost, st));
+    TRYCU(cudaStreamSynchronize(st));
+    ph_collect(ctx, false);
+    if ((uint32_t)hbin[2 * (size_t)nbins])
+      TRY(fail(ctx, GERBIL_E_INVAL, "offsets out of order or past the input"));
+    nrec = hbin[2 * (size_t)nbins + 1];
+    if (nrec <= rec_cap) break;
+    if (attempt > 0) TRY(fail(ctx, GERBIL_E_STATE, "super-mer record count changed between runs"));
+    dev_free(ctx, rec, rec_cap * 16);
+    rec = nullptr;
+    rec_cap = nrec;
+    TRY(dev_alloc(ctx, (void**)&rec, rec_cap * 16));
+    TRYCU(cudaMemsetAsync(binbuf, 0, (size_t)nbins * 16, st));
+    TRYCU(cudaMemsetAsync(rec_count, 0, 8, st));
+  }
   uint64_t acc = 0;
   for (int i = 0; i < nbins; ++i) {
     b->nsuper[i] = hbin[i];
@@ -456,7 +483,7 @@ int gerbil_partition(gerbil_ctx* ctx, const gerbil_reads* reads, int k, int m, i
   }
   b->sm_begin[nbins] = acc;
   b->n_super_total = acc;
-  b->sm_bytes = acc * 12 + 16;
+  if (acc != nrec) TRY(fail(ctx, GERBIL_E_STATE, "record and bin counts disagree"));
   TRY(dev_alloc(ctx, (void**)&b->sm_pos, acc * 8 + 8));
   TRY(dev_alloc(ctx, (void**)&b->sm_koff, acc * 4 + 8));
   {
@@ -467,12 +494,12 @@ int gerbil_partition(gerbil_ctx* ctx, const gerbil_reads* reads, int k, int m, i
   sp.sm_pos = b->sm_pos;
   sp.sm_koff = b->sm_koff;
   ph_begin(ctx, PH_SUPER1);
-  TRYCU(gerbil::launch_supermer(sp, 1, st));
-  if (sp.nwin) ctx->times.kernel_launches++;
+  TRYCU(gerbil::launch_scatter(sp, nrec, ctx->nsm, st));
+  if (nrec) ctx->times.kernel_launches++;
   ph_end(ctx, PH_SUPER1);
   TRYCU(cudaMemcpyAsync(ctx->hctr, perr, 4, cudaMemcpyDeviceToHost, st));
   TRYCU(cudaStreamSynchronize(st));
-  if (*(unsigned int*)ctx->hctr) TRY(fail(ctx, GERBIL_E_STATE, "phase-one passes disagree"));
+  if (*(unsigned int*)ctx->hctr) TRY(fail(ctx, GERBIL_E_STATE, "scatter overran a bin"));
   cleanup();
   *out = b;
   return GERBIL_OK;
@@ -553,7 +580,7 @@ static int count_impl(gerbil_ctx* ctx, const gerbil_bins* b, const std::vector<i
     // table sizing per bin (Sec. 3.4: expected distinct = ratio x k-mers of the file)
     std::vector<BinWork> work;
     work.reserve(list.size());
-    uint64_t slots = 0, tiles = 0;
+    uint64_t slots = 0, items = 0;
     for (int32_t bi : list) {
       if (b->nkmers[bi] == 0) continue;
       BinWork w{};
@@ -565,22 +592,24 @@ static int count_impl(gerbil_ctx* ctx, const gerbil_bins* b, const std::vector<i
       cap = std::min<uint64_t>(cap, 0xFFFFFFF0ull);
       w.cap = (uint32_t)cap;
       w.table_off = slots;
-      w.tile_begin = (uint32_t)tiles;
+      w.item_begin = (uint32_t)items;
       slots += cap;
-      tiles += (w.n_kmers + gerbil::COUNT_TILE - 1) / gerbil::COUNT_TILE;
+      items += (w.n_kmers + gerbil::ITEM_KMERS - 1) / gerbil::ITEM_KMERS;
       work.push_back(w);
     }
-    if (tiles >= (1ull << 32)) return fail(ctx, GERBIL_E_INVAL, "too many tiles");
+    if (items >= (1ull << 32)) return fail(ctx, GERBIL_E_INVAL, "too many work items");
     // the overflow area grows 4x per retry (a caller-given size is the starting size)
     const uint64_t ovf_cap = (opts.overflow_slots ? (uint64_t)opts.overflow_slots
                                                   : std::max<uint64_t>(1 << 16, occ / 32))
                              << (2 * round);
-    const size_t arena_need = slots * (W + 1) * 8;
+    const int SWk = gerbil::slot_words_for_k(k);
+    const size_t arena_need = slots * SWk * 8;
     int rc;
     if ((rc = scratch(ctx, &ctx->arena, &ctx->arena_bytes, arena_need + 256))) return rc;
     if ((rc = scratch(ctx, &ctx->ovf, &ctx->ovf_bytes, ovf_cap * W * 8 + 256))) return rc;
     const size_t work_bytes = work.size() * sizeof(BinWork);
-    const size_t small_need = work_bytes + work.size() * 4 + 512;
+    const size_t small_need = ((work_bytes + 255) & ~size_t(255)) + ((work.size() * 4 + 255) & ~size_t(255)) +
+                              items * 8 + 512;
     if ((rc = scratch(ctx, &ctx->small, &ctx->small_bytes, small_need))) return rc;
     BinWork* dwork = (BinWork*)ctx->small;
     uint32_t* bin_ovf = (uint32_t*)((char*)ctx->small + ((work_bytes + 255) & ~size_t(255)));
@@ -616,7 +645,6 @@ static int count_impl(gerbil_ctx* ctx, const gerbil_bins* b, const std::vector<i
       CKR(cudaMemcpyAsync(dwork, work.data(), work_bytes, cudaMemcpyHostToDevice, st));
       CKR(cudaMemsetAsync(bin_ovf, 0, work.size() * 4, st));
     }
-    ph_end(ctx, PH_CLEAR);
 
     gerbil::CountParams cp{};
     cp.packed = b->packed;
@@ -624,8 +652,8 @@ static int count_impl(gerbil_ctx* ctx, const gerbil_bins* b, const std::vector<i
     cp.sm_koff = b->sm_koff;
     cp.work = dwork;
     cp.nwork = (uint32_t)work.size();
-    cp.ntiles = (uint32_t)tiles;
-    cp.tile_base = 0;
+    cp.nitems = items;
+    cp.imap = (unsigned long long*)((char*)bin_ovf + ((work.size() * 4 + 255) & ~size_t(255)));
     cp.k = k;
     cp.canonical = opts.canonical ? 1 : 0;
     cp.theta = theta;
@@ -635,16 +663,16 @@ static int count_impl(gerbil_ctx* ctx, const gerbil_bins* b, const std::vector<i
     cp.ovf_cap = ovf_cap;
     cp.bin_ovf = bin_ovf;
     cp.ctr = ctx->ctr;
+    if (items) {
+      CKR(gerbil::launch_item_map(cp, st));  // preparation: timed with the clears
+      ctx->times.kernel_launches++;
+    }
+    ph_end(ctx, PH_CLEAR);
     ph_begin(ctx, PH_INSERT);
-    if (tiles) {
+    if (items) {
+      CKR(gerbil::launch_insert(k, cp, opts.persistent, ctx->nsm, st));
       ctx->times.kernel_launches++;
       ctx->times.insert_launches++;
-      if (opts.persistent) {
-        const unsigned grid = (unsigned)std::min<uint64_t>(tiles, (uint64_t)ctx->nsm * ctx->insert_ctas_per_sm);
-        CKR(gerbil::launch_insert_persistent(W, cp, grid, st));
-      } else {
-        CKR(gerbil::launch_insert(W, cp, (unsigned)tiles, st));
-      }
     }
     ph_end(ctx, PH_INSERT);
     gerbil::CompactParams xp{};
@@ -661,7 +689,7 @@ static int count_impl(gerbil_ctx* ctx, const gerbil_bins* b, const std::vector<i
     xp.out_cap = out_cap;
     xp.ctr = ctx->ctr;
     ph_begin(ctx, PH_COMPACT);
-    CKR(gerbil::launch_compact(W, xp, ctx->nsm, st));
+    CKR(gerbil::launch_compact(k, xp, ctx->nsm, st));
     if (slots) ctx->times.kernel_launches++;
     ph_end(ctx, PH_COMPACT);
     if ((rc = read_counters(ctx))) { drop(); return rc; }
@@ -683,7 +711,7 @@ static int count_impl(gerbil_ctx* ctx, const gerbil_bins* b, const std::vector<i
       if (ocap64 >= 0xFFFFFFF0ull) { drop(); return fail(ctx, GERBIL_E_OVERFLOW, "overflow too large"); }
       const uint32_t ocap = (uint32_t)ocap64;
       void* otab = nullptr;
-      const size_t obytes = (size_t)ocap * (W + 1) * 8;
+      const size_t obytes = (size_t)ocap * SWk * 8;
       if ((rc = dev_alloc(ctx, &otab, obytes))) { drop(); return rc; }
       CKR(cudaMemsetAsync(otab, 0, obytes, st));
       gerbil::OverflowParams op{};
@@ -698,12 +726,12 @@ static int count_impl(gerbil_ctx* ctx, const gerbil_bins* b, const std::vector<i
       op.out_cap = out_cap;
       op.ctr = ctx->ctr;
       ph_begin(ctx, PH_OVERFLOW);
-      CKR(gerbil::launch_overflow_insert(W, op, ctx->nsm, st));
+      CKR(gerbil::launch_overflow_insert(k, op, ctx->nsm, st));
       xp.mode = 1;
       xp.otab = op.otab;
       xp.ocap = ocap;
-      CKR(gerbil::launch_compact(W, xp, ctx->nsm, st));
-      CKR(gerbil::launch_overflow_emit(W, op, ctx->nsm, st));
+      CKR(gerbil::launch_compact(k, xp, ctx->nsm, st));
+      CKR(gerbil::launch_overflow_emit(k, op, ctx->nsm, st));
       ctx->times.kernel_launches += 3;
       ph_end(ctx, PH_OVERFLOW);
       rc = read_counters(ctx);
