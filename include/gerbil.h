@@ -96,9 +96,16 @@ typedef struct gerbil_opts {
                                   (Sec. 3.4 "Estimating table sizes"); 0: use the ratio the
                                   context measured on earlier calls (1.0 at first) */
   uint32_t overflow_slots;     /* capacity of the overflow area in k-mers; 0: automatic */
-  int32_t persistent;          /* count_batch: 1 = one persistent launch with a work queue
-                                  (default), 0 = one grid over all tiles */
-  uint32_t reserved[6];
+  int32_t persistent;          /* 1 (default): the insert kernel runs as many CTAs as fit on
+                                  the GPU at once, each warp striding over the work items of
+                                  all bins in bin order; 0: one warp per work item */
+  uint32_t ring_slots;         /* fused form: table slots of the ring (0: 60% of L2) */
+  int32_t fused;               /* 1: one kernel pops insert and compaction tasks of all bins
+                                  from a device queue, with the tables of small bins in an
+                                  L2-sized ring that is reused bin after bin; 0 (default):
+                                  separate insert and compaction kernels over tables that all
+                                  stay allocated until the compaction */
+  uint32_t reserved[4];
 } gerbil_opts;
 
 /* Per-call statistics of a count. */

@@ -18,17 +18,16 @@ namespace gerbil {
 // area, which is always correct because overflow counts are added to table counts before
 // the min_count filter.
 template <int WS>
-__device__ __forceinline__ int table_insert(unsigned long long* __restrict__ tab, uint32_t cap,
-                                            const unsigned long long st[WS], unsigned long long h,
-                                            uint32_t theta, uint32_t spin_limit) {
+__device__ __forceinline__ int table_insert_from(unsigned long long* __restrict__ tab, uint32_t cap,
+                                                 const unsigned long long st[WS], unsigned long long h,
+                                                 uint32_t theta, uint32_t spin_limit, uint32_t s,
+                                                 unsigned long long v[slot_words(WS)]) {
   constexpr int SW = slot_words(WS);
-  uint32_t s = (uint32_t)(((h & 0xFFFFFFFFull) * (unsigned long long)cap) >> 32);
   const uint32_t tagw = META_CLAIMED | (uint32_t)((h >> 34) & META_TAG_MASK);
   const unsigned long long claim = ((unsigned long long)tagw << 32) | 1ull;
   for (uint32_t t = 0; t < theta; ++t) {
     unsigned long long* slot = tab + (unsigned long long)s * SW;
-    unsigned long long v[SW];
-    load_slot<SW>(slot, v);
+    if (t > 0) load_slot<SW>(slot, v);
     if (v[0] == 0ull) {
       const unsigned long long old = cas_relaxed(slot, 0ull, claim);
       if (old == 0ull) {
@@ -69,6 +68,21 @@ __device__ __forceinline__ int table_insert(unsigned long long* __restrict__ tab
     s = (s + 1 == cap) ? 0u : s + 1;
   }
   return 1;
+}
+
+__device__ __forceinline__ uint32_t slot_of(unsigned long long h, uint32_t cap) {
+  return (uint32_t)(((h & 0xFFFFFFFFull) * (unsigned long long)cap) >> 32);
+}
+
+template <int WS>
+__device__ __forceinline__ int table_insert(unsigned long long* __restrict__ tab, uint32_t cap,
+                                            const unsigned long long st[WS], unsigned long long h,
+                                            uint32_t theta, uint32_t spin_limit) {
+  constexpr int SW = slot_words(WS);
+  const uint32_t s = slot_of(h, cap);
+  unsigned long long v[SW];
+  load_slot<SW>(tab + (unsigned long long)s * SW, v);
+  return table_insert_from<WS>(tab, cap, st, h, theta, spin_limit, s, v);
 }
 
 // Lookup in a complete table (no concurrent inserts); marks the slot MERGED and returns its
@@ -133,17 +147,17 @@ __global__ void __launch_bounds__(256) item_map_kernel(const BinWork* __restrict
   }
 }
 
+constexpr int PIPE = 1;  // k-mers per lane whose probes are in flight together
+
 struct WarpSmem {
   uint32_t koff[ITEM_KMERS];
   unsigned long long pos[ITEM_KMERS];
 };
 
 template <int W, int WS>
-__device__ __forceinline__ void count_item(const CountParams& P, unsigned long long item,
-                                           unsigned long long entry, WarpSmem& S, int lane) {
-  const uint32_t wi = (uint32_t)(entry >> 32), s_lo = (uint32_t)entry;
-  const BinWork wk = P.work[wi];
-  const uint32_t j0 = (uint32_t)(item - wk.item_begin) * ITEM_KMERS;
+__device__ __forceinline__ void insert_item(const CountParams& P, uint32_t wi, const BinWork& wk,
+                                            uint32_t it, uint32_t s_lo, WarpSmem& S, int lane) {
+  const uint32_t j0 = it * ITEM_KMERS;
   const uint32_t j1 = min(j0 + (uint32_t)ITEM_KMERS, wk.n_kmers);
   const uint32_t* koff = P.sm_koff + wk.sm_begin;
   const unsigned long long* spos = P.sm_pos + wk.sm_begin;
@@ -166,34 +180,61 @@ __device__ __forceinline__ void count_item(const CountParams& P, unsigned long l
     if (cnt < 32) break;
   }
   __syncwarp();
-  unsigned long long* tab = P.arena + wk.table_off * slot_words(WS);
+  // a lane's k-mers in groups of PIPE: keys, hashes and the first probe of a group are all
+  // issued before any of them is resolved, so their memory latencies overlap
+  constexpr int SW = slot_words(WS);
+  unsigned long long* tab = P.arena + wk.table_off * SW;
 #pragma unroll 1
-  for (int r = 0; r < ITEM_KMERS / 32; ++r) {
-    const uint32_t j = j0 + lane + 32 * r;
-    if (j >= j1) break;
-    uint32_t lo = 0, hi = ns;
-    while (hi - lo > 1) {
-      const uint32_t mid = (lo + hi) >> 1;
-      if (S.koff[mid] <= j) lo = mid; else hi = mid;
-    }
-    const unsigned long long pos = S.pos[lo] + (j - S.koff[lo]);
-    unsigned long long key[W];
-    load_kmer<W>(P.packed, pos, P.k, key);
-    if (P.canonical) {
-      unsigned long long rc[W];
-      revcomp<W>(key, P.k, rc);
-      if (key_less<W>(rc, key)) {
+  for (int r0 = 0; r0 < ITEM_KMERS / 32; r0 += PIPE) {
+    unsigned long long st[PIPE][WS], h[PIPE], v[PIPE][SW];
+    uint32_t s0[PIPE];
+    bool val[PIPE];
 #pragma unroll
-        for (int q = 0; q < W; ++q) key[q] = rc[q];
+    for (int p = 0; p < PIPE; ++p) {
+      const uint32_t j = j0 + lane + 32 * (r0 + p);
+      val[p] = j < j1;
+      if (!val[p]) continue;
+      uint32_t lo = 0, hi = ns;
+      while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (S.koff[mid] <= j) lo = mid; else hi = mid;
+      }
+      const unsigned long long pos = S.pos[lo] + (j - S.koff[lo]);
+      unsigned long long key[W];
+      load_kmer<W>(P.packed, pos, P.k, key);
+      if (P.canonical) {
+        unsigned long long rc[W];
+        revcomp<W>(key, P.k, rc);
+        if (key_less<W>(rc, key)) {
+#pragma unroll
+          for (int q = 0; q < W; ++q) key[q] = rc[q];
+        }
+      }
+      h[p] = key_hash<W>(key);
+      to_stored<W, WS>(key, st[p]);
+      s0[p] = slot_of(h[p], wk.cap);
+      load_slot<SW>(tab + (unsigned long long)s0[p] * SW, v[p]);
+    }
+#pragma unroll
+    for (int p = 0; p < PIPE; ++p) {
+      if (!val[p]) continue;
+      const int res = table_insert_from<WS>(tab, wk.cap, st[p], h[p], P.theta, P.spin_limit, s0[p], v[p]);
+      if (res) {
+        unsigned long long key[W];
+        from_stored<W, WS>(st[p], key);
+        to_overflow<W>(P, wi, key, res);
       }
     }
-    const unsigned long long h = key_hash<W>(key);
-    unsigned long long st[WS];
-    to_stored<W, WS>(key, st);
-    const int res = table_insert<WS>(tab, wk.cap, st, h, P.theta, P.spin_limit);
-    if (res) to_overflow<W>(P, wi, key, res);
   }
   __syncwarp();  // S is reused by the next item
+}
+
+template <int W, int WS>
+__device__ __forceinline__ void count_item(const CountParams& P, unsigned long long item,
+                                           unsigned long long entry, WarpSmem& S, int lane) {
+  const uint32_t wi = (uint32_t)(entry >> 32), s_lo = (uint32_t)entry;
+  const BinWork wk = P.work[wi];
+  insert_item<W, WS>(P, wi, wk, (uint32_t)(item - wk.item_begin), s_lo, S, lane);
 }
 
 // Warps stride over the items in bin order, so the bins in flight at any moment are few and
@@ -360,6 +401,167 @@ __device__ __forceinline__ void emit_rows(bool emit, const unsigned long long ke
   }
 }
 
+// ---- fused persistent phase two --------------------------------------------------------------
+// One queue holds, in bin order, the insert items of bin b followed by the compaction chunks of
+// bin b-1.  Warps pop tasks; a compaction chunk waits (bounded) until every insert item of its
+// bin is done, an insert item waits until the bin that used its table region before has been
+// compacted.  Both waits are on tasks that were popped earlier by running warps, so they end.
+// Tables of small bins live in a ring that fits in L2; compaction zeroes every slot it reads,
+// so a region is clean when the next bin takes it, and the whole arena is zero after a call.
+
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Lane 0 waits with acquire loads until *ctr >= target (bounded by wait_ns; on timeout the
+// error is recorded and the wait ends).
+__device__ __forceinline__ void warp_wait_at_least(const uint32_t* ctr, uint32_t target,
+                                                   unsigned long long wait_ns, Counters* c, int lane) {
+  if (lane == 0 && ld_acquire_u32(ctr) < target) {  // (the acquire orders lane 0's loads)
+    const unsigned long long t0 = globaltimer_ns();
+    unsigned ns = 32;
+    while (ld_acquire_u32(ctr) < target) {
+      if (globaltimer_ns() - t0 > wait_ns) {
+        set_err(c, ERR_QUEUE);
+        break;
+      }
+      __nanosleep(ns);
+      if (ns < 1024) ns *= 2;
+    }
+  }
+  // the other lanes are ordered after lane 0's acquire by the warp barrier
+  __syncwarp();
+}
+
+// Every lane makes its writes visible, then lane 0 counts the task as done.
+__device__ __forceinline__ void warp_signal(uint32_t* ctr, int lane) {
+  __threadfence();
+  __syncwarp();
+  if (lane == 0) atomicAdd(ctr, 1u);
+}
+
+__device__ __forceinline__ uint32_t warp_excl_scan(uint32_t x, int lane, uint32_t* total) {
+  uint32_t incl = x;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  *total = __shfl_sync(0xFFFFFFFFu, incl, 31);
+  return incl - x;
+}
+
+// One compaction chunk: count the rows (meta words only), take room for them with one atomic,
+// then write them and zero the live slots.
+template <int W, int WS>
+__device__ __forceinline__ void compact_chunk(const FusedParams& F, const BinWork& wk, uint32_t c,
+                                              int lane) {
+  constexpr int SW = slot_words(WS);
+  unsigned long long* tab = F.c.arena + wk.table_off * SW;
+  const uint32_t lo = c * CHUNK_SLOTS, hi = min(lo + (uint32_t)CHUNK_SLOTS, wk.cap);
+  uint32_t mine = 0, live = 0;
+  for (uint32_t s = lo + lane; s < hi; s += 32) {
+    const unsigned long long mt = ld_relaxed(tab + (unsigned long long)s * SW);
+    live += mt != 0ull;
+    mine += (mt != 0ull && (uint32_t)mt >= F.min_count);
+  }
+  uint32_t total = 0, tlive = 0;
+  const uint32_t excl = warp_excl_scan(mine, lane, &total);
+  (void)warp_excl_scan(live, lane, &tlive);
+  unsigned long long base = 0;
+  if (lane == 0) {
+    if (total) base = atomicAdd(&F.c.ctr->out_count, (unsigned long long)total);
+    if (tlive) atomicAdd(&F.c.ctr->distinct, (unsigned long long)tlive);
+  }
+  unsigned long long row = __shfl_sync(0xFFFFFFFFu, base, 0) + excl;
+  for (uint32_t s = lo + lane; s < hi; s += 32) {
+    unsigned long long* sp = tab + (unsigned long long)s * SW;
+    unsigned long long v[SW];
+    load_slot<SW>(sp, v);
+    if (v[0] == 0ull) continue;
+    bool all = true;
+#pragma unroll
+    for (int j = 0; j < WS; ++j) all &= (v[1 + j] & MARK) != 0ull;
+    if (!all) set_err(F.c.ctr, ERR_STATE);  // a claimed slot whose key was never written
+    if ((uint32_t)v[0] >= F.min_count) {
+      if (row < F.out_cap) {
+        unsigned long long key[W];
+        from_stored<W, WS>(&v[1], key);
+#pragma unroll
+        for (int j = 0; j < W; ++j) F.out_keys[row * W + j] = key[j];
+        F.out_counts[row] = (uint32_t)v[0];
+      } else {
+        set_err(F.c.ctr, ERR_OUT_FULL);
+      }
+      ++row;
+    }
+#pragma unroll
+    for (int i = 0; i < SW; i += 2) st_relaxed_v2(sp + i, 0ull, 0ull);
+  }
+}
+
+template <int W, int WS>
+__global__ void __launch_bounds__(256) fused_kernel(FusedParams F) {
+  __shared__ WarpSmem S[8];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  unsigned long long* queue = F.queue;
+  uint32_t checked = 0xFFFFFFFFu;  // bin whose dependencies this warp has seen complete
+  unsigned long long t = 0;
+  if (lane == 0) t = atomicAdd(queue, 1ull);
+  t = __shfl_sync(0xFFFFFFFFu, t, 0);
+  // a warp holds its current task and the next one, whose atomic is in flight meanwhile; a
+  // task only ever waits on tasks queued before it, so holding a later one cannot block
+  for (;;) {
+    if (t >= F.ntasks) break;
+    unsigned long long t_next = 0;
+    if (lane == 0) t_next = atomicAdd(queue, 1ull);
+    const unsigned long long e = __ldg(F.tasks + t);
+    const uint32_t wi = (uint32_t)(e >> 32) & 0x7FFFFFFFu, pay = (uint32_t)e;
+    const BinWork wk = F.c.work[wi];
+    if (!(e >> 63)) {
+      if (wi != checked) {  // completed dependencies stay complete
+        for (uint32_t d = 0; d < wk.dep_count; ++d) {
+          const uint32_t dw = __ldg(F.deps + wk.dep_begin + d);
+          warp_wait_at_least(F.chunks_done + dw, F.c.work[dw].n_chunks, F.wait_ns, F.c.ctr, lane);
+        }
+        checked = wi;
+      }
+      insert_item<W, WS>(F.c, wi, wk, (uint32_t)(t - wk.task_insert), pay, S[warp], lane);
+      warp_signal(F.items_done + wi, lane);
+    } else {
+      warp_wait_at_least(F.items_done + wi, wk.n_items, F.wait_ns, F.c.ctr, lane);
+      compact_chunk<W, WS>(F, wk, pay, lane);
+      warp_signal(F.chunks_done + wi, lane);
+    }
+    t = __shfl_sync(0xFFFFFFFFu, t_next, 0);
+  }
+}
+
+// Queue entries: the insert items of every bin (first super-mer of each item) and its
+// compaction chunks, at the positions the host gave each bin.
+__global__ void __launch_bounds__(256) task_map_kernel(FusedParams F) {
+  for (uint32_t wi = blockIdx.x; wi < F.c.nwork; wi += gridDim.x) {
+    const BinWork wk = F.c.work[wi];
+    const uint32_t* koff = F.c.sm_koff + wk.sm_begin;
+    unsigned long long* tasks = const_cast<unsigned long long*>(F.tasks);
+    for (uint32_t s = threadIdx.x; s < wk.n_super; s += blockDim.x) {
+      const unsigned long long a = koff[s];
+      const unsigned long long b = (s + 1 < wk.n_super) ? koff[s + 1] : wk.n_kmers;
+      for (unsigned long long t = (a + ITEM_KMERS - 1) / ITEM_KMERS; t * ITEM_KMERS < b; ++t)
+        tasks[wk.task_insert + t] = ((unsigned long long)wi << 32) | s;
+    }
+    for (uint32_t c = threadIdx.x; c < wk.n_chunks; c += blockDim.x)
+      tasks[wk.task_compact + c] = (1ull << 63) | ((unsigned long long)wi << 32) | c;
+  }
+}
+
 // ---- overflow recount (Sec. 3.4 "Probing Strategy": the emergency area is counted after the
 // file) -- a fresh table sized for all overflow k-mers, probed without a trial limit -----------
 template <int W, int WS>
@@ -494,6 +696,30 @@ cudaError_t launch_overflow_emit(int k, const OverflowParams& p, int nsm, cudaSt
 #define L_OEMIT(w, ws) overflow_emit_kernel<w, ws><<<grid, 256, 0, st>>>(p)
   GERBIL_KEY_SWITCH(W, WS, L_OEMIT)
 #undef L_OEMIT
+  return cudaGetLastError();
+}
+
+cudaError_t launch_task_map(const FusedParams& p, cudaStream_t st) {
+  if (p.c.nwork == 0) return cudaSuccess;
+  task_map_kernel<<<std::min<unsigned>(p.c.nwork, 4096u), 256, 0, st>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fused(int k, const FusedParams& p, int nsm, cudaStream_t st) {
+  if (p.ntasks == 0) return cudaSuccess;
+  const int W = (2 * k + 63) / 64, WS = stored_words(k);
+#define L_FUSED(w, ws)                                                                          \
+  {                                                                                             \
+    int per_sm = 0;                                                                             \
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fused_kernel<w, ws>, \
+                                                                  COUNT_THREADS, 0);            \
+    if (e != cudaSuccess) return e;                                                             \
+    const unsigned long long grid = std::min<unsigned long long>(                               \
+        (p.ntasks + 7) / 8, (unsigned long long)nsm * std::max(1, per_sm));                     \
+    fused_kernel<w, ws><<<(unsigned)grid, COUNT_THREADS, 0, st>>>(p);                           \
+  }
+  GERBIL_KEY_SWITCH(W, WS, L_FUSED)
+#undef L_FUSED
   return cudaGetLastError();
 }
 

@@ -54,6 +54,13 @@ struct BinWork {
   uint32_t n_kmers;
   uint32_t cap;                  // table slots
   uint32_t item_begin;           // first global work item of the bin
+  // fused (persistent) form only
+  uint32_t task_insert;          // queue position of the bin's first insert item
+  uint32_t task_compact;         // queue position of the bin's first compaction chunk
+  uint32_t n_items;
+  uint32_t n_chunks;
+  uint32_t dep_begin;            // this bin's entries in FusedParams::deps: the earlier bins
+  uint32_t dep_count;            // whose table regions it reuses (their compaction comes first)
 };
 
 constexpr int COUNT_THREADS = 256;
@@ -76,6 +83,24 @@ struct CountParams {
   unsigned long long ovf_cap;
   uint32_t* bin_ovf;             // overflow k-mers per work entry
   Counters* ctr;
+};
+
+constexpr int CHUNK_SLOTS = 2048;  // slots per compaction task of the fused kernel
+
+// Persistent phase-two kernel: one queue of insert items and compaction chunks in bin order.
+struct FusedParams {
+  CountParams c;                 // insert side (c.imap unused)
+  const unsigned long long* tasks;  // (compact << 63 | work index << 32 | s_lo or chunk)
+  const uint32_t* deps;          // work indices, see BinWork::dep_begin
+  unsigned long long ntasks;
+  uint32_t* items_done;          // per work entry
+  uint32_t* chunks_done;         // per work entry
+  uint32_t min_count;
+  unsigned long long* out_keys;
+  uint32_t* out_counts;
+  unsigned long long out_cap;
+  unsigned long long wait_ns;    // bound of every dependency wait
+  unsigned long long* queue;     // queue head (own 256-byte line)
 };
 
 struct CompactParams {
@@ -112,6 +137,8 @@ struct OverflowParams {
 int stored_words(int k);
 int slot_words_for_k(int k);
 cudaError_t launch_item_map(const CountParams& p, cudaStream_t st);
+cudaError_t launch_task_map(const FusedParams& p, cudaStream_t st);
+cudaError_t launch_fused(int k, const FusedParams& p, int nsm, cudaStream_t st);
 cudaError_t launch_insert(int k, const CountParams& p, int persistent, int nsm, cudaStream_t st);
 cudaError_t launch_compact(int k, const CompactParams& p, int nsm, cudaStream_t st);
 cudaError_t launch_overflow_insert(int k, const OverflowParams& p, int nsm, cudaStream_t st);

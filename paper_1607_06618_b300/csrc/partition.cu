@@ -76,6 +76,8 @@ __global__ void boundary_kernel(const uint64_t* __restrict__ offsets, uint64_t n
 // L_max windows past its range.  Each super-mer becomes one record (start, k-mers, bin),
 // appended with one atomic per warp, and counted into its bin.
 
+constexpr int SEG = 8;  // consecutive m-mers per thread in the key pass
+
 __device__ __forceinline__ unsigned long long bases64(const unsigned long long* sw, int lb) {
   const int w = lb >> 5, o = 2 * (lb & 31);
   return o ? ((sw[w] << o) | (sw[w + 1] >> (64 - o))) : sw[w];
@@ -108,6 +110,7 @@ __device__ __forceinline__ uint32_t mmer_rank(uint32_t v, int m, int ordering, i
   return c;
 }
 
+template <int MLEN>  // the minimizer length, so that every shift below is a constant
 __global__ void __launch_bounds__(256) supermer_kernel(SupermerParams P) {
   extern __shared__ __align__(16) unsigned char smem[];
   const long long T = P.tile;
@@ -116,7 +119,8 @@ __global__ void __launch_bounds__(256) supermer_kernel(SupermerParams P) {
   if (P0 >= nwin) return;
   const long long P1 = min(P0 + T, nwin);
   const long long O = P0 - 1;  // global window / base of local index 0
-  const int k = P.k, m = P.m, w = k - m + 1;
+  constexpr int m = MLEN;
+  const int k = P.k, w = k - m + 1;
   const long long lmax = P.lmax;
   const int NW = (int)(min(P1 + lmax, nwin) - O);
   const int NQ = NW + (k - m);
@@ -124,12 +128,19 @@ __global__ void __launch_bounds__(256) supermer_kernel(SupermerParams P) {
   const long long wlo = (O >= 0) ? (O >> 5) : -1;  // first staged word
   const int nsw = (int)(((O + NB - 1) >> 5) - wlo) + 2;
 
+  // shared memory: staged words and masks | PRE | SUF (window minima later) | [KEY if w <= 8]
+  // | sparse table over segment minima | V | SB | BB
+  const int NSEG = (NQ + SEG - 1) / SEG;
+  const int midmax = ((w - 1) / SEG) + 1;
+  const int LEV = 32 - __clz(midmax);
   unsigned long long* sw = reinterpret_cast<unsigned long long*>(smem);
   uint32_t* snm = reinterpret_cast<uint32_t*>(sw + nsw);
   uint32_t* sbm = snm + nsw;
-  uint32_t* rk0 = sbm + nsw;
-  uint32_t* rk1 = rk0 + NQ;
-  uint8_t* V = reinterpret_cast<uint8_t*>(rk1 + NQ);
+  uint32_t* PRE = sbm + nsw;
+  uint32_t* SUF = PRE + NQ;
+  uint32_t* KEY = SUF + NQ;
+  uint32_t* ST = KEY + (w <= SEG ? NQ : 0);
+  uint8_t* V = reinterpret_cast<uint8_t*>(ST + LEV * NSEG);
   const int nbw = (NW + 31) >> 5;
   uint32_t* SB = reinterpret_cast<uint32_t*>(V + ((NW + 15) & ~15));
   uint32_t* BB = SB + nbw;
@@ -144,43 +155,91 @@ __global__ void __launch_bounds__(256) supermer_kernel(SupermerParams P) {
   }
   __syncthreads();
 
+  // keys of the m-mers, SEG consecutive ones per thread, all cut from one 32-base window and
+  // its reverse complement; per segment the running minima from the left (PRE) and from the
+  // right (SUF) and the segment minimum (level 0 of the sparse table)
   const int lbO = (int)(O - 32 * wlo);  // local base index of global base O
   const long long n = (long long)P.n;
-  for (int iq = threadIdx.x; iq < NQ; iq += blockDim.x) {
-    const long long q = O + iq;
-    uint32_t key = 0u;
-    if (q >= 0 && q + m <= n) {
-      const int lb = lbO + iq;
-      bool ok = (bits32(snm, lb) >> (32 - m)) == 0u;
-      if (m >= 2) ok = ok && (bits32(sbm, lb + 1) >> (33 - m)) == 0u;  // no read start inside
-      if (ok) {
-        const uint32_t v = (uint32_t)(bases64(sw, lb) >> (64 - 2 * m));
-        key = mmer_rank(v, m, P.ordering, P.canon_min) + 1u;
+  const uint32_t vmask = (1u << (2 * m)) - 1u;
+  // local index ranges of m-mers inside the input (q >= 0, q + m <= n) and of windows
+  // inside it (0 <= p < nwin), so that the loops below use 32-bit indices only
+  const int q_lo = (O < 0) ? 1 : 0;
+  const int q_hi = (int)min((long long)NQ, n - m - O + 1);
+  const int p_hi = (int)min((long long)NW, nwin - O);
+  __shared__ uint32_t s_omod;
+  if (threadIdx.x == 0) s_omod = (uint32_t)(((O % lmax) + lmax) % lmax);
+  for (int seg = threadIdx.x; seg < NSEG; seg += blockDim.x) {
+    const int q0 = seg * SEG;
+    const int lb = lbO + q0;
+    const unsigned long long win = bases64(sw, lb);
+    const unsigned long long rcwin = rev2(~win);
+    const uint32_t nm32 = bits32(snm, lb), bm32 = bits32(sbm, lb);
+    uint32_t key[SEG];
+    uint32_t pre = 0xFFFFFFFFu;
+#pragma unroll
+    for (int d = 0; d < SEG; ++d) {
+      const int iq = q0 + d;
+      uint32_t kk = 0xFFFFFFFFu;  // past the tile: neutral
+      if (iq < NQ) {
+        kk = 0u;
+        bool ok = iq >= q_lo && iq < q_hi && ((nm32 << d) >> (32 - m)) == 0u;
+        if constexpr (m >= 2) ok = ok && ((bm32 << (d + 1)) >> (33 - m)) == 0u;  // no read start inside
+        if (ok) {
+          const uint32_t v = (uint32_t)(win >> (64 - 2 * m - 2 * d)) & vmask;
+          uint32_t c = v;
+          if (P.canon_min) {
+            const uint32_t rc = (uint32_t)(rcwin >> (2 * d)) & vmask;
+            c = rc < v ? rc : v;
+          }
+          if (P.ordering == 0) c |= kmc2_demoted(c, m) << 30;
+          kk = c + 1u;
+        }
+      }
+      key[d] = kk;
+      pre = min(pre, kk);
+      if (iq < NQ) {
+        PRE[iq] = pre;
+        if (w <= SEG) KEY[iq] = kk;
       }
     }
-    rk0[iq] = key;
+    uint32_t suf = 0xFFFFFFFFu;
+#pragma unroll
+    for (int d = SEG - 1; d >= 0; --d) {
+      suf = min(suf, key[d]);
+      if (q0 + d < NQ) SUF[q0 + d] = suf;
+    }
+    ST[seg] = pre;
   }
-
-  // sliding minimum over w keys: after the loop A[i] = min(key[i .. i+span)).
-  uint32_t* A = rk0;
-  uint32_t* B = rk1;
-  int len = NQ, span = 1;
-  while (2 * span <= w) {
+  for (int l = 1; l < LEV; ++l) {
     __syncthreads();
-    for (int i = threadIdx.x; i < len - span; i += blockDim.x) B[i] = min(A[i], A[i + span]);
-    len -= span;
-    span *= 2;
-    uint32_t* t = A;
-    A = B;
-    B = t;
+    const uint32_t* src = ST + (l - 1) * NSEG;
+    uint32_t* dst = ST + l * NSEG;
+    const int half = 1 << (l - 1);
+    for (int j = threadIdx.x; j < NSEG; j += blockDim.x)
+      dst[j] = (j + half < NSEG) ? min(src[j], src[j + half]) : src[j];
   }
   __syncthreads();
-  uint32_t* M = B;  // window minima: 0 = window not counted, else 1 + minimizer rank
+
+  // window minima (0 = window not counted, else 1 + minimizer rank), written over SUF
+  uint32_t* M = SUF;
   for (int i = threadIdx.x; i < NW; i += blockDim.x) {
-    const uint32_t mk = min(A[i], A[i + w - span]);
+    const int a = i, bq = i + w - 1;
+    uint32_t mk;
+    if (w <= SEG) {
+      mk = 0xFFFFFFFFu;
+      for (int q = a; q <= bq; ++q) mk = min(mk, KEY[q]);
+    } else {
+      const int sa = a / SEG, sb = bq / SEG;
+      mk = min(SUF[a], PRE[bq]);
+      const int mid = sb - sa - 1;
+      if (mid > 0) {
+        const int l = 31 - __clz(mid);
+        const uint32_t* row = ST + l * NSEG;
+        mk = min(mk, min(row[sa + 1], row[sb - (1 << l)]));
+      }
+    }
     M[i] = mk;
-    const long long p = O + i;
-    bool ok = p >= 0 && p < nwin && mk != 0u;
+    bool ok = i >= q_lo && i < p_hi && mk != 0u;
     if (ok && m == 1) {  // m = 1: no m-mer straddles a read start, test the window itself
       const int lb = lbO + i;
       for (int c = 1; ok && c < k; c += 32) {
@@ -197,14 +256,14 @@ __global__ void __launch_bounds__(256) supermer_kernel(SupermerParams P) {
   // sits on a multiple of L_max; a boundary is a start or an uncounted window.
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
   {
-    const long long Omod = ((O % lmax) + lmax) % lmax;
+    const uint32_t Omod = s_omod;  // written before the barriers above
     const uint32_t lm = (uint32_t)lmax;
     const bool pow2 = (lm & (lm - 1)) == 0;
     for (int w0 = warp * 32; w0 < nbw * 32; w0 += nwarp * 32) {
       const int i = w0 + lane;
       bool st = false, bd = true;
       if (i >= 1 && i < NW) {
-        const uint32_t r = (uint32_t)Omod + (uint32_t)i;
+        const uint32_t r = Omod + (uint32_t)i;
         const bool cut = pow2 ? ((r & (lm - 1)) == 0u) : (r % lm == 0u);
         st = V[i] && (!V[i - 1] || M[i - 1] != M[i] || cut);
         bd = !V[i] || st;
@@ -219,70 +278,116 @@ __global__ void __launch_bounds__(256) supermer_kernel(SupermerParams P) {
   }
   __syncthreads();
 
-  const uint32_t vmask = (1u << (2 * m)) - 1u;
+  // records: count the starts of every thread, take room for all of the CTA's records with one
+  // atomic, then write them (a thread's windows are 1 + tid + 256 r)
   const int own = (int)(P1 - P0);
-  for (int base = 0; base < own; base += blockDim.x) {  // uniform trip count (ballots inside)
-    const int i = 1 + base + threadIdx.x;
-    const bool is_start = i <= own && ((SB[i >> 5] >> (i & 31)) & 1u);
-    uint32_t nk = 0, bin = 0;
-    if (is_start) {
-      // end = first boundary after i (a cut every L_max windows bounds the search)
-      const int j = i + 1;
-      int end = NW;
-      for (int wj = j >> 5; wj < nbw; ++wj) {
-        const uint32_t bits = BB[wj] & (wj == (j >> 5) ? (0xFFFFFFFFu << (j & 31)) : 0xFFFFFFFFu);
-        if (bits) {
-          end = min(NW, (wj << 5) + __ffs(bits) - 1);
-          break;
-        }
-      }
-      nk = (uint32_t)(end - i);
-      const uint32_t h = fmix32((M[i] - 1u) & vmask);
-      if (P.bounds) {
-        uint32_t lo = 0, hi = P.nbins - 1;  // number of split points <= h
-        while (lo < hi) {
-          const uint32_t mid = (lo + hi) >> 1;
-          if (__ldg(P.bounds + mid) <= h) lo = mid + 1; else hi = mid;
-        }
-        bin = lo;
-      } else {
-        bin = h % P.nbins;
-      }
-      atomicAdd(P.bin_nsuper + bin, 1ull);
-      atomicAdd(P.bin_nkmers + bin, (unsigned long long)nk);
+  uint32_t mine = 0;
+  for (int i = 1 + threadIdx.x; i <= own; i += blockDim.x) mine += (SB[i >> 5] >> (i & 31)) & 1u;
+  __shared__ uint32_t s_wsum[8];
+  __shared__ unsigned long long s_rbase;
+  uint32_t incl = mine;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane == 31) s_wsum[warp] = incl;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t acc = 0;
+    for (int x = 0; x < nwarp; ++x) {
+      const uint32_t t = s_wsum[x];
+      s_wsum[x] = acc;
+      acc += t;
     }
-    const uint32_t bal = __ballot_sync(0xFFFFFFFFu, is_start);
-    if (bal) {
-      unsigned long long rbase = 0;
-      if (lane == 0) rbase = atomicAdd(P.rec_count, (unsigned long long)__popc(bal));
-      rbase = __shfl_sync(0xFFFFFFFFu, rbase, 0);
-      if (is_start) {
-        const unsigned long long idx = rbase + __popc(bal & ((1u << lane) - 1u));
-        if (idx < P.rec_cap) {
-          P.rec[idx] = make_ulonglong2((unsigned long long)(O + i),
-                                       ((unsigned long long)bin << 32) | nk);
-        }
+    s_rbase = acc ? atomicAdd(P.rec_count, (unsigned long long)acc) : 0ull;
+  }
+  __syncthreads();
+  unsigned long long idx = s_rbase + s_wsum[warp] + (incl - mine);
+  for (int i = 1 + threadIdx.x; i <= own; i += blockDim.x) {
+    if (!((SB[i >> 5] >> (i & 31)) & 1u)) continue;
+    // end = first boundary after i (a cut every L_max windows bounds the search)
+    const int j = i + 1;
+    int end = NW;
+    for (int wj = j >> 5; wj < nbw; ++wj) {
+      const uint32_t bits = BB[wj] & (wj == (j >> 5) ? (0xFFFFFFFFu << (j & 31)) : 0xFFFFFFFFu);
+      if (bits) {
+        end = min(NW, (wj << 5) + __ffs(bits) - 1);
+        break;
       }
     }
+    const uint32_t nk = (uint32_t)(end - i);
+    const uint32_t h = fmix32((M[i] - 1u) & vmask);
+    uint32_t bin;
+    if (P.bounds) {
+      uint32_t lo = 0, hi = P.nbins - 1;  // number of split points <= h
+      while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (__ldg(P.bounds + mid) <= h) lo = mid + 1; else hi = mid;
+      }
+      bin = lo;
+    } else {
+      bin = h % P.nbins;
+    }
+    atomicAdd(P.bin_nsuper + bin, 1ull);
+    atomicAdd(P.bin_nkmers + bin, (unsigned long long)nk);
+    if (idx < P.rec_cap)
+      P.rec[idx] = make_ulonglong2((unsigned long long)(O + i), ((unsigned long long)bin << 32) | nk);
+    ++idx;
   }
 }
 
-// Scatter of the records into their bins.  One 64-bit atomic per record takes both the
-// super-mer's index and its first k-mer within the bin, so that within a bin super-mer order
-// and k-mer order agree.
+// Scatter of the records into their bins.  A 64-bit atomic add of (1 << 32 | k-mers) takes
+// both a super-mer's index and its first k-mer within the bin, so that within a bin super-mer
+// order and k-mer order agree.  With few bins a CTA first sums its chunk of records per bin in
+// shared memory (the same packed add, giving each record its place within the CTA's share)
+// and then takes every bin's share with one global atomic.
+constexpr int SCATTER_RPT = 8;       // records per thread per chunk
+constexpr int SCATTER_MAX_BINS = 2048;
+
 __global__ void __launch_bounds__(256) scatter_kernel(SupermerParams P, unsigned long long nrec) {
-  for (unsigned long long r = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; r < nrec;
-       r += (unsigned long long)gridDim.x * blockDim.x) {
-    const ulonglong2 rec = P.rec[r];
-    const uint32_t bin = (uint32_t)(rec.y >> 32), nk = (uint32_t)rec.y;
-    const unsigned long long old = atomicAdd(P.bin_cursor + bin, (1ull << 32) | nk);
-    if ((old >> 32) >= P.bin_nsuper[bin]) {  // never expected
-      atomicOr(P.err, ERR_STATE);
-      continue;
+  extern __shared__ unsigned long long hist[];  // [nbins] local sums, then [nbins] global bases
+  const uint32_t nb = P.nbins;
+  const bool local = nb <= (uint32_t)SCATTER_MAX_BINS;
+  const unsigned long long per = (unsigned long long)blockDim.x * SCATTER_RPT;
+  for (unsigned long long c0 = blockIdx.x * per; c0 < nrec; c0 += (unsigned long long)gridDim.x * per) {
+    ulonglong2 rec[SCATTER_RPT];
+    unsigned long long mine[SCATTER_RPT];
+    if (local) {
+      for (uint32_t b = threadIdx.x; b < nb; b += blockDim.x) hist[b] = 0ull;
+      __syncthreads();
     }
-    const unsigned long long idx = P.bin_sm_begin[bin] + (old >> 32);
-    P.sm_pos[idx] = rec.x;
-    P.sm_koff[idx] = (uint32_t)old;
+#pragma unroll
+    for (int u = 0; u < SCATTER_RPT; ++u) {
+      const unsigned long long r = c0 + u * blockDim.x + threadIdx.x;
+      if (r >= nrec) continue;
+      rec[u] = P.rec[r];
+      const uint32_t bin = (uint32_t)(rec[u].y >> 32), nk = (uint32_t)rec[u].y;
+      mine[u] = atomicAdd(local ? hist + bin : P.bin_cursor + bin, (1ull << 32) | nk);
+    }
+    if (local) {
+      __syncthreads();
+      for (uint32_t b = threadIdx.x; b < nb; b += blockDim.x)
+        hist[nb + b] = hist[b] ? atomicAdd(P.bin_cursor + b, hist[b]) : 0ull;
+      __syncthreads();
+    }
+#pragma unroll
+    for (int u = 0; u < SCATTER_RPT; ++u) {
+      const unsigned long long r = c0 + u * blockDim.x + threadIdx.x;
+      if (r >= nrec) continue;
+      const uint32_t bin = (uint32_t)(rec[u].y >> 32);
+      const unsigned long long g = local ? hist[nb + bin] : 0ull;
+      const unsigned long long sidx = (g >> 32) + (mine[u] >> 32);
+      const uint32_t koff = (uint32_t)g + (uint32_t)mine[u];
+      if (sidx >= P.bin_nsuper[bin]) {  // never expected
+        atomicOr(P.err, ERR_STATE);
+        continue;
+      }
+      const unsigned long long idx = P.bin_sm_begin[bin] + sidx;
+      P.sm_pos[idx] = rec[u].x;
+      P.sm_koff[idx] = koff;
+    }
+    if (local) __syncthreads();  // hist is reused by the next chunk
   }
 }
 
@@ -291,8 +396,10 @@ size_t supermer_smem_bytes(int tile, int lmax, int k) {
   const long long NQ = NW + k;  // upper bound (m >= 1)
   const long long NB = NW + k;
   const long long nsw = NB / 32 + 3;
+  const long long nseg = (NQ + SEG - 1) / SEG;
+  const long long lev = 32 - __builtin_clz((unsigned)((k - 1) / SEG + 1));
   const long long nbw = (NW + 31) / 32;
-  return nsw * 8 + 2 * nsw * 4 + 2 * NQ * 4 + ((NW + 15) & ~15LL) + 2 * nbw * 4 + 16;
+  return nsw * 16 + 3 * NQ * 4 + lev * nseg * 4 + ((NW + 15) & ~15LL) + 2 * nbw * 4 + 64;
 }
 
 cudaError_t launch_encode(const uint8_t* seq, uint64_t n, unsigned long long* packed,
@@ -311,21 +418,47 @@ cudaError_t launch_boundary(const uint64_t* offsets, uint64_t nreads, uint64_t n
   return cudaGetLastError();
 }
 
+template <int M>
+static cudaError_t launch_supermer_m(const SupermerParams& p, uint64_t blocks, size_t smem, cudaStream_t st) {
+  cudaError_t e = cudaFuncSetAttribute(supermer_kernel<M>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  supermer_kernel<M><<<(unsigned)blocks, 256, smem, st>>>(p);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_supermer(const SupermerParams& p, cudaStream_t st) {
   if (p.nwin == 0) return cudaSuccess;
   const uint64_t blocks = (p.nwin + p.tile - 1) / p.tile;
   const size_t smem = supermer_smem_bytes(p.tile, p.lmax, p.k);
-  cudaError_t e = cudaFuncSetAttribute(supermer_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
-  if (e != cudaSuccess) return e;
-  supermer_kernel<<<(unsigned)blocks, 256, smem, st>>>(p);
-  return cudaGetLastError();
+  switch (p.m) {
+    case 1: return launch_supermer_m<1>(p, blocks, smem, st);
+    case 2: return launch_supermer_m<2>(p, blocks, smem, st);
+    case 3: return launch_supermer_m<3>(p, blocks, smem, st);
+    case 4: return launch_supermer_m<4>(p, blocks, smem, st);
+    case 5: return launch_supermer_m<5>(p, blocks, smem, st);
+    case 6: return launch_supermer_m<6>(p, blocks, smem, st);
+    case 7: return launch_supermer_m<7>(p, blocks, smem, st);
+    case 8: return launch_supermer_m<8>(p, blocks, smem, st);
+    case 9: return launch_supermer_m<9>(p, blocks, smem, st);
+    case 10: return launch_supermer_m<10>(p, blocks, smem, st);
+    case 11: return launch_supermer_m<11>(p, blocks, smem, st);
+    case 12: return launch_supermer_m<12>(p, blocks, smem, st);
+    case 13: return launch_supermer_m<13>(p, blocks, smem, st);
+    case 14: return launch_supermer_m<14>(p, blocks, smem, st);
+    case 15: return launch_supermer_m<15>(p, blocks, smem, st);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 cudaError_t launch_scatter(const SupermerParams& p, unsigned long long nrec, int nsm, cudaStream_t st) {
   if (nrec == 0) return cudaSuccess;
-  const unsigned blocks = (unsigned)std::min<unsigned long long>((nrec + 255) / 256, (unsigned long long)nsm * 8);
-  scatter_kernel<<<blocks, 256, 0, st>>>(p, nrec);
+  const unsigned long long per = 256ull * SCATTER_RPT;
+  const unsigned blocks = (unsigned)std::min<unsigned long long>((nrec + per - 1) / per, (unsigned long long)nsm * 8);
+  const size_t smem = p.nbins <= (uint32_t)SCATTER_MAX_BINS ? (size_t)p.nbins * 16 : 0;
+  cudaError_t e = cudaFuncSetAttribute(scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  scatter_kernel<<<blocks, 256, smem, st>>>(p, nrec);
   return cudaGetLastError();
 }
 

@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <new>
 #include <string>
 #include <vector>
@@ -24,6 +25,8 @@ struct gerbil_ctx {
   uint64_t used = 0;
   int nsm = 148;
   int insert_ctas_per_sm = 8;
+  int l2_bytes = 126 << 20;
+  size_t arena_dirty = 0;  // bytes at the start of the table arena that may be non-zero
   double ratio = 1.0;  // distinct / occurrences measured on earlier calls
   bool ratio_known = false;
   Counters* ctr = nullptr;   // device
@@ -104,9 +107,10 @@ void dev_free(gerbil_ctx* ctx, void* p, size_t bytes) {
   ctx->used -= std::min(ctx->used, (uint64_t)bytes);
 }
 
-// Grow-only scratch buffer cached in the context.
-int scratch(gerbil_ctx* ctx, void** buf, size_t* have, size_t need) {
+// Grow-only scratch buffer cached in the context (*grown set when it was reallocated).
+int scratch(gerbil_ctx* ctx, void** buf, size_t* have, size_t need, bool* grown = nullptr) {
   if (*have >= need && *buf) return GERBIL_OK;
+  if (grown) *grown = true;
   dev_free(ctx, *buf, *have);
   *buf = nullptr;
   *have = 0;
@@ -180,6 +184,8 @@ void gerbil_opts_default(gerbil_opts* o) {
   o->distinct_ratio = 0.0f;
   o->overflow_slots = 0;
   o->persistent = 1;
+  o->ring_slots = 0;
+  o->fused = 0;
 }
 
 const char* gerbil_strerror(int s) {
@@ -215,6 +221,7 @@ int gerbil_create(gerbil_ctx** out, int device, uint64_t budget, void* stream) {
   do {
     if (cudaSetDevice(device) != cudaSuccess) { rc = GERBIL_E_CUDA; break; }
     cudaDeviceGetAttribute(&ctx->nsm, cudaDevAttrMultiProcessorCount, device);
+    cudaDeviceGetAttribute(&ctx->l2_bytes, cudaDevAttrL2CacheSize, device);
     if (stream) {
       ctx->stream = (cudaStream_t)stream;
     } else {
@@ -559,6 +566,237 @@ void gerbil_bins_free(gerbil_bins* b) {
 }
 
 // ---- phase two ---------------------------------------------------------------------------------
+// ---- phase two, fused persistent form -----------------------------------------------------------
+// Returns FUSED_FALLBACK when the overflow area was used: the result is then recomputed by the
+// classic form, which merges overflow counts.
+static const int FUSED_FALLBACK = -1;
+static const int LAG = 5;  // bins between a bin's inserts and its compaction in the queue
+
+static int count_fused(gerbil_ctx* ctx, const gerbil_bins* b, const std::vector<int32_t>& list,
+                       int k, uint32_t min_count, const gerbil_opts& opts, double ratio,
+                       double alpha, uint32_t theta, uint32_t spin_limit, gerbil_counts** out) {
+  const int W = words_for(k);
+  const int SW = gerbil::slot_words_for_k(k);
+  cudaStream_t st = ctx->stream;
+  std::vector<BinWork> work;
+  uint64_t occ = 0;
+  for (int32_t bi : list) {
+    if (b->nkmers[bi] == 0) continue;
+    BinWork w{};
+    w.sm_begin = b->sm_begin[bi];
+    w.n_super = (uint32_t)b->nsuper[bi];
+    w.n_kmers = (uint32_t)b->nkmers[bi];
+    const double est = std::max(1.0, std::ceil(ratio * (double)w.n_kmers));
+    w.cap = (uint32_t)std::min<uint64_t>((uint64_t)std::ceil(est / alpha) + 16, 0xFFFFF000ull);
+    w.n_items = (w.n_kmers + gerbil::ITEM_KMERS - 1) / gerbil::ITEM_KMERS;
+    w.n_chunks = (w.cap + gerbil::CHUNK_SLOTS - 1) / gerbil::CHUNK_SLOTS;
+    occ += w.n_kmers;
+    work.push_back(w);
+  }
+  const size_t nw = work.size();
+  // table placement: bins up to 1/(LAG+2) of the ring go to the L2-sized ring (first fit,
+  // wrapping), the rest to dedicated memory after it.  The ring is kept as intervals with the
+  // last bin that used each; a bin depends on every bin whose interval it overlaps.  A bin
+  // that would overlap one of its LAG predecessors (whose compactions are queued after its
+  // inserts) gets dedicated memory instead.
+  const uint64_t ring = opts.ring_slots ? (uint64_t)opts.ring_slots
+                                        : std::max<uint64_t>(4096, (uint64_t)(0.6 * ctx->l2_bytes) / (SW * 8));
+  std::map<uint64_t, std::pair<uint64_t, uint32_t>> owner;  // start -> (end, work index)
+  std::vector<uint32_t> deps;
+  uint64_t cursor = 0, ded = 0;
+  bool any_ring = false;
+  std::vector<char> dedicated(nw, 0);
+  for (size_t i = 0; i < nw; ++i) {
+    BinWork& w = work[i];
+    w.dep_begin = (uint32_t)deps.size();
+    w.dep_count = 0;
+    if ((uint64_t)w.cap * (LAG + 2) > ring) {
+      dedicated[i] = 1;
+      continue;
+    }
+    const uint64_t a = (cursor + w.cap > ring) ? 0 : cursor, e = a + w.cap;
+    // collect and cut the owners of [a, e)
+    bool too_close = false;
+    for (auto it2 = owner.begin(); it2 != owner.end(); ++it2)
+      if (it2->first < e && it2->second.first > a && it2->second.second + LAG + 1 > i) too_close = true;
+    if (too_close) {
+      dedicated[i] = 1;
+      continue;
+    }
+    auto it = owner.upper_bound(a);
+    if (it != owner.begin()) --it;
+    std::vector<std::pair<uint64_t, std::pair<uint64_t, uint32_t>>> keep;
+    while (it != owner.end() && it->first < e) {
+      const uint64_t s0 = it->first, e0 = it->second.first;
+      const uint32_t who = it->second.second;
+      if (e0 > a) {
+        if (std::find(deps.begin() + w.dep_begin, deps.end(), who) == deps.end()) deps.push_back(who);
+        if (s0 < a) keep.push_back({s0, {a, who}});
+        if (e0 > e) keep.push_back({e, {e0, who}});
+        it = owner.erase(it);
+      } else {
+        ++it;
+      }
+    }
+    for (auto& kv : keep) owner[kv.first] = kv.second;
+    owner[a] = {e, (uint32_t)i};
+    w.dep_count = (uint32_t)deps.size() - w.dep_begin;
+
+    w.table_off = a;
+    cursor = e;
+    any_ring = true;
+  }
+  const uint64_t ring_used = any_ring ? ring : 0;
+  for (size_t i = 0; i < nw; ++i)
+    if (dedicated[i]) {
+      work[i].table_off = ring_used + ded;
+      ded += work[i].cap;
+    }
+  const uint64_t slots = ring_used + ded;
+  // queue order: the compaction chunks of bin i follow the insert items of bin i+LAG:
+  // I(0) .. I(LAG), C(0), I(LAG+1), C(1), ..., C(last)
+  uint64_t pos = 0;
+  for (size_t i = 0; i < nw; ++i) {
+    work[i].task_insert = (uint32_t)pos;
+    pos += work[i].n_items;
+    if (i >= (size_t)LAG) {
+      work[i - LAG].task_compact = (uint32_t)pos;
+      pos += work[i - LAG].n_chunks;
+    }
+  }
+  for (size_t i = (nw > (size_t)LAG ? nw - LAG : 0); i < nw; ++i) {
+    work[i].task_compact = (uint32_t)pos;
+    pos += work[i].n_chunks;
+  }
+  const uint64_t ntasks = pos;
+  if (ntasks >= (1ull << 32)) return fail(ctx, GERBIL_E_INVAL, "too many work items");
+
+  const uint64_t ovf_cap = opts.overflow_slots ? (uint64_t)opts.overflow_slots
+                                               : std::max<uint64_t>(1 << 16, occ / 32);
+  int rc;
+  bool grown = false;
+  const size_t arena_need = slots * SW * 8;
+  if ((rc = scratch(ctx, &ctx->arena, &ctx->arena_bytes, arena_need + 256, &grown))) return rc;
+  if (grown) ctx->arena_dirty = ctx->arena_bytes;
+  if ((rc = scratch(ctx, &ctx->ovf, &ctx->ovf_bytes, ovf_cap * W * 8 + 256))) return rc;
+  auto up = [](size_t x) { return (x + 255) & ~size_t(255); };
+  const size_t o_work = 0, o_bovf = up(nw * sizeof(BinWork)), o_items = o_bovf + up(nw * 4),
+               o_chunks = o_items + up(nw * 4), o_queue = o_chunks + up(nw * 4),
+               o_deps = o_queue + 256, o_tasks = o_deps + up(deps.size() * 4 + 4),
+               small_need = o_tasks + up(ntasks * 8) + 256;
+  if ((rc = scratch(ctx, &ctx->small, &ctx->small_bytes, small_need))) return rc;
+  char* sm = (char*)ctx->small;
+
+  // rows <= live slots of all tables (ring regions are reused, so count every bin's table)
+  uint64_t cap_sum = 0;
+  for (const BinWork& w : work) cap_sum += w.cap;
+  const uint64_t out_cap = std::max<uint64_t>(1, std::min<uint64_t>(occ, cap_sum));
+  gerbil_counts* res = new (std::nothrow) gerbil_counts;
+  if (!res) return GERBIL_E_NOMEM;
+  res->ctx = ctx;
+  res->W = W;
+  res->bytes = out_cap * (W * 8 + 4);
+  if ((rc = dev_alloc(ctx, (void**)&res->keys, out_cap * W * 8))) { delete res; return rc; }
+  if ((rc = dev_alloc(ctx, (void**)&res->counts, out_cap * 4))) {
+    dev_free(ctx, res->keys, out_cap * W * 8);
+    delete res;
+    return rc;
+  }
+  auto drop = [&]() { gerbil_counts_free(res); };
+#define CKF(call)                                                                          \
+  do {                                                                                     \
+    cudaError_t e_ = (call);                                                               \
+    if (e_ != cudaSuccess) {                                                               \
+      drop();                                                                              \
+      ctx->arena_dirty = ctx->arena_bytes;                                                            \
+      return fail(ctx, GERBIL_E_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    }                                                                                      \
+  } while (0)
+
+  ctx->times.calls++;
+  ph_begin(ctx, PH_CLEAR);
+  if (ctx->arena_dirty)
+    CKF(cudaMemsetAsync(ctx->arena, 0, std::min(ctx->arena_bytes, std::max(ctx->arena_dirty, arena_need)), st));
+  ctx->arena_dirty = 0;
+  CKF(cudaMemsetAsync(ctx->ctr, 0, sizeof(Counters), st));
+  CKF(cudaMemsetAsync(sm + o_bovf, 0, o_tasks - o_bovf, st));
+  if (nw) CKF(cudaMemcpyAsync(sm + o_work, work.data(), nw * sizeof(BinWork), cudaMemcpyHostToDevice, st));
+  if (!deps.empty())
+    CKF(cudaMemcpyAsync(sm + o_deps, deps.data(), deps.size() * 4, cudaMemcpyHostToDevice, st));
+  gerbil::FusedParams fp{};
+  fp.c.packed = b->packed;
+  fp.c.sm_pos = b->sm_pos;
+  fp.c.sm_koff = b->sm_koff;
+  fp.c.work = (const BinWork*)(sm + o_work);
+  fp.c.nwork = (uint32_t)nw;
+  fp.c.nitems = 0;
+  fp.c.imap = nullptr;
+  fp.c.k = k;
+  fp.c.canonical = opts.canonical ? 1 : 0;
+  fp.c.theta = theta;
+  fp.c.spin_limit = spin_limit;
+  fp.c.arena = (unsigned long long*)ctx->arena;
+  fp.c.ovf = (unsigned long long*)ctx->ovf;
+  fp.c.ovf_cap = ovf_cap;
+  fp.c.bin_ovf = (uint32_t*)(sm + o_bovf);
+  fp.c.ctr = ctx->ctr;
+  fp.tasks = (const unsigned long long*)(sm + o_tasks);
+  fp.deps = (const uint32_t*)(sm + o_deps);
+  fp.ntasks = ntasks;
+  fp.items_done = (uint32_t*)(sm + o_items);
+  fp.chunks_done = (uint32_t*)(sm + o_chunks);
+  fp.min_count = min_count;
+  fp.out_keys = res->keys;
+  fp.out_counts = res->counts;
+  fp.out_cap = out_cap;
+  fp.wait_ns = 2000000000ull;  // 2 s
+  fp.queue = (unsigned long long*)(sm + o_queue);
+  if (nw) {
+    CKF(gerbil::launch_task_map(fp, st));
+    ctx->times.kernel_launches++;
+  }
+  ph_end(ctx, PH_CLEAR);
+  ph_begin(ctx, PH_INSERT);
+  if (ntasks) {
+    CKF(gerbil::launch_fused(k, fp, ctx->nsm, st));
+    ctx->times.kernel_launches++;
+    ctx->times.insert_launches++;
+  }
+  ph_end(ctx, PH_INSERT);
+  if ((rc = read_counters(ctx))) {
+    drop();
+    ctx->arena_dirty = ctx->arena_bytes;
+    return rc;
+  }
+  const Counters h = *ctx->hctr;
+  if (h.err & (gerbil::ERR_QUEUE | gerbil::ERR_STATE | gerbil::ERR_OUT_FULL | gerbil::ERR_SPIN)) {
+    drop();
+    ctx->arena_dirty = ctx->arena_bytes;
+    if (h.err & gerbil::ERR_QUEUE) return fail(ctx, GERBIL_E_TIMEOUT, "work-queue wait gave up");
+    return fail(ctx, GERBIL_E_STATE, "device consistency check failed");
+  }
+  // every table region was compacted and zeroed: the arena is clean again
+  if (h.ovf_count || (h.err & gerbil::ERR_OVF_FULL)) {
+    drop();
+    return FUSED_FALLBACK;
+  }
+  gerbil_count_stats stats{};
+  stats.bins = (uint32_t)list.size();
+  stats.occurrences = occ;
+  stats.emitted = h.out_count;
+  stats.distinct = h.distinct;
+  stats.table_slots = cap_sum;
+  res->n = h.out_count;
+  res->stats = stats;
+  if (occ > 0) {
+    ctx->ratio = (double)h.distinct / (double)occ;
+    ctx->ratio_known = true;
+  }
+  *out = res;
+  return GERBIL_OK;
+#undef CKF
+}
+
 static int count_impl(gerbil_ctx* ctx, const gerbil_bins* b, const std::vector<int32_t>& list,
                       int k, uint32_t min_count, const gerbil_opts& opts, gerbil_counts** out) {
   const int W = words_for(k);
@@ -575,6 +813,11 @@ static int count_impl(gerbil_ctx* ctx, const gerbil_bins* b, const std::vector<i
   gerbil_count_stats stats{};
   stats.bins = (uint32_t)list.size();
   stats.occurrences = occ;
+
+  if (opts.fused) {
+    const int rc = count_fused(ctx, b, list, k, min_count, opts, ratio, alpha, theta, spin_limit, out);
+    if (rc != FUSED_FALLBACK) return rc;
+  }
 
   for (int round = 0; round < 4; ++round) {
     // table sizing per bin (Sec. 3.4: expected distinct = ratio x k-mers of the file)
@@ -605,7 +848,9 @@ static int count_impl(gerbil_ctx* ctx, const gerbil_bins* b, const std::vector<i
     const int SWk = gerbil::slot_words_for_k(k);
     const size_t arena_need = slots * SWk * 8;
     int rc;
-    if ((rc = scratch(ctx, &ctx->arena, &ctx->arena_bytes, arena_need + 256))) return rc;
+    bool grown = false;
+    if ((rc = scratch(ctx, &ctx->arena, &ctx->arena_bytes, arena_need + 256, &grown))) return rc;
+    if (grown) ctx->arena_dirty = ctx->arena_bytes;
     if ((rc = scratch(ctx, &ctx->ovf, &ctx->ovf_bytes, ovf_cap * W * 8 + 256))) return rc;
     const size_t work_bytes = work.size() * sizeof(BinWork);
     const size_t small_need = ((work_bytes + 255) & ~size_t(255)) + ((work.size() * 4 + 255) & ~size_t(255)) +
@@ -640,6 +885,7 @@ static int count_impl(gerbil_ctx* ctx, const gerbil_bins* b, const std::vector<i
     ctx->times.calls++;
     ph_begin(ctx, PH_CLEAR);
     CKR(cudaMemsetAsync(ctx->arena, 0, arena_need, st));
+    ctx->arena_dirty = std::max(ctx->arena_dirty, arena_need);  // tables stay in the arena
     CKR(cudaMemsetAsync(ctx->ctr, 0, sizeof(Counters), st));
     if (!work.empty()) {
       CKR(cudaMemcpyAsync(dwork, work.data(), work_bytes, cudaMemcpyHostToDevice, st));

@@ -58,7 +58,8 @@ class gerbil_opts(ctypes.Structure):
                 ("bin_bounds", ctypes.c_void_p), ("max_probes", ctypes.c_uint32),
                 ("load_factor", ctypes.c_float), ("distinct_ratio", ctypes.c_float),
                 ("overflow_slots", ctypes.c_uint32), ("persistent", ctypes.c_int32),
-                ("reserved", ctypes.c_uint32 * 6)]
+                ("ring_slots", ctypes.c_uint32), ("fused", ctypes.c_int32),
+                ("reserved", ctypes.c_uint32 * 4)]
 
 
 class gerbil_count_stats(ctypes.Structure):
