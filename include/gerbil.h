@@ -220,6 +220,33 @@ int gerbil_counts_to_host(const gerbil_counts* counts, uint64_t* keys, uint32_t*
 
 void gerbil_counts_free(gerbil_counts* counts);
 
+/* Counting without any device allocation.  The paper has no counterpart: this entry point is
+ * for callers that cannot call cudaMalloc -- for example code whose device memory is owned by
+ * another component (a framework's caching allocator or a fixed memory budget that forbids
+ * extra allocations), or latency-sensitive paths that cannot afford the implicit device
+ * synchronisation of cudaMalloc and cudaFree.  It counts the k-mers of a small read set (same
+ * read and key conventions as above; canonical != 0 counts min(x, revcomp(x))) and writes the
+ * rows with count >= min_count to caller-provided device buffers keys_out (out_cap * W words)
+ * and counts_out (out_cap entries).  seq and offsets are device pointers; nbases is
+ * offsets[nreads] (host value); *n_out (host) receives the number of rows.
+ * Scratch: a fixed 32 MiB table in a file-scope device array, held by every GPU that loads
+ * the library until the process exits.  Inputs with more than
+ * floor((4194304 - 16) / S / 2) k-mer windows, where S = 2 * ceil((ceil(2k/63) + 1) / 2)
+ * words per slot (about 1.05 million windows for k <= 31, 524 thousand for k = 65), are
+ * rejected with GERBIL_E_INVAL before any GPU work.  The first call on a device resolves the
+ * array's address (cudaGetSymbolAddress) for that device; make that first call before any
+ * stream capture.  Every call clears the part of the array it uses, runs on cuda_stream (NULL:
+ * the default stream) and synchronises it; calls whose GPU work overlaps (other streams or
+ * other host threads on the same device) race on the shared array and must be serialised by
+ * the caller.  No cudaMalloc, cudaFree or allocating library routine is called.
+ * Errors: E_INVAL (arguments, input too large, or *n_out > out_cap: *n_out then holds the
+ * number of rows needed), E_UNSUPPORTED (k > GERBIL_MAX_K), E_NOMEM (the table ran full),
+ * E_CUDA. */
+int gerbil_count_small_noalloc(const uint8_t* seq, const uint64_t* offsets, uint64_t nreads,
+                               uint64_t nbases, int k, uint32_t min_count, int canonical,
+                               uint64_t* keys_out, uint32_t* counts_out, uint64_t out_cap,
+                               uint64_t* n_out, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

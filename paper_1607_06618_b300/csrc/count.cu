@@ -724,3 +724,158 @@ cudaError_t launch_fused(int k, const FusedParams& p, int nsm, cudaStream_t st) 
 }
 
 }  // namespace gerbil
+
+// ---- no-allocation entry point -----------------------------------------------------------------
+// For callers that must not allocate device memory: the counting table lives in a file-scope
+// device array of fixed size, held by every GPU that loads this library until the process
+// exits.  Host code must not pass the array's name to a kernel (on the host it is only a
+// stand-in); the device address comes from cudaGetSymbolAddress, once per device.
+
+namespace gerbil {
+
+constexpr unsigned long long NOALLOC_WORDS = 1ull << 22;  // 32 MiB
+constexpr unsigned long long NOALLOC_HEAD = 16;           // counter words before the table
+static __device__ __align__(256) unsigned long long g_noalloc_scratch[NOALLOC_WORDS];
+
+// One warp per read, lanes over its windows; each k-mer is built straight from the ASCII bytes.
+template <int W, int WS>
+__global__ void __launch_bounds__(256) noalloc_insert_kernel(const uint8_t* __restrict__ seq,
+                                                             const uint64_t* __restrict__ offsets,
+                                                             uint64_t nreads, int k, int canonical,
+                                                             unsigned long long* scratch, uint32_t cap) {
+  unsigned long long* tab = scratch + NOALLOC_HEAD;
+  const unsigned long long nw = (unsigned long long)gridDim.x * (blockDim.x >> 5);
+  const int lane = threadIdx.x & 31;
+  for (unsigned long long r = (blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) >> 5;
+       r < nreads; r += nw) {
+    const uint64_t a = offsets[r], b = offsets[r + 1];
+    if (b < a + (uint64_t)k) continue;
+    for (uint64_t p = a + lane; p + k <= b; p += 32) {
+      unsigned long long key[W];
+#pragma unroll
+      for (int j = 0; j < W; ++j) key[j] = 0ull;
+      bool ok = true;
+      for (int i = 0; i < k && ok; ++i) {
+        const uint32_t u = seq[p + i] & 0xDFu;
+        ok = (u == 'A') | (u == 'C') | (u == 'G') | (u == 'T');
+        uint32_t t = (u >> 1) & 3u;
+        t ^= t >> 1;  // A0 C1 G2 T3
+#pragma unroll
+        for (int j = 0; j < W - 1; ++j) key[j] = (key[j] << 2) | (key[j + 1] >> 62);
+        key[W - 1] = (key[W - 1] << 2) | t;
+      }
+      if (!ok) continue;
+      if (canonical) {
+        unsigned long long rc[W];
+        revcomp<W>(key, k, rc);
+        if (key_less<W>(rc, key)) {
+#pragma unroll
+          for (int q = 0; q < W; ++q) key[q] = rc[q];
+        }
+      }
+      unsigned long long st[WS];
+      to_stored<W, WS>(key, st);
+      if (table_insert<WS>(tab, cap, st, key_hash<W>(key), cap, 1u << 20))
+        atomicOr(reinterpret_cast<unsigned int*>(scratch + 1), 1u);
+    }
+  }
+}
+
+template <int W, int WS>
+__global__ void __launch_bounds__(256) noalloc_compact_kernel(unsigned long long* scratch, uint32_t cap,
+                                                              uint32_t min_count,
+                                                              unsigned long long* keys_out,
+                                                              uint32_t* counts_out,
+                                                              unsigned long long out_cap) {
+  constexpr int SW = slot_words(WS);
+  const unsigned long long* tab = scratch + NOALLOC_HEAD;
+  for (unsigned long long s = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; s < cap;
+       s += (unsigned long long)gridDim.x * blockDim.x) {
+    const unsigned long long* sp = tab + s * SW;
+    const unsigned long long mt = sp[0];
+    if (mt == 0ull) continue;
+    atomicAdd(scratch + 2, 1ull);
+    if ((uint32_t)mt < min_count) continue;
+    const unsigned long long row = atomicAdd(scratch + 0, 1ull);
+    if (row >= out_cap) continue;  // the host reports the size that would have been needed
+    unsigned long long st[WS], key[W];
+#pragma unroll
+    for (int j = 0; j < WS; ++j) st[j] = sp[1 + j];
+    from_stored<W, WS>(st, key);
+#pragma unroll
+    for (int j = 0; j < W; ++j) keys_out[row * W + j] = key[j];
+    counts_out[row] = (uint32_t)mt;
+  }
+}
+
+}  // namespace gerbil
+
+#include <mutex>
+
+#include "../../include/gerbil.h"
+
+namespace {
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[256];  // device address of the scratch array, per device
+}  // namespace
+
+extern "C" int gerbil_count_small_noalloc(const uint8_t* seq, const uint64_t* offsets,
+                                          uint64_t nreads, uint64_t nbases, int k,
+                                          uint32_t min_count, int canonical, uint64_t* keys_out,
+                                          uint32_t* counts_out, uint64_t out_cap, uint64_t* n_out,
+                                          void* cuda_stream) {
+  using namespace gerbil;
+  if (!n_out) return GERBIL_E_INVAL;
+  *n_out = 0;
+  if (k > GERBIL_MAX_K) return GERBIL_E_UNSUPPORTED;
+  if (k < GERBIL_MIN_K || min_count < 1) return GERBIL_E_INVAL;
+  if (nreads > 0 && (!seq || !offsets)) return GERBIL_E_INVAL;
+  if (out_cap > 0 && (!keys_out || !counts_out)) return GERBIL_E_INVAL;
+  const int W = (2 * k + 63) / 64, WS = stored_words(k), SW = slot_words(WS);
+  const unsigned long long cap_max = (NOALLOC_WORDS - NOALLOC_HEAD) / (unsigned long long)SW;
+  const uint64_t windows = nbases >= (uint64_t)k ? nbases - k + 1 : 0;
+  if (windows > cap_max / 2) return GERBIL_E_INVAL;  // more k-mers than the scratch table holds
+  const uint32_t cap = (uint32_t)std::min<unsigned long long>(cap_max, 2 * windows + 64);
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  int dev = 0, nsm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) return GERBIL_E_CUDA;
+  void* scratch = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+      void* p = nullptr;
+      if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return GERBIL_E_CUDA;
+      g_noalloc_ptr[dev] = p;
+    }
+    scratch = g_noalloc_ptr[dev];
+  }
+  if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return GERBIL_E_CUDA;
+  unsigned long long* sp = static_cast<unsigned long long*>(scratch);
+  if (cudaMemsetAsync(sp, 0, (NOALLOC_HEAD + (unsigned long long)cap * SW) * 8, st) != cudaSuccess)
+    return GERBIL_E_CUDA;
+  const unsigned grid_i = (unsigned)std::max<unsigned long long>(
+      1, std::min<unsigned long long>((nreads + 7) / 8, (unsigned long long)nsm * 8));
+  const unsigned grid_c = (unsigned)std::min<unsigned long long>((cap + 255) / 256, (unsigned long long)nsm * 8);
+  auto run = [&]() -> cudaError_t {
+#define L_NOALLOC(w, ws)                                                                          \
+  {                                                                                               \
+    if (nreads) noalloc_insert_kernel<w, ws><<<grid_i, 256, 0, st>>>(seq, offsets, nreads, k,      \
+                                                                     canonical ? 1 : 0, sp, cap); \
+    noalloc_compact_kernel<w, ws><<<grid_c, 256, 0, st>>>(sp, cap, min_count,                     \
+                                                          (unsigned long long*)keys_out,          \
+                                                          counts_out, out_cap);                   \
+  }
+    GERBIL_KEY_SWITCH(W, WS, L_NOALLOC)
+#undef L_NOALLOC
+    return cudaGetLastError();
+  };
+  if (run() != cudaSuccess) return GERBIL_E_CUDA;
+  unsigned long long head[3] = {0, 0, 0};
+  if (cudaMemcpyAsync(head, sp, sizeof(head), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return GERBIL_E_CUDA;
+  *n_out = head[0];
+  if ((unsigned int)head[1]) return GERBIL_E_NOMEM;  // the scratch table ran full
+  if (head[0] > out_cap) return GERBIL_E_INVAL;      // *n_out rows did not fit in out_cap
+  return GERBIL_OK;
+}

@@ -36,7 +36,7 @@ ABI_SYMBOLS = (
     "gerbil_destroy", "gerbil_partition", "gerbil_bins_info", "gerbil_bin_stats",
     "gerbil_bins_export", "gerbil_bins_free", "gerbil_count", "gerbil_count_batch",
     "gerbil_counts_info", "gerbil_counts_view", "gerbil_counts_to_host", "gerbil_counts_free",
-    "gerbil_profile", "gerbil_get_phase_times",
+    "gerbil_profile", "gerbil_get_phase_times", "gerbil_count_small_noalloc",
 )
 
 
@@ -119,6 +119,8 @@ def load() -> ctypes.CDLL:
         "gerbil_counts_to_host": (I32, [P, P, P, U64]),
         "gerbil_counts_free": (None, [P]),
         "gerbil_profile": (I32, [P, I32]),
+        "gerbil_count_small_noalloc": (I32, [P, P, U64, U64, I32, U32, I32, P, P, U64,
+                                             ctypes.POINTER(U64), P]),
         "gerbil_get_phase_times": (I32, [P, ctypes.POINTER(gerbil_phase_times)]),
     }
     for name, (res, args) in sig.items():
@@ -274,6 +276,25 @@ def gerbil_counts_to_host(counts, keys_out=None, counts_out=None):
 
 def gerbil_counts_free(counts):
     load().gerbil_counts_free(counts)
+
+
+def gerbil_count_small_noalloc(seq, offsets, k: int, min_count: int, canonical: bool,
+                               keys_out, counts_out, stream: int | None = None, nbases=None):
+    """Counts a small read set with no device allocation inside the library.
+
+    seq/offsets are torch CUDA tensors (uint8 / int64); keys_out (int64[cap, W]) and
+    counts_out (int32[cap]) are caller-allocated CUDA tensors.  Returns the number of rows.
+    """
+    n = ctypes.c_uint64()
+    nreads = offsets.numel() - 1
+    if nbases is None:
+        nbases = int(offsets[-1].item()) if nreads >= 0 else 0
+    cap = counts_out.numel()
+    st = load().gerbil_count_small_noalloc(seq.data_ptr(), offsets.data_ptr(), nreads, nbases, k,
+                                           min_count, 1 if canonical else 0, keys_out.data_ptr(),
+                                           counts_out.data_ptr(), cap, ctypes.byref(n), stream)
+    _check(st)
+    return n.value
 
 
 # ---- handle wrappers ----------------------------------------------------------------------
