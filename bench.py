@@ -46,6 +46,9 @@ def _args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-reads", type=int, default=40000)
     ap.add_argument("--ref-sample-reads", type=int, default=5000)
+    ap.add_argument("--fused", type=int, default=None,
+                    help="phase-two form: 0 all tables, 1 fused queue kernel, 2 waves")
+    ap.add_argument("--schedule", type=int, default=None, help="1 device queue, 0 fixed striding")
     return ap.parse_args()
 
 
@@ -206,7 +209,12 @@ def main_ours(a, world, rank, local):
     o_dev = torch.from_numpy(offs.view(np.int64)).cuda()
     stream = torch.cuda.current_stream()
     ctx = gerbil.Context(local, stream=stream.cuda_stream)
-    opts = gerbil.default_opts()
+    kw = {}
+    if a.fused is not None:
+        kw["fused"] = a.fused
+    if a.schedule is not None:
+        kw["schedule"] = a.schedule
+    opts = gerbil.default_opts(**kw)
 
     info = {}
 
@@ -267,6 +275,22 @@ def main_ours(a, world, rank, local):
                 "bytes_per_launch": kbytes, "launch_ms": ins_ms}
     phase_ms = {key[:-3]: ph[key] / a.steps for key in ph if key.endswith("_ms")}
 
+    # ceilings of the operations the insert kernel is made of (random 32-byte slot load, then
+    # an atomic add on it), L2-resident and HBM-sized, measured on this GPU
+    membench = None
+    if rank == 0:
+        membench = {}
+        for label, nbytes in (("l2_32MB", 32 << 20), ("hbm_4GB", 4 << 30)):
+            for op, name in ((0, "red"), (1, "load32"), (2, "load32_then_red"), (3, "cas")):
+                membench["%s_%s_gops" % (label, name)] = gerbil.gerbil_membench(ctx.handle, nbytes, op, 256)
+        ins_rate = occ / (ins_ms / 1000.0) / 1e9
+        roofline["l2_ops"] = {
+            "achieved": ins_rate, "unit": "G inserts/s",
+            "peak": membench["l2_32MB_load32_then_red_gops"],
+            "frac": ins_rate / membench["l2_32MB_load32_then_red_gops"],
+            "peak_kind": "measured in this run: random 32-byte slot load then atomic add, "
+                         "32 MB footprint (gerbil_membench op 2)"}
+
     # batched (one persistent launch) vs one count call per bin, phase two only
     bvp = None
     if a.per_bin_steps > 0 and rank == 0:
@@ -277,14 +301,17 @@ def main_ours(a, world, rank, local):
             ctx.count_batch(bins, None, k, mc, opts).free()
         torch.cuda.synchronize()
         tb = (time.perf_counter() - tb) / a.per_bin_steps
-        classic = gerbil.default_opts(fused=1)
-        ctx.count_batch(bins, None, k, mc, classic).free()
-        torch.cuda.synchronize()
-        tc = time.perf_counter()
-        for _ in range(a.per_bin_steps):
-            ctx.count_batch(bins, None, k, mc, classic).free()
-        torch.cuda.synchronize()
-        tc = (time.perf_counter() - tc) / a.per_bin_steps
+        def host_ms(o):
+            ctx.count_batch(bins, None, k, mc, o).free()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(a.per_bin_steps):
+                ctx.count_batch(bins, None, k, mc, o).free()
+            torch.cuda.synchronize()
+            return (time.perf_counter() - t0) / a.per_bin_steps
+        tc = host_ms(gerbil.default_opts(fused=1))
+        ts = host_ms(gerbil.default_opts(schedule=0))
+        tw = host_ms(gerbil.default_opts(fused=2))
         tp = time.perf_counter()
         for _ in range(a.per_bin_steps):
             for b in range(nbins):
@@ -292,7 +319,9 @@ def main_ours(a, world, rank, local):
         torch.cuda.synchronize()
         tp = (time.perf_counter() - tp) / a.per_bin_steps
         bins.free()
-        bvp = {"batched_ms": 1000 * tb, "batched_fused_ms": 1000 * tc, "per_bin_ms": 1000 * tp,
+        bvp = {"batched_ms": 1000 * tb, "batched_fused_ms": 1000 * tc,
+               "batched_static_schedule_ms": 1000 * ts, "batched_waves_ms": 1000 * tw,
+               "per_bin_ms": 1000 * tp,
                "speedup": tp / tb,
                "what": "phase two over all %d bins, host-timed: one count_batch (persistent insert "
                        "grid + compaction grid), one fused count_batch (queue + L2 table ring), "
@@ -354,6 +383,7 @@ def main_ours(a, world, rank, local):
                            "achieved_gbs": step_bytes / (p2_ms / 1000.0) / 1e9},
             "phase_ms": phase_ms, "cpu_baseline": cpu, "e2e": e2e, "clocks": ck,
             "gpu_launches": int(ph["kernel_launches"]), "batched_vs_per_bin": bvp,
+            "membench": membench,
         }
         print(json.dumps(line), flush=True)
     ctx.close()

@@ -99,13 +99,18 @@ typedef struct gerbil_opts {
   int32_t persistent;          /* 1 (default): the insert kernel runs as many CTAs as fit on
                                   the GPU at once, each warp striding over the work items of
                                   all bins in bin order; 0: one warp per work item */
-  uint32_t ring_slots;         /* fused form: table slots of the ring (0: 60% of L2) */
-  int32_t fused;               /* 1: one kernel pops insert and compaction tasks of all bins
+  uint32_t ring_slots;         /* fused form: table slots of the ring (0: 60% of L2); waves:
+                                  table slots per wave (0: 50% of L2) */
+  int32_t fused;               /* 0 (default): separate insert and compaction kernels over
+                                  tables that all stay allocated until the compaction;
+                                  1: one kernel pops insert and compaction tasks of all bins
                                   from a device queue, with the tables of small bins in an
-                                  L2-sized ring that is reused bin after bin; 0 (default):
-                                  separate insert and compaction kernels over tables that all
-                                  stay allocated until the compaction */
-  uint32_t reserved[4];
+                                  L2-sized ring that is reused bin after bin; 2: waves of bins
+                                  whose tables fit in half of L2, each cleared, filled and
+                                  compacted in one reused region while hot in L2 */
+  int32_t schedule;            /* insert work items: 1 (default) taken in bin order from a
+                                  device counter; 0 fixed, each warp striding over them */
+  uint32_t reserved[3];
 } gerbil_opts;
 
 /* Per-call statistics of a count. */
@@ -219,6 +224,16 @@ int gerbil_counts_to_host(const gerbil_counts* counts, uint64_t* keys, uint32_t*
                           uint64_t cap);
 
 void gerbil_counts_free(gerbil_counts* counts);
+
+/* Memory-throughput probe (the paper has no counterpart; a measurement helper for the
+ * roofline of the insert kernel).  Runs one kernel in which every thread performs per_thread
+ * operations at pseudo-random 32-byte slots of a device array of `bytes` bytes, allocated from
+ * the context: op 0 = 8-byte atomic add, 1 = 32-byte relaxed load, 2 = 32-byte load then atomic
+ * add on the same slot (the shape of a found-key insert), 3 = 8-byte compare-and-swap.  A
+ * footprint below the L2 size measures L2; a larger one measures HBM.  *gops receives
+ * operations per second / 1e9, timed with CUDA events on the context's stream.
+ * Errors: E_INVAL, E_NOMEM, E_CUDA. */
+int gerbil_membench(gerbil_ctx* ctx, uint64_t bytes, int op, uint64_t per_thread, double* gops);
 
 /* Counting without any device allocation.  The paper has no counterpart: this entry point is
  * for callers that cannot call cudaMalloc -- for example code whose device memory is owned by

@@ -184,18 +184,16 @@ __device__ __forceinline__ bool key_less(const unsigned long long a[W],
   return false;
 }
 
-// 64-bit hash of a key: per-word multiply/xorshift rounds, MurmurHash3-style finalizer.
+// 64-bit hash of a key: one multiply per word, then a multiply/xorshift finalizer (the slot
+// index uses the low 32 bits, the tag bits 34..63).
 template <int W>
 __device__ __forceinline__ unsigned long long key_hash(const unsigned long long key[W]) {
-  unsigned long long h = 0x9E3779B97F4A7C15ull * (unsigned long long)(W + 1);
+  unsigned long long h = 0x243F6A8885A308D3ull;
 #pragma unroll
-  for (int j = 0; j < W; ++j) {
-    h ^= key[j];
-    h *= 0xff51afd7ed558ccdull;
-    h ^= h >> 33;
-  }
-  h *= 0xc4ceb9fe1a85ec53ull;
-  h ^= h >> 33;
+  for (int j = 0; j < W; ++j) h = (h ^ key[j]) * 0x9E3779B97F4A7C15ull;
+  h ^= h >> 32;
+  h *= 0xD6E8FEB86659FD93ull;
+  h ^= h >> 32;
   return h;
 }
 

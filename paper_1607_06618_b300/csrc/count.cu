@@ -147,12 +147,18 @@ __global__ void __launch_bounds__(256) item_map_kernel(const BinWork* __restrict
   }
 }
 
-constexpr int PIPE = 1;  // k-mers per lane whose probes are in flight together
 
 struct WarpSmem {
   uint32_t koff[ITEM_KMERS];
   unsigned long long pos[ITEM_KMERS];
 };
+
+// A lane takes KPL consecutive k-mers of the item.  Within a super-mer the next k-mer and its
+// reverse complement follow from the previous ones by one base: shift the forward key left by
+// two bits and append the new base; shift the reverse complement right by two bits and put the
+// new base's complement on top.  Only the lane's first k-mer and the first k-mer of every new
+// super-mer are cut from the packed words in full.
+constexpr int KPL = ITEM_KMERS / 32;
 
 template <int W, int WS>
 __device__ __forceinline__ void insert_item(const CountParams& P, uint32_t wi, const BinWork& wk,
@@ -180,51 +186,56 @@ __device__ __forceinline__ void insert_item(const CountParams& P, uint32_t wi, c
     if (cnt < 32) break;
   }
   __syncwarp();
-  // a lane's k-mers in groups of PIPE: keys, hashes and the first probe of a group are all
-  // issued before any of them is resolved, so their memory latencies overlap
   constexpr int SW = slot_words(WS);
   unsigned long long* tab = P.arena + wk.table_off * SW;
+  const int k = P.k;
+  const int nb0 = k - 32 * (W - 1);  // bases in key word 0
+  const unsigned long long mask0 = (nb0 == 32) ? ~0ull : ((1ull << (2 * nb0)) - 1ull);
+  const uint32_t ja = j0 + (uint32_t)lane * KPL;
+  const uint32_t jb = min(ja + (uint32_t)KPL, j1);
+  unsigned long long fwd[W], rc[W], pos = 0;
+  uint32_t sidx = 0, send = 0;  // current super-mer and its first k-mer past the end
 #pragma unroll 1
-  for (int r0 = 0; r0 < ITEM_KMERS / 32; r0 += PIPE) {
-    unsigned long long st[PIPE][WS], h[PIPE], v[PIPE][SW];
-    uint32_t s0[PIPE];
-    bool val[PIPE];
-#pragma unroll
-    for (int p = 0; p < PIPE; ++p) {
-      const uint32_t j = j0 + lane + 32 * (r0 + p);
-      val[p] = j < j1;
-      if (!val[p]) continue;
-      uint32_t lo = 0, hi = ns;
-      while (hi - lo > 1) {
-        const uint32_t mid = (lo + hi) >> 1;
-        if (S.koff[mid] <= j) lo = mid; else hi = mid;
-      }
-      const unsigned long long pos = S.pos[lo] + (j - S.koff[lo]);
-      unsigned long long key[W];
-      load_kmer<W>(P.packed, pos, P.k, key);
-      if (P.canonical) {
-        unsigned long long rc[W];
-        revcomp<W>(key, P.k, rc);
-        if (key_less<W>(rc, key)) {
-#pragma unroll
-          for (int q = 0; q < W; ++q) key[q] = rc[q];
+  for (uint32_t j = ja; j < jb; ++j) {
+    if (j == ja || j >= send) {  // cut the k-mer in full
+      if (j == ja) {
+        uint32_t lo = 0, hi = ns;
+        while (hi - lo > 1) {
+          const uint32_t mid = (lo + hi) >> 1;
+          if (S.koff[mid] <= j) lo = mid; else hi = mid;
         }
+        sidx = lo;
+      } else {
+        ++sidx;
       }
-      h[p] = key_hash<W>(key);
-      to_stored<W, WS>(key, st[p]);
-      s0[p] = slot_of(h[p], wk.cap);
-      load_slot<SW>(tab + (unsigned long long)s0[p] * SW, v[p]);
-    }
+      send = (sidx + 1 < ns) ? S.koff[sidx + 1] : 0xFFFFFFFFu;
+      pos = S.pos[sidx] + (j - S.koff[sidx]);
+      load_kmer<W>(P.packed, pos, k, fwd);
+      revcomp<W>(fwd, k, rc);
+    } else {  // roll by one base
+      const unsigned long long q = pos + (unsigned long long)k;  // the new last base
+      const unsigned long long b = (__ldg(P.packed + (q >> 5)) >> (62 - 2 * (int)(q & 31))) & 3ull;
 #pragma unroll
-    for (int p = 0; p < PIPE; ++p) {
-      if (!val[p]) continue;
-      const int res = table_insert_from<WS>(tab, wk.cap, st[p], h[p], P.theta, P.spin_limit, s0[p], v[p]);
-      if (res) {
-        unsigned long long key[W];
-        from_stored<W, WS>(st[p], key);
-        to_overflow<W>(P, wi, key, res);
-      }
+      for (int t = 0; t < W - 1; ++t) fwd[t] = (fwd[t] << 2) | (fwd[t + 1] >> 62);
+      fwd[W - 1] = (fwd[W - 1] << 2) | b;
+      fwd[0] &= mask0;
+#pragma unroll
+      for (int t = W - 1; t >= 1; --t) rc[t] = (rc[t] >> 2) | (rc[t - 1] << 62);
+      rc[0] = (rc[0] >> 2) | ((3ull - b) << (2 * nb0 - 2));
+      ++pos;
     }
+    unsigned long long key[W];
+    const bool use_rc = P.canonical && key_less<W>(rc, fwd);
+#pragma unroll
+    for (int t = 0; t < W; ++t) key[t] = use_rc ? rc[t] : fwd[t];
+    const unsigned long long h = key_hash<W>(key);
+    unsigned long long st[WS];
+    to_stored<W, WS>(key, st);
+    const uint32_t s0 = slot_of(h, wk.cap);
+    unsigned long long v[SW];
+    load_slot<SW>(tab + (unsigned long long)s0 * SW, v);
+    const int res = table_insert_from<WS>(tab, wk.cap, st, h, P.theta, P.spin_limit, s0, v);
+    if (res) to_overflow<W>(P, wi, key, res);
   }
   __syncwarp();  // S is reused by the next item
 }
@@ -237,18 +248,31 @@ __device__ __forceinline__ void count_item(const CountParams& P, unsigned long l
   insert_item<W, WS>(P, wi, wk, (uint32_t)(item - wk.item_begin), s_lo, S, lane);
 }
 
-// Warps stride over the items in bin order, so the bins in flight at any moment are few and
-// their tables stay hot in L2.  Launched with as many CTAs as fit on the GPU (persistent) or
-// one warp per item.
+// Warps take items in bin order from a device counter (the next one is requested while the
+// current one runs), so the bins in flight at any moment are few and their tables stay hot in
+// L2; or (schedule 0) each warp strides over the items.  Launched with as many CTAs as fit on
+// the GPU (persistent) or one warp per item.
 template <int W, int WS>
 __global__ void __launch_bounds__(256) insert_kernel(CountParams P) {
   __shared__ WarpSmem S[8];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const unsigned long long nw = (unsigned long long)gridDim.x * (blockDim.x >> 5);
-  for (unsigned long long item = blockIdx.x * (unsigned long long)(blockDim.x >> 5) + warp;
-       item < P.nitems; item += nw) {
+  if (!P.schedule) {  // fixed: warp w takes items base + w, base + w + nw, ...
+    const unsigned long long nw = (unsigned long long)gridDim.x * (blockDim.x >> 5);
+    for (unsigned long long item = P.item_base + blockIdx.x * (unsigned long long)(blockDim.x >> 5) + warp;
+         item < P.nitems; item += nw)
+      count_item<W, WS>(P, item, __ldg(P.imap + item), S[warp], lane);
+    return;
+  }
+  unsigned long long* queue = P.queue;
+  unsigned long long item = 0;
+  if (lane == 0) item = P.item_base + atomicAdd(queue, 1ull);
+  item = __shfl_sync(0xFFFFFFFFu, item, 0);
+  while (item < P.nitems) {
+    unsigned long long next = 0;
+    if (lane == 0) next = P.item_base + atomicAdd(queue, 1ull);
     const unsigned long long entry = __ldg(P.imap + item);
     count_item<W, WS>(P, item, entry, S[warp], lane);
+    item = __shfl_sync(0xFFFFFFFFu, next, 0);
   }
 }
 
@@ -459,7 +483,11 @@ __device__ __forceinline__ uint32_t warp_excl_scan(uint32_t x, int lane, uint32_
 }
 
 // One compaction chunk: count the rows (meta words only), take room for them with one atomic,
-// then write them and zero the live slots.
+// then write them and zero the live slots.  Loads are issued in batches (all of a batch before
+// any is used), since a warp issues in order and would otherwise wait once per slot.
+constexpr int CB_META = 8;  // meta words per lane per batch (count pass)
+constexpr int CB_SLOT = 4;  // slots per lane per batch (write pass)
+
 template <int W, int WS>
 __device__ __forceinline__ void compact_chunk(const FusedParams& F, const BinWork& wk, uint32_t c,
                                               int lane) {
@@ -467,10 +495,18 @@ __device__ __forceinline__ void compact_chunk(const FusedParams& F, const BinWor
   unsigned long long* tab = F.c.arena + wk.table_off * SW;
   const uint32_t lo = c * CHUNK_SLOTS, hi = min(lo + (uint32_t)CHUNK_SLOTS, wk.cap);
   uint32_t mine = 0, live = 0;
-  for (uint32_t s = lo + lane; s < hi; s += 32) {
-    const unsigned long long mt = ld_relaxed(tab + (unsigned long long)s * SW);
-    live += mt != 0ull;
-    mine += (mt != 0ull && (uint32_t)mt >= F.min_count);
+  for (uint32_t b0 = lo; b0 < hi; b0 += 32 * CB_META) {
+    unsigned long long mt[CB_META];
+#pragma unroll
+    for (int u = 0; u < CB_META; ++u) {
+      const uint32_t s = b0 + u * 32 + lane;
+      mt[u] = s < hi ? ld_relaxed(tab + (unsigned long long)s * SW) : 0ull;
+    }
+#pragma unroll
+    for (int u = 0; u < CB_META; ++u) {
+      live += mt[u] != 0ull;
+      mine += (mt[u] != 0ull && (uint32_t)mt[u] >= F.min_count);
+    }
   }
   uint32_t total = 0, tlive = 0;
   const uint32_t excl = warp_excl_scan(mine, lane, &total);
@@ -481,29 +517,41 @@ __device__ __forceinline__ void compact_chunk(const FusedParams& F, const BinWor
     if (tlive) atomicAdd(&F.c.ctr->distinct, (unsigned long long)tlive);
   }
   unsigned long long row = __shfl_sync(0xFFFFFFFFu, base, 0) + excl;
-  for (uint32_t s = lo + lane; s < hi; s += 32) {
-    unsigned long long* sp = tab + (unsigned long long)s * SW;
-    unsigned long long v[SW];
-    load_slot<SW>(sp, v);
-    if (v[0] == 0ull) continue;
-    bool all = true;
+  for (uint32_t b0 = lo; b0 < hi; b0 += 32 * CB_SLOT) {
+    unsigned long long v[CB_SLOT][SW];
 #pragma unroll
-    for (int j = 0; j < WS; ++j) all &= (v[1 + j] & MARK) != 0ull;
-    if (!all) set_err(F.c.ctr, ERR_STATE);  // a claimed slot whose key was never written
-    if ((uint32_t)v[0] >= F.min_count) {
-      if (row < F.out_cap) {
-        unsigned long long key[W];
-        from_stored<W, WS>(&v[1], key);
-#pragma unroll
-        for (int j = 0; j < W; ++j) F.out_keys[row * W + j] = key[j];
-        F.out_counts[row] = (uint32_t)v[0];
+    for (int u = 0; u < CB_SLOT; ++u) {
+      const uint32_t s = b0 + u * 32 + lane;
+      if (s < hi) {
+        load_slot<SW>(tab + (unsigned long long)s * SW, v[u]);
       } else {
-        set_err(F.c.ctr, ERR_OUT_FULL);
+#pragma unroll
+        for (int i = 0; i < SW; ++i) v[u][i] = 0ull;
       }
-      ++row;
     }
 #pragma unroll
-    for (int i = 0; i < SW; i += 2) st_relaxed_v2(sp + i, 0ull, 0ull);
+    for (int u = 0; u < CB_SLOT; ++u) {
+      if (v[u][0] == 0ull) continue;
+      unsigned long long* sp = tab + (unsigned long long)(b0 + u * 32 + lane) * SW;
+      bool all = true;
+#pragma unroll
+      for (int j = 0; j < WS; ++j) all &= (v[u][1 + j] & MARK) != 0ull;
+      if (!all) set_err(F.c.ctr, ERR_STATE);  // a claimed slot whose key was never written
+      if ((uint32_t)v[u][0] >= F.min_count) {
+        if (row < F.out_cap) {
+          unsigned long long key[W];
+          from_stored<W, WS>(&v[u][1], key);
+#pragma unroll
+          for (int j = 0; j < W; ++j) F.out_keys[row * W + j] = key[j];
+          F.out_counts[row] = (uint32_t)v[u][0];
+        } else {
+          set_err(F.c.ctr, ERR_OUT_FULL);
+        }
+        ++row;
+      }
+#pragma unroll
+      for (int i = 0; i < SW; i += 2) st_relaxed_v2(sp + i, 0ull, 0ull);
+    }
   }
 }
 
@@ -647,7 +695,7 @@ cudaError_t launch_item_map(const CountParams& p, cudaStream_t st) {
 // persistent: as many CTAs as are resident at once (occupancy query), each warp striding over
 // the items; otherwise one warp per item.
 cudaError_t launch_insert(int k, const CountParams& p, int persistent, int nsm, cudaStream_t st) {
-  const unsigned long long need = (p.nitems + 7) / 8;
+  const unsigned long long need = (p.nitems - p.item_base + 7) / 8;
   if (need == 0) return cudaSuccess;
   const int W = (2 * k + 63) / 64, WS = stored_words(k);
 #define L_INSERT(w, ws)                                                                          \

@@ -72,12 +72,15 @@ struct CountParams {
   const uint32_t* sm_koff;
   const BinWork* work;
   uint32_t nwork;
-  unsigned long long nitems;     // warp work items over all bins
+  unsigned long long nitems;     // end of the items of this launch
+  unsigned long long item_base;  // first item of this launch
+  unsigned long long* queue;     // item counter (schedule 1), zero before the launch
   unsigned long long* imap;      // item -> (work index << 32 | first super-mer of the item)
   int k;
   int canonical;
   uint32_t theta;                // max probes (Alg. 1)
-  uint32_t spin_limit;           // bounded wait on an unpublished slot
+  uint32_t spin_limit;           // bounded wait on a slot whose key is being written
+  int schedule;                  // 1: items from a device counter in order; 0: fixed striding
   unsigned long long* arena;     // all tables, slot_words_for_k(k) words per slot
   unsigned long long* ovf;       // overflow area, W words per k-mer
   unsigned long long ovf_cap;

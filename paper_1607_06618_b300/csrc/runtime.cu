@@ -186,6 +186,7 @@ void gerbil_opts_default(gerbil_opts* o) {
   o->persistent = 1;
   o->ring_slots = 0;
   o->fused = 0;
+  o->schedule = 1;
 }
 
 const char* gerbil_strerror(int s) {
@@ -273,6 +274,17 @@ void gerbil_destroy(gerbil_ctx* ctx) {
   if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
   delete ctx;
 }
+
+// Device memory from the context's pool and budget, for helpers outside this file.
+int gerbil_internal_alloc(gerbil_ctx* ctx, void** p, size_t bytes, void** stream, int* nsm) {
+  if (!ctx) return GERBIL_E_INVAL;
+  CK(cudaSetDevice(ctx->device));
+  *stream = ctx->stream;
+  *nsm = ctx->nsm;
+  return dev_alloc(ctx, p, bytes);
+}
+
+void gerbil_internal_free(gerbil_ctx* ctx, void* p, size_t bytes) { dev_free(ctx, p, bytes); }
 
 int gerbil_profile(gerbil_ctx* ctx, int enable) {
   if (!ctx) return GERBIL_E_INVAL;
@@ -797,6 +809,176 @@ static int count_fused(gerbil_ctx* ctx, const gerbil_bins* b, const std::vector<
 #undef CKF
 }
 
+// ---- phase two in waves -------------------------------------------------------------------------
+// Bins are grouped into waves whose tables together fit in half of L2; every wave reuses the
+// same arena region: clear it, insert the wave's items, compact its tables.  A table is thus
+// created, filled and read while it is hot in L2.  Returns WAVES_FALLBACK when the overflow
+// area was used (the all-tables form below merges overflow counts).
+static const int WAVES_FALLBACK = -2;
+
+static int count_waves(gerbil_ctx* ctx, const gerbil_bins* b, const std::vector<int32_t>& list,
+                       int k, uint32_t min_count, const gerbil_opts& opts, double ratio,
+                       double alpha, uint32_t theta, uint32_t spin_limit, gerbil_counts** out) {
+  const int W = words_for(k);
+  const int SW = gerbil::slot_words_for_k(k);
+  cudaStream_t st = ctx->stream;
+  std::vector<BinWork> work;
+  uint64_t occ = 0, items = 0, cap_sum = 0;
+  for (int32_t bi : list) {
+    if (b->nkmers[bi] == 0) continue;
+    BinWork w{};
+    w.sm_begin = b->sm_begin[bi];
+    w.n_super = (uint32_t)b->nsuper[bi];
+    w.n_kmers = (uint32_t)b->nkmers[bi];
+    const double est = std::max(1.0, std::ceil(ratio * (double)w.n_kmers));
+    w.cap = (uint32_t)std::min<uint64_t>((uint64_t)std::ceil(est / alpha) + 16, 0xFFFFF000ull);
+    w.item_begin = (uint32_t)items;
+    items += (w.n_kmers + gerbil::ITEM_KMERS - 1) / gerbil::ITEM_KMERS;
+    occ += w.n_kmers;
+    cap_sum += w.cap;
+    work.push_back(w);
+  }
+  if (items >= (1ull << 32)) return fail(ctx, GERBIL_E_INVAL, "too many work items");
+  const size_t nw = work.size();
+  const uint64_t budget = opts.ring_slots ? (uint64_t)opts.ring_slots
+                                          : std::max<uint64_t>(4096, (uint64_t)(0.5 * ctx->l2_bytes) / (SW * 8));
+  struct Wave { size_t w0, w1; uint64_t slots, it0, it1; };
+  std::vector<Wave> waves;
+  uint64_t region = 0;
+  for (size_t i = 0; i < nw;) {
+    Wave v{i, i, 0, work[i].item_begin, 0};
+    while (v.w1 < nw && (v.w1 == v.w0 || v.slots + work[v.w1].cap <= budget)) {
+      work[v.w1].table_off = v.slots;
+      v.slots += work[v.w1].cap;
+      ++v.w1;
+    }
+    v.it1 = (v.w1 < nw) ? work[v.w1].item_begin : items;
+    region = std::max(region, v.slots);
+    waves.push_back(v);
+    i = v.w1;
+  }
+  const uint64_t ovf_cap = opts.overflow_slots ? (uint64_t)opts.overflow_slots
+                                               : std::max<uint64_t>(1 << 16, occ / 32);
+  int rc;
+  bool grown = false;
+  const size_t arena_need = region * SW * 8;
+  if ((rc = scratch(ctx, &ctx->arena, &ctx->arena_bytes, arena_need + 256, &grown))) return rc;
+  if (grown) ctx->arena_dirty = ctx->arena_bytes;
+  if ((rc = scratch(ctx, &ctx->ovf, &ctx->ovf_bytes, ovf_cap * W * 8 + 256))) return rc;
+  auto up = [](size_t x) { return (x + 255) & ~size_t(255); };
+  const size_t o_work = 0, o_bovf = up(nw * sizeof(BinWork)), o_queue = o_bovf + up(nw * 4),
+               o_imap = o_queue + up(waves.size() * 8), small_need = o_imap + up(items * 8) + 256;
+  if ((rc = scratch(ctx, &ctx->small, &ctx->small_bytes, small_need))) return rc;
+  char* sm = (char*)ctx->small;
+
+  const uint64_t out_cap = std::max<uint64_t>(1, std::min<uint64_t>(occ, cap_sum));
+  gerbil_counts* res = new (std::nothrow) gerbil_counts;
+  if (!res) return GERBIL_E_NOMEM;
+  res->ctx = ctx;
+  res->W = W;
+  res->bytes = out_cap * (W * 8 + 4);
+  if ((rc = dev_alloc(ctx, (void**)&res->keys, out_cap * W * 8))) { delete res; return rc; }
+  if ((rc = dev_alloc(ctx, (void**)&res->counts, out_cap * 4))) {
+    dev_free(ctx, res->keys, out_cap * W * 8);
+    delete res;
+    return rc;
+  }
+  auto drop = [&]() { gerbil_counts_free(res); };
+#define CKW(call)                                                                          \
+  do {                                                                                     \
+    cudaError_t e_ = (call);                                                               \
+    if (e_ != cudaSuccess) {                                                               \
+      drop();                                                                              \
+      ctx->arena_dirty = ctx->arena_bytes;                                                 \
+      return fail(ctx, GERBIL_E_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    }                                                                                      \
+  } while (0)
+
+  ctx->times.calls++;
+  ph_begin(ctx, PH_CLEAR);
+  CKW(cudaMemsetAsync(ctx->ctr, 0, sizeof(Counters), st));
+  CKW(cudaMemsetAsync(sm + o_bovf, 0, o_imap - o_bovf, st));
+  if (nw) CKW(cudaMemcpyAsync(sm + o_work, work.data(), nw * sizeof(BinWork), cudaMemcpyHostToDevice, st));
+  gerbil::CountParams cp{};
+  cp.packed = b->packed;
+  cp.sm_pos = b->sm_pos;
+  cp.sm_koff = b->sm_koff;
+  cp.work = (const BinWork*)(sm + o_work);
+  cp.nwork = (uint32_t)nw;
+  cp.imap = (unsigned long long*)(sm + o_imap);
+  cp.k = k;
+  cp.canonical = opts.canonical ? 1 : 0;
+  cp.theta = theta;
+  cp.spin_limit = spin_limit;
+  cp.arena = (unsigned long long*)ctx->arena;
+  cp.ovf = (unsigned long long*)ctx->ovf;
+  cp.ovf_cap = ovf_cap;
+  cp.bin_ovf = (uint32_t*)(sm + o_bovf);
+  cp.ctr = ctx->ctr;
+  cp.schedule = opts.schedule;
+  if (items) {
+    cp.nitems = items;
+    CKW(gerbil::launch_item_map(cp, st));
+    ctx->times.kernel_launches++;
+  }
+  ph_end(ctx, PH_CLEAR);
+  ph_begin(ctx, PH_INSERT);
+  for (size_t wv = 0; wv < waves.size(); ++wv) {
+    const Wave& v = waves[wv];
+    CKW(cudaMemsetAsync(ctx->arena, 0, v.slots * SW * 8, st));
+    cp.item_base = v.it0;
+    cp.nitems = v.it1;
+    cp.queue = (unsigned long long*)(sm + o_queue) + wv;
+    CKW(gerbil::launch_insert(k, cp, opts.persistent, ctx->nsm, st));
+    gerbil::CompactParams xp{};
+    xp.work = cp.work + v.w0;
+    xp.nwork = (uint32_t)(v.w1 - v.w0);
+    xp.slot_lo = 0;
+    xp.slot_hi = v.slots;
+    xp.arena = cp.arena;
+    xp.bin_ovf = cp.bin_ovf + v.w0;
+    xp.mode = 0;
+    xp.min_count = min_count;
+    xp.out_keys = res->keys;
+    xp.out_counts = res->counts;
+    xp.out_cap = out_cap;
+    xp.ctr = ctx->ctr;
+    CKW(gerbil::launch_compact(k, xp, ctx->nsm, st));
+    ctx->times.kernel_launches += 2;
+    ctx->times.insert_launches++;
+  }
+  ph_end(ctx, PH_INSERT);
+  ctx->arena_dirty = std::max(ctx->arena_dirty, arena_need);  // the last wave's tables stay
+  if ((rc = read_counters(ctx))) {
+    drop();
+    return rc;
+  }
+  const Counters h = *ctx->hctr;
+  if (h.err & (gerbil::ERR_STATE | gerbil::ERR_OUT_FULL | gerbil::ERR_SPIN)) {
+    drop();
+    return fail(ctx, GERBIL_E_STATE, "device consistency check failed");
+  }
+  if (h.ovf_count || (h.err & gerbil::ERR_OVF_FULL)) {
+    drop();
+    return WAVES_FALLBACK;
+  }
+  gerbil_count_stats stats{};
+  stats.bins = (uint32_t)list.size();
+  stats.occurrences = occ;
+  stats.emitted = h.out_count;
+  stats.distinct = h.distinct;
+  stats.table_slots = cap_sum;
+  res->n = h.out_count;
+  res->stats = stats;
+  if (occ > 0) {
+    ctx->ratio = (double)h.distinct / (double)occ;
+    ctx->ratio_known = true;
+  }
+  *out = res;
+  return GERBIL_OK;
+#undef CKW
+}
+
 static int count_impl(gerbil_ctx* ctx, const gerbil_bins* b, const std::vector<int32_t>& list,
                       int k, uint32_t min_count, const gerbil_opts& opts, gerbil_counts** out) {
   const int W = words_for(k);
@@ -814,9 +996,12 @@ static int count_impl(gerbil_ctx* ctx, const gerbil_bins* b, const std::vector<i
   stats.bins = (uint32_t)list.size();
   stats.occurrences = occ;
 
-  if (opts.fused) {
+  if (opts.fused == 1) {
     const int rc = count_fused(ctx, b, list, k, min_count, opts, ratio, alpha, theta, spin_limit, out);
     if (rc != FUSED_FALLBACK) return rc;
+  } else if (opts.fused == 2) {
+    const int rc = count_waves(ctx, b, list, k, min_count, opts, ratio, alpha, theta, spin_limit, out);
+    if (rc != WAVES_FALLBACK) return rc;
   }
 
   for (int round = 0; round < 4; ++round) {
@@ -899,6 +1084,8 @@ static int count_impl(gerbil_ctx* ctx, const gerbil_bins* b, const std::vector<i
     cp.work = dwork;
     cp.nwork = (uint32_t)work.size();
     cp.nitems = items;
+    cp.item_base = 0;
+    cp.queue = &((Counters*)ctx->ctr)->queue_head;
     cp.imap = (unsigned long long*)((char*)bin_ovf + ((work.size() * 4 + 255) & ~size_t(255)));
     cp.k = k;
     cp.canonical = opts.canonical ? 1 : 0;
@@ -909,6 +1096,7 @@ static int count_impl(gerbil_ctx* ctx, const gerbil_bins* b, const std::vector<i
     cp.ovf_cap = ovf_cap;
     cp.bin_ovf = bin_ovf;
     cp.ctr = ctx->ctr;
+    cp.schedule = opts.schedule;
     if (items) {
       CKR(gerbil::launch_item_map(cp, st));  // preparation: timed with the clears
       ctx->times.kernel_launches++;

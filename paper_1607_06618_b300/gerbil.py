@@ -36,7 +36,7 @@ ABI_SYMBOLS = (
     "gerbil_destroy", "gerbil_partition", "gerbil_bins_info", "gerbil_bin_stats",
     "gerbil_bins_export", "gerbil_bins_free", "gerbil_count", "gerbil_count_batch",
     "gerbil_counts_info", "gerbil_counts_view", "gerbil_counts_to_host", "gerbil_counts_free",
-    "gerbil_profile", "gerbil_get_phase_times", "gerbil_count_small_noalloc",
+    "gerbil_profile", "gerbil_get_phase_times", "gerbil_count_small_noalloc", "gerbil_membench",
 )
 
 
@@ -59,7 +59,7 @@ class gerbil_opts(ctypes.Structure):
                 ("load_factor", ctypes.c_float), ("distinct_ratio", ctypes.c_float),
                 ("overflow_slots", ctypes.c_uint32), ("persistent", ctypes.c_int32),
                 ("ring_slots", ctypes.c_uint32), ("fused", ctypes.c_int32),
-                ("reserved", ctypes.c_uint32 * 4)]
+                ("schedule", ctypes.c_int32), ("reserved", ctypes.c_uint32 * 3)]
 
 
 class gerbil_count_stats(ctypes.Structure):
@@ -119,6 +119,7 @@ def load() -> ctypes.CDLL:
         "gerbil_counts_to_host": (I32, [P, P, P, U64]),
         "gerbil_counts_free": (None, [P]),
         "gerbil_profile": (I32, [P, I32]),
+        "gerbil_membench": (I32, [P, U64, I32, U64, ctypes.POINTER(ctypes.c_double)]),
         "gerbil_count_small_noalloc": (I32, [P, P, U64, U64, I32, U32, I32, P, P, U64,
                                              ctypes.POINTER(U64), P]),
         "gerbil_get_phase_times": (I32, [P, ctypes.POINTER(gerbil_phase_times)]),
@@ -171,6 +172,12 @@ def gerbil_get_phase_times(ctx):
     t = gerbil_phase_times()
     _check(load().gerbil_get_phase_times(ctx, ctypes.byref(t)), ctx)
     return t.as_dict()
+
+
+def gerbil_membench(ctx, nbytes: int, op: int, per_thread: int) -> float:
+    g = ctypes.c_double()
+    _check(load().gerbil_membench(ctx, nbytes, op, per_thread, ctypes.byref(g)), ctx)
+    return g.value
 
 
 def _reads_struct(seq, offsets):

@@ -137,16 +137,17 @@ def test_count_config1_full_batch_grid_and_per_bin(g):
     seq, offs, p = synth.workload("uniform-20k-k32")
     want = oracle.count(seq, offs, p["k"], min_count=1)
     assert int(want[1].sum()) == oracle.windows(seq, offs, p["k"])
-    for batch, persistent, fused in ((True, 1, 0), (True, 0, 0), (True, 1, 1), (False, 1, 0),
-                                     (False, 1, 1)):
+    for batch, persistent, fused in ((True, 1, 0), (True, 0, 0), (True, 1, 1), (True, 1, 2),
+                                     (False, 1, 0), (False, 1, 1), (False, 1, 2)):
         got, _ = _gpu_count(g, seq, offs, p["k"], p["m"], p["nbins"], 1, batch=batch,
                             persistent=persistent, fused=fused)
         assert_same_rows(got, want)
 
 
 def test_fused_ring_wrap_dedicated_and_classic(g):
-    """Persistent form with a tiny table ring: ring regions are reused many times (each reuse
-    waits for the previous tenant's compaction) and the larger bins get dedicated tables."""
+    """Fused form with a tiny table ring: ring regions are reused many times (each reuse waits
+    for the previous tenant's compaction) and the larger bins get dedicated tables; waves of
+    several sizes; the two-kernel form."""
     seq, offs = synth.random_small(3000, 100, 300, p_n=0.002, seed=21)
     seq = np.concatenate([seq, seq[: int(offs[800])]])
     offs = np.concatenate([offs, offs[1:801] + offs[-1]])
@@ -161,6 +162,9 @@ def test_fused_ring_wrap_dedicated_and_classic(g):
     # a two-kernel call leaves tables in the arena; the next fused call must clear them
     got, _ = _gpu_count(g, seq, offs, k, 9, 97, 2, fused=1, ring_slots=20000)
     assert_same_rows(got, want)
+    for wave in (3000, 20000, 0):
+        got, st = _gpu_count(g, seq, offs, k, 9, 97, 2, fused=2, ring_slots=wave)
+        assert_same_rows(got, want)
     # forced overflow in the fused form falls back to the overflow recount
     got, st = _gpu_count(g, seq, offs, k, 9, 97, 2, fused=1, max_probes=1, distinct_ratio=0.05,
                          overflow_slots=1 << 22)
