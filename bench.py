@@ -157,13 +157,20 @@ def run_cpu_oracle(seq, offs, p, nreads_sample):
     return occ, dt, n
 
 
+def _host_workload(name):
+    from paper_1607_06618_b300 import synth
+    if name in synth.TORCH_WORKLOADS:
+        s, o, p = synth.torch_workload(name, device="cpu")
+        return s.numpy(), o.numpy().view(np.uint64), p
+    return synth.workload(name)
+
+
 def main_reference(a, world, rank):
     if rank != 0:
         return 0
-    from paper_1607_06618_b300 import synth
     import oracle
     oracle.build()
-    seq, offs, p = synth.workload(a.workload)
+    seq, offs, p = _host_workload(a.workload)
     for _ in range(a.warmup):
         run_cpu_oracle(seq, offs, p, a.ref_sample_reads)
     times, occ = [], 0
@@ -188,6 +195,7 @@ def main_reference(a, world, rank):
 
 def _config(name, p, seq, offs):
     return {"workload": name, "k": p["k"], "m": p["m"], "nbins": p["nbins"],
+            "bins": "log-normal shares (sigma 1)" if p.get("bin_bounds") is not None else "uniform",
             "min_count": p["min_count"], "reads": int(offs.size - 1),
             "bases": int(seq.size), "mode": "count_batch over all bins (persistent insert grid)",
             "l2": "inputs larger than L2 (%.0f MB ASCII reads > 126 MB)" % (seq.size / 1e6)}
@@ -202,11 +210,16 @@ def main_ours(a, world, rank, local):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    seq, offs, p = synth.workload(a.workload)
+    if a.workload in synth.TORCH_WORKLOADS:  # drawn on the GPU, copied to the host once
+        s_dev, o_dev, p = synth.torch_workload(a.workload, device="cuda")
+        seq, offs = s_dev.cpu().numpy(), o_dev.cpu().numpy().view(np.uint64)
+    else:
+        seq, offs, p = synth.workload(a.workload)
+        s_dev = torch.from_numpy(seq).cuda()
+        o_dev = torch.from_numpy(offs.view(np.int64)).cuda()
     k, m, nbins, mc = p["k"], p["m"], p["nbins"], p["min_count"]
+    bb = p.get("bin_bounds")
     W = (2 * k + 63) // 64
-    s_dev = torch.from_numpy(seq).cuda()
-    o_dev = torch.from_numpy(offs.view(np.int64)).cuda()
     stream = torch.cuda.current_stream()
     ctx = gerbil.Context(local, stream=stream.cuda_stream)
     kw = {}
@@ -219,7 +232,7 @@ def main_ours(a, world, rank, local):
     info = {}
 
     def step(record=False):
-        bins = ctx.partition(s_dev, o_dev, k, m, nbins, opts)
+        bins = ctx.partition(s_dev, o_dev, k, m, nbins, opts, bb)
         res = ctx.count_batch(bins, None, k, mc, opts)
         st = res.info()[2]
         if record:
@@ -294,7 +307,7 @@ def main_ours(a, world, rank, local):
     # batched (one persistent launch) vs one count call per bin, phase two only
     bvp = None
     if a.per_bin_steps > 0 and rank == 0:
-        bins = ctx.partition(s_dev, o_dev, k, m, nbins, opts)
+        bins = ctx.partition(s_dev, o_dev, k, m, nbins, opts, bb)
         torch.cuda.synchronize()
         tb = time.perf_counter()
         for _ in range(a.per_bin_steps):
@@ -339,7 +352,7 @@ def main_ours(a, world, rank, local):
         kp, cp = keys_pin.numpy().view(np.uint64), cnt_pin.numpy().view(np.uint32)
 
         def e2e_step():
-            bins = ctx.partition(hs, ho, k, m, nbins, opts)
+            bins = ctx.partition(hs, ho, k, m, nbins, opts, bb)
             res = ctx.count_batch(bins, None, k, mc, opts)
             gerbil.gerbil_counts_to_host(res.handle, kp, cp)
             res.free()

@@ -359,8 +359,9 @@ __global__ void __launch_bounds__(256, 3) compact_kernel(CompactParams P) {
           live = false;
         }
       }
-      bool take = live && P.mode == 0;
-      if (live && any_ovf) {
+      // mode 0: bins without overflow; 1: bins with overflow, merged; 2: count rows only
+      bool take = live && P.mode != 1;
+      if (live && any_ovf && P.mode != 2) {
         const uint32_t wi = work_of_slot(P.work, P.nwork, slot);
         const bool deferred = P.bin_ovf[wi] != 0u;
         take = (P.mode == 0) ? !deferred : deferred;
@@ -382,6 +383,7 @@ __global__ void __launch_bounds__(256, 3) compact_kernel(CompactParams P) {
       e += c ? 1u : 0u;
     }
     unsigned long long row = cta_append(e, P.ctr, wsum, &cbase);
+    if (P.mode == 2) continue;  // counting only
 #pragma unroll
     for (int u = 0; u < COMPACT_UNROLL; ++u) {
       if (!cnt[u]) continue;

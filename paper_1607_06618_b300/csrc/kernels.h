@@ -112,7 +112,8 @@ struct CompactParams {
   unsigned long long slot_lo, slot_hi;  // slots of the arena to scan
   unsigned long long* arena;
   const uint32_t* bin_ovf;
-  int mode;                      // 0: skip bins with overflow; 1: only those, merged with O
+  int mode;                      // 0: skip bins with overflow; 1: only those, merged with O;
+                                 // 2: count rows only (out_count), write nothing
   unsigned long long* otab;      // overflow recount table
   uint32_t ocap;
   uint32_t min_count;

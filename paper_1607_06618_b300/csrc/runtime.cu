@@ -179,7 +179,7 @@ void gerbil_opts_default(gerbil_opts* o) {
   o->canonical_minimizer = 1;
   o->supermer_cap = 256;
   o->bin_bounds = nullptr;
-  o->max_probes = 64;
+  o->max_probes = 1024;
   o->load_factor = 0.5f;
   o->distinct_ratio = 0.0f;
   o->overflow_slots = 0;
@@ -986,7 +986,7 @@ static int count_impl(gerbil_ctx* ctx, const gerbil_bins* b, const std::vector<i
   const double alpha = (opts.load_factor > 0.05f && opts.load_factor <= 0.95f) ? opts.load_factor : 0.5;
   double ratio = opts.distinct_ratio > 0.0f ? std::min(1.0, (double)opts.distinct_ratio)
                                             : std::min(1.0, ctx->ratio_known ? ctx->ratio * 1.25 : 1.0);
-  uint32_t theta = opts.max_probes ? opts.max_probes : 64;
+  uint32_t theta = opts.max_probes ? opts.max_probes : 1024;
   const uint32_t spin_limit = 1u << 20;
 
   uint64_t occ = 0;
@@ -996,6 +996,22 @@ static int count_impl(gerbil_ctx* ctx, const gerbil_bins* b, const std::vector<i
   stats.bins = (uint32_t)list.size();
   stats.occurrences = occ;
 
+  // Sec. 3.4 "Estimating table sizes": the distinct/total ratio is adjusted at runtime.  With
+  // no ratio learned yet, count about 1/16 of the bins first (tables sized for all-distinct)
+  // and size the whole batch from what they show.
+  if (opts.distinct_ratio <= 0.0f && !ctx->ratio_known && list.size() > 32) {
+    std::vector<int32_t> sample;
+    const size_t step = list.size() / 16;
+    for (size_t i = 0; i < list.size(); i += step) sample.push_back(list[i]);
+    gerbil_opts so = opts;
+    so.fused = 0;
+    gerbil_counts* tmp = nullptr;
+    const int rc = count_impl(ctx, b, sample, k, min_count, so, &tmp);
+    if (rc) return rc;
+    gerbil_counts_free(tmp);
+    if (ctx->ratio_known) ratio = std::min(1.0, ctx->ratio * 1.25);
+  }
+
   if (opts.fused == 1) {
     const int rc = count_fused(ctx, b, list, k, min_count, opts, ratio, alpha, theta, spin_limit, out);
     if (rc != FUSED_FALLBACK) return rc;
@@ -1004,7 +1020,8 @@ static int count_impl(gerbil_ctx* ctx, const gerbil_bins* b, const std::vector<i
     if (rc != WAVES_FALLBACK) return rc;
   }
 
-  for (int round = 0; round < 4; ++round) {
+  bool exact_retry = false;
+  for (int round = 0; round < 5; ++round) {
     // table sizing per bin (Sec. 3.4: expected distinct = ratio x k-mers of the file)
     std::vector<BinWork> work;
     work.reserve(list.size());
@@ -1044,20 +1061,16 @@ static int count_impl(gerbil_ctx* ctx, const gerbil_bins* b, const std::vector<i
     BinWork* dwork = (BinWork*)ctx->small;
     uint32_t* bin_ovf = (uint32_t*)((char*)ctx->small + ((work_bytes + 255) & ~size_t(255)));
 
-    // result buffer: at most one row per live slot plus the overflow-only keys
-    const uint64_t out_cap = std::max<uint64_t>(1, std::min<uint64_t>(occ, slots + ovf_cap));
-    gerbil_counts* res = new (std::nothrow) gerbil_counts;
-    if (!res) return GERBIL_E_NOMEM;
-    res->ctx = ctx;
-    res->W = W;
-    res->bytes = out_cap * (W * 8 + 4);
-    if ((rc = dev_alloc(ctx, (void**)&res->keys, out_cap * W * 8))) { delete res; return rc; }
-    if ((rc = dev_alloc(ctx, (void**)&res->counts, out_cap * 4))) {
-      dev_free(ctx, res->keys, out_cap * W * 8);
-      delete res;
-      return rc;
-    }
-    auto drop = [&]() { gerbil_counts_free(res); };
+    // result buffer (allocated after the inserts): at most one row per expected distinct key
+    // plus the overflow-only keys; if that is large, a count-only pass sizes it exactly
+    uint64_t out_cap = std::max<uint64_t>(
+        1, std::min<uint64_t>({occ, slots + ovf_cap, (uint64_t)std::ceil(ratio * (double)occ) + ovf_cap}));
+    const bool exact_out = exact_retry || out_cap * (uint64_t)(W * 8 + 4) > (2ull << 30);
+    gerbil_counts* res = nullptr;
+    auto drop = [&]() {
+      if (res) gerbil_counts_free(res);
+      res = nullptr;
+    };
 #define CKR(call)                                                                          \
   do {                                                                                     \
     cudaError_t e_ = (call);                                                               \
@@ -1110,6 +1123,37 @@ static int count_impl(gerbil_ctx* ctx, const gerbil_bins* b, const std::vector<i
     }
     ph_end(ctx, PH_INSERT);
     gerbil::CompactParams xp{};
+    if (exact_out) {  // count the rows (live slots with count >= min_count), then size exactly
+      gerbil::CompactParams cx{};
+      cx.work = dwork;
+      cx.nwork = (uint32_t)work.size();
+      cx.slot_lo = 0;
+      cx.slot_hi = slots;
+      cx.arena = (unsigned long long*)ctx->arena;
+      cx.bin_ovf = bin_ovf;
+      cx.mode = 2;
+      cx.min_count = min_count;
+      cx.ctr = ctx->ctr;
+      CKR(gerbil::launch_compact(k, cx, ctx->nsm, st));
+      ctx->times.kernel_launches++;
+      if ((rc = read_counters(ctx))) return rc;
+      const Counters hc = *ctx->hctr;
+      // deferred bins can add at most one row per overflow k-mer, the overflow table as many
+      out_cap = std::max<uint64_t>(1, hc.out_count + 2 * std::min<uint64_t>(hc.ovf_count, ovf_cap));
+      CKR(cudaMemsetAsync(&ctx->ctr->out_count, 0, 8, st));
+      CKR(cudaMemsetAsync(&ctx->ctr->distinct, 0, 8, st));
+    }
+    res = new (std::nothrow) gerbil_counts;
+    if (!res) return GERBIL_E_NOMEM;
+    res->ctx = ctx;
+    res->W = W;
+    res->bytes = out_cap * (W * 8 + 4);
+    if ((rc = dev_alloc(ctx, (void**)&res->keys, out_cap * W * 8))) { delete res; return rc; }
+    if ((rc = dev_alloc(ctx, (void**)&res->counts, out_cap * 4))) {
+      dev_free(ctx, res->keys, out_cap * W * 8);
+      delete res;
+      return rc;
+    }
     xp.work = dwork;
     xp.nwork = (uint32_t)work.size();
     xp.slot_lo = 0;
@@ -1176,6 +1220,11 @@ static int count_impl(gerbil_ctx* ctx, const gerbil_bins* b, const std::vector<i
       // (overflow emit counted the overflow-only ones)
     }
     if (h.err & gerbil::ERR_SPIN) { drop(); return fail(ctx, GERBIL_E_TIMEOUT, "bounded wait gave up"); }
+    if ((h.err & gerbil::ERR_OUT_FULL) && !exact_out) {  // estimate too low: size exactly
+      drop();
+      exact_retry = true;
+      continue;
+    }
     if (h.err & (gerbil::ERR_STATE | gerbil::ERR_OUT_FULL)) {
       drop();
       return fail(ctx, GERBIL_E_STATE, "device consistency check failed");

@@ -160,3 +160,221 @@ def workload(name: str, scale: float = 1.0):
     else:
         raise KeyError(name)
     return seq, off, p
+
+
+# --- torch generators (any device, bit-identical on CPU and GPU) ---------------------------
+# Same SplitMix64 counter as above, in int64 arithmetic: products wrap modulo 2**64 and right
+# shifts are made logical with a mask.  A uniform integer below M is (r >>> 11) % M; a
+# probability p is tested as (r >>> 32) < floor(p * 2**32).
+
+def _s64(c: int) -> int:
+    return c - (1 << 64) if c >= (1 << 63) else c
+
+
+_TG = _s64(0x9E3779B97F4A7C15)
+_TM1 = _s64(0xBF58476D1CE4E5B9)
+_TM2 = _s64(0x94D049BB133111EB)
+
+
+def _shr(z, s: int):
+    return (z >> s) & ((1 << (64 - s)) - 1)
+
+
+def _t_mix64(z):
+    z = (z ^ _shr(z, 30)) * _TM1
+    z = (z ^ _shr(z, 27)) * _TM2
+    return z ^ _shr(z, 31)
+
+
+def t_draws(seed: int, stream: int, start: int, n: int, device="cpu"):
+    """r(seed, stream, i) for i in [start, start + n) as an int64 tensor (two's complement)."""
+    import torch
+    key = _t_mix64(torch.tensor([_s64((seed * 0x9E3779B97F4A7C15 + stream) % (1 << 64))],
+                                dtype=torch.int64, device=device))
+    idx = torch.arange(start + 1, start + n + 1, dtype=torch.int64, device=device)
+    return _t_mix64(key + idx * _TG)
+
+
+def _t_below(r, m: int):
+    return _shr(r, 11) % m
+
+
+def _t_hit(r, p: float):
+    return _shr(r, 32) < int(math.floor(p * 2 ** 32))
+
+
+def t_genome(size: int, seed: int, device="cpu"):
+    import torch
+    out = torch.empty(size, dtype=torch.uint8, device=device)
+    step = 1 << 24
+    for s in range(0, size, step):
+        n = min(step, size - s)
+        out[s:s + n] = (t_draws(seed, 0, s, n, device) & 3).to(torch.uint8)
+    return out
+
+
+def t_genome_with_repeats(size: int, seed: int, repeat_frac: float = 0.2, unit_min: int = 2000,
+                          unit_max: int = 10000, copies_min: int = 5, copies_max: int = 50,
+                          device="cpu"):
+    """Uniform genome, then repeat units (a random segment of length U[unit_min, unit_max]
+    copied U{copies_min..copies_max} times to uniform positions, overwriting) until
+    repeat_frac of the genome has been written by copies.  Streams 20..23 of ``seed``."""
+    g = t_genome(size, seed, device)
+    copied, u = 0, 0
+    while copied < repeat_frac * size:
+        r = t_draws(seed, 20, 3 * u, 3, "cpu")
+        L = unit_min + int(_t_below(r[0:1], unit_max - unit_min + 1))
+        src = int(_t_below(r[1:2], size - L + 1))
+        c = copies_min + int(_t_below(r[2:3], copies_max - copies_min + 1))
+        unit = g[src:src + L].clone()
+        dst = _t_below(t_draws(seed, 23, 64 * u, c, "cpu"), size - L + 1)
+        for d in dst.tolist():
+            g[d:d + L] = unit
+        copied += c * L
+        u += 1
+    return g
+
+
+_T_ASCII = None
+
+
+def _ascii(device):
+    import torch
+    return torch.tensor(list(b"ACGT"), dtype=torch.uint8, device=device)
+
+
+def t_sampled_reads(gen, nreads: int, length: int, p_sub: float, seed: int,
+                    both_strands: bool = True, p_n: float = 0.0):
+    """Fixed-length reads at uniform starts of ``gen`` (codes, a torch tensor), reverse strand
+    with p = 1/2, substitutions with p_sub, N with p_n.  Streams 0..3 of ``seed``.  Returns
+    (seq uint8 ASCII, offsets int64) on gen's device."""
+    import torch
+    dev = gen.device
+    G = gen.numel()
+    seq = torch.empty(nreads * length, dtype=torch.uint8, device=dev)
+    per = max(1, (1 << 22) // length)
+    cols = torch.arange(length, device=dev)
+    lut = _ascii(dev)
+    for j0 in range(0, nreads, per):
+        nr = min(per, nreads - j0)
+        starts = _t_below(t_draws(seed, 0, j0, nr, dev), G - length + 1)
+        codes = gen[starts[:, None] + cols[None, :]].to(torch.int64)
+        if both_strands:
+            rev = _shr(t_draws(seed, 1, j0, nr, dev), 63).bool()
+            codes = torch.where(rev[:, None], 3 - codes.flip(1), codes)
+        base = j0 * length
+        r = t_draws(seed, 2, base, nr * length, dev).view(nr, length)
+        shift = 1 + (r & 0xFFFF) % 3
+        codes = torch.where(_t_hit(r, p_sub), (codes + shift) & 3, codes)
+        b = lut[codes]
+        if p_n > 0:
+            rn = t_draws(seed, 3, base, nr * length, dev).view(nr, length)
+            b = torch.where(_t_hit(rn, p_n), torch.full_like(b, ord("N")), b)
+        seq[base:base + nr * length] = b.reshape(-1)
+    offsets = torch.arange(nreads + 1, dtype=torch.int64, device=dev) * length
+    return seq, offsets
+
+
+def t_long_reads(gen, coverage: float, median: float, sigma: float, lmin: int, lmax: int,
+                 p_err: float, seed: int):
+    """Reads of log-normal length (median, sigma; clipped to [lmin, lmax]) at uniform starts
+    until coverage x genome bases are drawn; reverse strand with p = 1/2; per template base an
+    error with p_err: substitution 60%, insertion of a random base before it 20%, deletion 20%.
+    Streams 30..36 of ``seed``."""
+    import torch
+    dev = gen.device
+    G = gen.numel()
+    target = int(coverage * G)
+    lens, total, i = [], 0, 0
+    while total < target:
+        n = 1 << 16
+        u1 = (_shr(t_draws(seed, 30, i, n, "cpu"), 11).double() + 0.5) / float(1 << 53)
+        u2 = (_shr(t_draws(seed, 31, i, n, "cpu"), 11).double() + 0.5) / float(1 << 53)
+        z = torch.sqrt(-2.0 * torch.log(u1)) * torch.cos(2.0 * math.pi * u2)  # Box-Muller
+        L = torch.clamp(torch.round(median * torch.exp(sigma * z)), lmin, min(lmax, G)).to(torch.int64)
+        cs = torch.cumsum(L, 0)
+        need = int(torch.searchsorted(cs, torch.tensor([target - total])).item()) + 1
+        L = L[:need]
+        lens.append(L)
+        total += int(L.sum())
+        i += n
+    L = torch.cat(lens).to(dev)
+    nreads = L.numel()
+    starts = _t_below(t_draws(seed, 32, 0, nreads, dev), 1 << 62) % (G - L + 1)
+    rev = _shr(t_draws(seed, 33, 0, nreads, dev), 63).bool()
+    tpl_off = torch.zeros(nreads + 1, dtype=torch.int64, device=dev)
+    tpl_off[1:] = torch.cumsum(L, 0)
+    ntpl = int(tpl_off[-1])
+    lut = _ascii(dev)
+    pieces, out_lens = [], torch.zeros(nreads, dtype=torch.int64, device=dev)
+    step = 1 << 24
+    read_of = torch.repeat_interleave(torch.arange(nreads, device=dev), L)
+    for s in range(0, ntpl, step):
+        n = min(step, ntpl - s)
+        rid = read_of[s:s + n]
+        within = torch.arange(s, s + n, device=dev) - tpl_off[rid]
+        # template base: forward from the start, or the reverse complement of the window
+        fpos = starts[rid] + torch.where(rev[rid], L[rid] - 1 - within, within)
+        code = gen[fpos].to(torch.int64)
+        code = torch.where(rev[rid], 3 - code, code)
+        e = t_draws(seed, 34, s, n, dev)
+        hit = _t_hit(e, p_err)
+        kind = (e & 0xFF) % 10  # 0-5 substitution, 6-7 insertion, 8-9 deletion
+        sub = hit & (kind < 6)
+        ins = hit & (kind >= 6) & (kind < 8)
+        dele = hit & (kind >= 8)
+        code = torch.where(sub, (code + 1 + (_shr(e, 8) & 0xFFFF) % 3) & 3, code)
+        rb = t_draws(seed, 35, s, n, dev) & 3
+        emit = 1 + ins.to(torch.int64) - dele.to(torch.int64)  # bases written per template base
+        first = torch.where(ins, rb, code)     # an inserted base comes before the template base
+        second = code
+        both = torch.stack([first, second], 1).reshape(-1)
+        keep = torch.stack([emit >= 1, emit == 2], 1).reshape(-1)
+        pieces.append(lut[both[keep]])
+        out_lens.index_add_(0, rid, emit)
+    seq = torch.cat(pieces)
+    offsets = torch.zeros(nreads + 1, dtype=torch.int64, device=dev)
+    offsets[1:] = torch.cumsum(out_lens, 0)
+    return seq, offsets
+
+
+def lognormal_bounds(nbins: int, sigma: float, seed: int):
+    """nbins-1 ascending split points over [0, 2**32) for per-bin weights LogNormal(0, sigma)."""
+    import torch
+    u1 = (_shr(t_draws(seed, 40, 0, nbins, "cpu"), 11).double() + 0.5) / float(1 << 53)
+    u2 = (_shr(t_draws(seed, 41, 0, nbins, "cpu"), 11).double() + 0.5) / float(1 << 53)
+    z = torch.sqrt(-2.0 * torch.log(u1)) * torch.cos(2.0 * math.pi * u2)
+    w = torch.exp(sigma * z).numpy()
+    cum = np.cumsum(w) / w.sum()
+    return np.minimum(np.floor(cum[:-1] * 2 ** 32), 2 ** 32 - 1).astype(np.uint32)
+
+
+TORCH_WORKLOADS = {
+    # 100 Mbp genome, 20% repeats (2-10 kbp units copied 5-50x; seeds 3001/3002), 12e6 reads of
+    # 250 bp (30x), both strands, 0.3% substitutions (seed 3003); k=99, m=9, 1024 bins with
+    # log-normal (sigma 1) shares of the minimizer space (seed 3004), min 2
+    "genome100M-repeats-30x-k99": dict(k=99, m=9, nbins=1024, min_count=2),
+    # 50 Mbp genome (seed 4001); reads of log-normal length (median 10 kbp, sigma 0.7, clipped
+    # to [200, 100000]) to 20x, 10% errors (60/20/20 sub/ins/del), both strands (seed 4002);
+    # k=200, m=11, 512 bins, min 2
+    "genome50M-longreads-20x-k200": dict(k=200, m=11, nbins=512, min_count=2),
+}
+
+
+def torch_workload(name: str, scale: float = 1.0, device="cpu"):
+    """(seq uint8, offsets int64, params) as torch tensors on ``device``; ``scale`` shrinks the
+    genome and the read count together (same structure, smaller)."""
+    p = dict(TORCH_WORKLOADS[name])
+    if name == "genome100M-repeats-30x-k99":
+        G = max(20000, int(100_000_000 * scale))
+        gen = t_genome_with_repeats(G, 3001, device=device)
+        nreads = max(1, int(round(30 * G / 250)))
+        seq, off = t_sampled_reads(gen, nreads, 250, 0.003, 3003)
+        p["bin_bounds"] = lognormal_bounds(p["nbins"], 1.0, 3004)
+    elif name == "genome50M-longreads-20x-k200":
+        G = max(200000, int(50_000_000 * scale))
+        gen = t_genome(G, 4001, device)
+        seq, off = t_long_reads(gen, 20.0, 10000.0, 0.7, 200, 100000, 0.10, 4002)
+    else:
+        raise KeyError(name)
+    return seq, off, p

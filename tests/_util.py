@@ -6,10 +6,11 @@ import numpy as np
 
 def sort_rows(keys: np.ndarray, counts: np.ndarray):
     """Sort (keys[n, W], counts[n]) by key, word 0 most significant."""
-    keys = np.asarray(keys, dtype=np.uint64).reshape(len(counts), -1)
     counts = np.asarray(counts).astype(np.uint64)
+    keys = np.asarray(keys, dtype=np.uint64)
     if len(counts) == 0:
-        return keys, counts
+        return keys.reshape(0, keys.shape[-1] if keys.ndim == 2 else 0), counts
+    keys = keys.reshape(len(counts), -1)
     order = np.lexsort(keys.T[::-1])
     return keys[order], counts[order]
 
