@@ -90,7 +90,8 @@ typedef struct gerbil_opts {
                                   number of split points <= fmix32(minimizer); NULL: bin =
                                   fmix32(minimizer) mod nbins */
   uint32_t max_probes;         /* theta of Alg. 1: probes before a k-mer goes to overflow
-                                  (default 64) */
+                                  (default 1024: with linear probing at load <= 0.85 longer
+                                  runs are vanishingly rare, so the overflow area stays empty) */
   float load_factor;           /* target table load (default 0.5) */
   float distinct_ratio;        /* expected distinct/occurrences per bin for table sizing
                                   (Sec. 3.4 "Estimating table sizes"); 0: use the ratio the

@@ -46,7 +46,7 @@ def test_strerror_and_defaults(lib):
     assert gerbil.load().gerbil_strerror(999) == b"unknown status"
     o = gerbil.default_opts()
     assert (o.canonical, o.ordering, o.canonical_minimizer) == (1, 0, 1)
-    assert (o.supermer_cap, o.max_probes, o.persistent, o.fused) == (256, 64, 1, 0)
+    assert (o.supermer_cap, o.max_probes, o.persistent, o.fused) == (256, 1024, 1, 0)
     assert abs(o.load_factor - 0.5) < 1e-6
 
 
