@@ -64,7 +64,7 @@ struct BinWork {
 };
 
 constexpr int COUNT_THREADS = 256;
-constexpr int ITEM_KMERS = 128;  // k-mers per warp work item (4 per lane)
+constexpr int ITEM_KMERS = 256;  // k-mers per warp work item (8 consecutive ones per lane)
 
 struct CountParams {
   const unsigned long long* packed;
