@@ -15,6 +15,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import math
 import os
 import re
 import statistics
@@ -31,6 +32,7 @@ METRIC = ("canonical k-mers counted/sec on 1 B300 (bit-exact), fraction of HBM r
           "batched vs per-bin")
 UNIT = "k-mers/s"
 DEFAULT_WORKLOAD = "genome5M-30x-k65"
+SERVING_WORKLOAD = "serving-poisson20-k32-65-127"
 L2_BYTES = 126 * 2 ** 20
 
 
@@ -49,6 +51,13 @@ def _args():
     ap.add_argument("--fused", type=int, default=None,
                     help="phase-two form: 0 all tables, 1 fused queue kernel, 2 waves")
     ap.add_argument("--schedule", type=int, default=None, help="1 device queue, 0 fixed striding")
+    ap.add_argument("--serving-jobs", type=int, default=48,
+                    help="jobs of the serving stream (--workload %s)" % SERVING_WORKLOAD)
+    ap.add_argument("--serving-slots", type=int, default=4)
+    ap.add_argument("--serving-budget-gb", type=float, default=150.0)
+    ap.add_argument("--serving-scale", type=float, default=1.0,
+                    help="shrink every serving job's genome and reads by this factor")
+    ap.add_argument("--serving-rate", type=float, default=20.0, help="mean arrivals per second")
     return ap.parse_args()
 
 
@@ -405,9 +414,120 @@ def main_ours(a, world, rank, local):
     return 0
 
 
+def _pct(xs, q):
+    xs = sorted(xs)
+    if not xs:
+        return None
+    i = min(len(xs) - 1, max(0, int(math.ceil(q / 100.0 * len(xs))) - 1))
+    return xs[i]
+
+
+def main_serving(a, world, rank, local):
+    """Counting jobs arriving as a Poisson stream, served by gerbil.Server under an HBM budget:
+    aggregate k-mers/s over the whole stream (first arrival to last result) and the p50/p99
+    of the job latency (arrival to result on the device), host wall clock.  Every job's reads
+    are drawn on the device before the clock starts; results stay on the device and are freed
+    once waited for.  Each rank serves its own stream (replicas)."""
+    import threading
+    import torch
+    from paper_1607_06618_b300 import gerbil, synth
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    jobs = synth.serving_jobs(a.serving_jobs, rate=a.serving_rate)
+    reads = [synth.t_serving_reads(j, "cuda", a.serving_scale) for j in jobs]
+    torch.cuda.synchronize()
+    budget = int(a.serving_budget_gb * 1e9)
+
+    def run_stream(server, order, arrivals):
+        ids = [None] * len(order)
+        t0 = time.perf_counter()
+
+        def submitter():
+            for x, j in enumerate(order):
+                delay = t0 + arrivals[x] - time.perf_counter()
+                if delay > 0:
+                    time.sleep(delay)
+                jb = jobs[j]
+                s, o = reads[j]
+                ids[x] = server.submit(s, o, jb["k"], jb["m"], jb["nbins"], jb["min_count"])
+
+        th = threading.Thread(target=submitter)
+        th.start()
+        out = []
+        for x in range(len(order)):
+            while ids[x] is None:
+                time.sleep(0.0005)
+            res, times = server.wait(ids[x])
+            n, W, st = res.info()
+            res.free()
+            out.append(dict(times, occurrences=st["occurrences"], rows=n, groups=st["groups"]))
+        th.join()
+        return time.perf_counter() - t0, out
+
+    # warm-up: the smallest jobs, all at once
+    server = gerbil.Server(local, budget, a.serving_slots)
+    small = sorted(range(len(jobs)), key=lambda j: jobs[j]["nreads"])[:max(3, a.warmup)]
+    run_stream(server, small, [0.0] * len(small))
+    if dist:
+        dist.barrier()
+    clocks = Clocks(local)
+    wall, out = run_stream(server, list(range(len(jobs))), [j["arrival_s"] for j in jobs])
+    ck = clocks.stop()
+    st = server.stats()
+    server.close()
+    occ = sum(r["occurrences"] for r in out)
+    value = occ / wall
+    if dist:
+        t = torch.tensor([value], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        value = float(t.item())
+    lat = [r["latency_ms"] for r in out]
+    if rank == 0:
+        line = {
+            "metric": "serving: aggregate canonical k-mers counted/sec, p50/p99 job latency",
+            "value": value, "unit": UNIT, "n_gpus": world, "steps": len(jobs),
+            "warmup": len(small), "ms_per_step": 1000 * wall / len(jobs),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+            "data": "synthetic",
+            "config": {"workload": SERVING_WORKLOAD, "jobs": len(jobs),
+                       "rate_jobs_per_s": a.serving_rate, "slots": a.serving_slots,
+                       "hbm_budget_bytes": budget, "scale": a.serving_scale,
+                       "bases_total": int(sum(int(r[0].numel()) for r in reads)),
+                       "occurrences_total": occ,
+                       "k_mix": {str(k): sum(1 for j in jobs if j["k"] == k) for k, _ in synth.SERVING_K},
+                       "l2": "each job's reads are read once; inputs far larger than L2"},
+            "latency_ms": {"p50": _pct(lat, 50), "p99": _pct(lat, 99), "mean": statistics.mean(lat),
+                           "max": max(lat)},
+            "queue_ms": {"p50": _pct([r["queue_ms"] for r in out], 50),
+                         "p99": _pct([r["queue_ms"] for r in out], 99)},
+            "run_ms": {"p50": _pct([r["run_ms"] for r in out], 50),
+                       "p99": _pct([r["run_ms"] for r in out], 99)},
+            "makespan_s": wall, "last_arrival_s": jobs[-1]["arrival_s"],
+            "server": st, "jobs_grouped": sum(1 for r in out if r["groups"] > 1),
+            "clocks": ck, "gpu_launches": int(st["kernel_launches"]),
+            "cpu_baseline": None, "e2e": None,
+            "timing": "host wall clock from the first arrival to the last result; device-resident reads",
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
 def main():
     a = _args()
     world, rank, local = _dist()
+    if a.workload == SERVING_WORKLOAD:
+        if a.impl == "reference":
+            if rank == 0:
+                print(json.dumps({"impl": "reference", "unavailable":
+                                  "the oracle counts one input at a time; no serving arm"}))
+            return 0
+        return main_serving(a, world, rank, local)
     if a.impl == "reference":
         return main_reference(a, world, rank)
     return main_ours(a, world, rank, local)

@@ -111,7 +111,13 @@ typedef struct gerbil_opts {
                                   compacted in one reused region while hot in L2 */
   int32_t schedule;            /* insert work items: 1 (default) taken in bin order from a
                                   device counter; 0 fixed, each warp striding over them */
-  uint32_t reserved[3];
+  uint32_t max_table_mib;      /* device memory the hash tables of one batch may take, MiB;
+                                  a batch whose tables need more is counted in consecutive
+                                  groups of bins under this limit (each k-mer lives in one
+                                  bin, so the groups' rows are joined unchanged).  0 (default):
+                                  half of what the context's budget leaves, or half of the
+                                  device's free memory when the context has no budget */
+  uint32_t reserved[2];
 } gerbil_opts;
 
 /* Per-call statistics of a count. */
@@ -123,6 +129,9 @@ typedef struct gerbil_count_stats {
   uint64_t table_slots; /* hash-table slots allocated over all bins */
   uint32_t retries;     /* rounds repeated with larger tables because overflow was full */
   uint32_t bins;        /* bins counted */
+  uint32_t groups;      /* groups of bins counted one after another because the tables of
+                           the whole batch did not fit under the table limit (0: one batch) */
+  uint32_t reserved;
 } gerbil_count_stats;
 
 /* Device time of each step of the path, accumulated over the calls made since profiling was
@@ -156,6 +165,13 @@ int gerbil_create(gerbil_ctx** out, int device, uint64_t hbm_budget_bytes, void*
 
 /* Destroys the context and releases its scratch memory (not the caller's stream). */
 void gerbil_destroy(gerbil_ctx* ctx);
+
+/* Releases the context's cached scratch (table arena, overflow area, work lists) back to the
+ * device pool; the next count allocates it again.  Results and bins are not affected. */
+int gerbil_trim(gerbil_ctx* ctx);
+
+/* Device bytes the context currently holds (scratch, bins, results). */
+uint64_t gerbil_device_bytes(const gerbil_ctx* ctx);
 
 /* Enables (1) or disables (0) per-step event timing and resets the accumulated times and
  * launch counters.  Timing adds two event records per step; results are unchanged. */
@@ -225,6 +241,60 @@ int gerbil_counts_to_host(const gerbil_counts* counts, uint64_t* keys, uint32_t*
                           uint64_t cap);
 
 void gerbil_counts_free(gerbil_counts* counts);
+
+/* ---- serving: counting jobs admitted continuously under an HBM budget ----------------------
+ * The paper has no counterpart (it counts one input at a time).  A server keeps `slots` worker
+ * contexts, each with its own CUDA stream and host thread.  A submitted job waits, in arrival
+ * order, until a worker is free and its estimated peak device memory fits under
+ * hbm_budget_bytes (0: no limit) next to the running jobs and the finished results not yet
+ * handed over.  The estimate covers reads copied from the host, the phase-one buffers, hash
+ * tables at the largest distinct ratio seen so far for the job's k (every k-mer distinct
+ * before the first such job, unless opts->distinct_ratio is given), the overflow area and
+ * the result rows.  The first waiting job that fits is admitted, so a large job does not hold
+ * up smaller ones; a job passed over 4 x slots times stops later jobs from starting until it
+ * fits; a job larger than the whole budget runs when nothing else does.  One job's tables
+ * take at most hbm_budget_bytes / (2 x slots) (its opts->max_table_mib, when 0): larger
+ * batches are counted in groups of bins.  Each job learns its own distinct ratio (Sec. 3.4)
+ * on a sample of its bins.  Admitted jobs run phase one and phase two (gerbil_partition +
+ * gerbil_count_batch over all bins) concurrently on their streams, so their kernels overlap on
+ * the GPU.  Each job's result stays on the device (a gerbil_counts of the worker's context)
+ * and counts against the budget until gerbil_server_wait hands it over; free every result
+ * before destroying the server. */
+typedef struct gerbil_server gerbil_server;
+
+typedef struct gerbil_server_stats {
+  uint64_t submitted, completed, failed;
+  uint64_t kmers;          /* k-mer occurrences counted by completed jobs */
+  uint32_t max_concurrent; /* most jobs running at once */
+  uint32_t reserved;
+  uint64_t kernel_launches; /* kernels of this library launched by the workers */
+} gerbil_server_stats;
+
+typedef struct gerbil_job_times {
+  double queue_ms;   /* arrival (submit) -> admission */
+  double run_ms;     /* admission -> result on the device */
+  double latency_ms; /* arrival -> result on the device */
+  int32_t worker;
+  int32_t reserved;
+} gerbil_job_times;
+
+/* Errors: E_INVAL (slots outside 1..64), E_CUDA, E_NOMEM. */
+int gerbil_server_create(gerbil_server** out, int device, uint64_t hbm_budget_bytes, int slots);
+
+/* Queues one job.  Host reads are copied at submit; device reads must stay valid until the
+ * job's result has been waited for.  opts->bin_bounds is copied.  *job_id receives the id. */
+int gerbil_server_submit(gerbil_server* s, const gerbil_reads* reads, int k, int m, int nbins,
+                         uint32_t min_count, const gerbil_opts* opts, uint64_t* job_id);
+
+/* Waits for a job (timeout_ms < 0: no limit) and hands over its result (*out, NULL if the job
+ * failed) and times; returns the job's status, or E_TIMEOUT (the job stays queued/running). */
+int gerbil_server_wait(gerbil_server* s, uint64_t job_id, int64_t timeout_ms, gerbil_counts** out,
+                       gerbil_job_times* times);
+
+int gerbil_server_get_stats(gerbil_server* s, gerbil_server_stats* out);
+
+/* Stops the workers after their current jobs and frees every result not yet handed over. */
+void gerbil_server_destroy(gerbil_server* s);
 
 /* Memory-throughput probe (the paper has no counterpart; a measurement helper for the
  * roofline of the insert kernel).  Runs one kernel in which every thread performs per_thread

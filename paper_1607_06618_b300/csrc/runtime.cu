@@ -2,6 +2,7 @@
 // HBM budget, phase-one orchestration, table sizing (Sec. 3.4 "Estimating table sizes"),
 // phase-two launches and the overflow recount (Sec. 3.4 "Probing Strategy").
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -22,7 +23,7 @@ struct gerbil_ctx {
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   uint64_t budget = 0;  // 0 = unbounded
-  uint64_t used = 0;
+  std::atomic<uint64_t> used{0};  // results may be freed from another thread
   int nsm = 148;
   int insert_ctas_per_sm = 8;
   int l2_bytes = 126 << 20;
@@ -68,6 +69,9 @@ struct gerbil_counts {
   uint32_t* counts = nullptr;
   size_t bytes = 0;
   gerbil_count_stats stats{};
+  // a batch counted in groups of bins: the groups' results in bin order (keys/counts above
+  // stay empty until a device view joins them into one buffer)
+  std::vector<gerbil_counts*> parts;
 };
 
 namespace {
@@ -104,7 +108,7 @@ void dev_free(gerbil_ctx* ctx, void* p, size_t bytes) {
   if (!p) return;
   bytes = (bytes + 255) & ~size_t(255);
   cudaFreeAsync(p, ctx->stream);
-  ctx->used -= std::min(ctx->used, (uint64_t)bytes);
+  ctx->used.fetch_sub(std::min(ctx->used.load(), (uint64_t)bytes));
 }
 
 // Grow-only scratch buffer cached in the context (*grown set when it was reallocated).
@@ -243,11 +247,7 @@ int gerbil_create(gerbil_ctx** out, int device, uint64_t budget, void* stream) {
     for (cudaEvent_t& e : ctx->ev)
       if (cudaEventCreate(&e) != cudaSuccess) { rc = GERBIL_E_CUDA; break; }
     if (rc) break;
-    int occ = 0;
-    // resident CTAs of the insert kernel decide the persistent grid; 8 x 256 threads is the
-    // SM's thread limit, refined by the occupancy query of the kernel in use at launch.
-    ctx->insert_ctas_per_sm = 8;
-    (void)occ;
+    ctx->insert_ctas_per_sm = 8;  // refined by an occupancy query of the kernel at launch
   } while (0);
   if (rc) {
     cudaGetLastError();
@@ -285,6 +285,25 @@ int gerbil_internal_alloc(gerbil_ctx* ctx, void** p, size_t bytes, void** stream
 }
 
 void gerbil_internal_free(gerbil_ctx* ctx, void* p, size_t bytes) { dev_free(ctx, p, bytes); }
+
+void gerbil_internal_forget_ratio(gerbil_ctx* ctx) {
+  if (ctx) ctx->ratio_known = false;
+}
+
+int gerbil_trim(gerbil_ctx* ctx) {
+  if (!ctx) return GERBIL_E_INVAL;
+  CK(cudaSetDevice(ctx->device));
+  dev_free(ctx, ctx->arena, ctx->arena_bytes);
+  dev_free(ctx, ctx->ovf, ctx->ovf_bytes);
+  dev_free(ctx, ctx->small, ctx->small_bytes);
+  ctx->arena = ctx->ovf = ctx->small = nullptr;
+  ctx->arena_bytes = ctx->ovf_bytes = ctx->small_bytes = 0;
+  ctx->arena_dirty = 0;
+  CK(cudaStreamSynchronize(ctx->stream));
+  return GERBIL_OK;
+}
+
+uint64_t gerbil_device_bytes(const gerbil_ctx* ctx) { return ctx ? ctx->used.load() : 0; }
 
 int gerbil_profile(gerbil_ctx* ctx, int enable) {
   if (!ctx) return GERBIL_E_INVAL;
@@ -979,6 +998,37 @@ static int count_waves(gerbil_ctx* ctx, const gerbil_bins* b, const std::vector<
 #undef CKW
 }
 
+// Bytes the hash tables of one batch may take (gerbil_opts.max_table_mib).
+static uint64_t table_limit(gerbil_ctx* ctx, const gerbil_opts& opts) {
+  if (opts.max_table_mib) return (uint64_t)opts.max_table_mib << 20;
+  if (ctx->budget) return (ctx->budget - std::min<uint64_t>(ctx->budget, ctx->used.load())) / 2;
+  size_t free_b = 0, total_b = 0;
+  if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) return ~0ull;
+  // the context's own cached arena is reused by the tables, so it counts as free
+  return ((uint64_t)free_b + ctx->arena_bytes) / 2;
+}
+
+// Append a group's result to a joined result (flattening a joined part).
+static void join_part(gerbil_counts* joined, gerbil_counts* part) {
+  gerbil_count_stats& a = joined->stats;
+  const gerbil_count_stats& p = part->stats;
+  a.occurrences += p.occurrences;
+  a.distinct += p.distinct;
+  a.emitted += p.emitted;
+  a.overflowed += p.overflowed;
+  a.table_slots += p.table_slots;
+  a.retries += p.retries;
+  a.bins += p.bins;
+  joined->n += part->n;
+  if (!part->parts.empty()) {
+    for (gerbil_counts* q : part->parts) joined->parts.push_back(q);
+    part->parts.clear();
+    delete part;
+  } else {
+    joined->parts.push_back(part);
+  }
+}
+
 static int count_impl(gerbil_ctx* ctx, const gerbil_bins* b, const std::vector<int32_t>& list,
                       int k, uint32_t min_count, const gerbil_opts& opts, gerbil_counts** out) {
   const int W = words_for(k);
@@ -1010,6 +1060,47 @@ static int count_impl(gerbil_ctx* ctx, const gerbil_bins* b, const std::vector<i
     if (rc) return rc;
     gerbil_counts_free(tmp);
     if (ctx->ratio_known) ratio = std::min(1.0, ctx->ratio * 1.25);
+  }
+
+  // The tables of all bins of a call are held at once.  Where they would take more than the
+  // table limit, the bins are counted in consecutive groups under it, one after another in
+  // the same arena (each k-mer lives in exactly one bin, Sec. 3.2, so the rows of the groups
+  // are joined unchanged).
+  if (list.size() > 1) {
+    const uint64_t limit = table_limit(ctx, opts);
+    const uint64_t slot_bytes = 8ull * gerbil::slot_words_for_k(k);
+    auto bin_bytes = [&](int32_t bi) -> uint64_t {
+      if (b->nkmers[bi] == 0) return 0;
+      const double est = std::max(1.0, std::ceil(ratio * (double)b->nkmers[bi]));
+      return ((uint64_t)std::ceil(est / alpha) + 16) * slot_bytes;
+    };
+    uint64_t need = 0;
+    for (int32_t bi : list) need += bin_bytes(bi);
+    if (need > limit) {
+      gerbil_counts* joined = new (std::nothrow) gerbil_counts;
+      if (!joined) return fail(ctx, GERBIL_E_NOMEM, "host allocation");
+      joined->ctx = ctx;
+      joined->W = W;
+      size_t i = 0;
+      while (i < list.size()) {
+        std::vector<int32_t> group;
+        uint64_t g = 0;
+        while (i < list.size() && (group.empty() || g + bin_bytes(list[i]) <= limit)) {
+          g += bin_bytes(list[i]);
+          group.push_back(list[i++]);
+        }
+        gerbil_counts* part = nullptr;
+        const int rc = count_impl(ctx, b, group, k, min_count, opts, &part);
+        if (rc) {
+          gerbil_counts_free(joined);
+          return rc;
+        }
+        join_part(joined, part);
+      }
+      joined->stats.groups = (uint32_t)joined->parts.size();
+      *out = joined;
+      return GERBIL_OK;
+    }
   }
 
   if (opts.fused == 1) {
@@ -1303,8 +1394,39 @@ int gerbil_counts_info(const gerbil_counts* c, uint64_t* n, int* words, gerbil_c
   return GERBIL_OK;
 }
 
-int gerbil_counts_view(const gerbil_counts* c, const uint64_t** keys, const uint32_t** counts) {
-  if (!c) return GERBIL_E_INVAL;
+int gerbil_counts_view(const gerbil_counts* cc, const uint64_t** keys, const uint32_t** counts) {
+  if (!cc) return GERBIL_E_INVAL;
+  gerbil_counts* c = const_cast<gerbil_counts*>(cc);
+  if (!c->parts.empty()) {
+    // join the groups' rows into one buffer on first view
+    gerbil_ctx* ctx = c->ctx;
+    CK(cudaSetDevice(ctx->device));
+    const int W = c->W;
+    unsigned long long* k2 = nullptr;
+    uint32_t* c2 = nullptr;
+    if (c->n) {
+      int rc;
+      if ((rc = dev_alloc(ctx, (void**)&k2, c->n * W * 8))) return rc;
+      if ((rc = dev_alloc(ctx, (void**)&c2, c->n * 4))) {
+        dev_free(ctx, k2, c->n * W * 8);
+        return rc;
+      }
+      uint64_t at = 0;
+      for (gerbil_counts* p : c->parts) {
+        if (p->n) {
+          CK(cudaMemcpyAsync(k2 + at * W, p->keys, p->n * W * 8, cudaMemcpyDeviceToDevice, ctx->stream));
+          CK(cudaMemcpyAsync(c2 + at, p->counts, p->n * 4, cudaMemcpyDeviceToDevice, ctx->stream));
+        }
+        at += p->n;
+      }
+      CK(cudaStreamSynchronize(ctx->stream));
+    }
+    for (gerbil_counts* p : c->parts) gerbil_counts_free(p);
+    c->parts.clear();
+    c->keys = k2;
+    c->counts = c2;
+    c->bytes = c->n * (W * 8 + 4);
+  }
   if (keys) *keys = (const uint64_t*)c->keys;
   if (counts) *counts = c->counts;
   return GERBIL_OK;
@@ -1316,8 +1438,19 @@ int gerbil_counts_to_host(const gerbil_counts* c, uint64_t* keys, uint32_t* coun
   if (cap < c->n || (c->n && (!keys || !counts))) return fail(ctx, GERBIL_E_INVAL, "cap < n");
   if (c->n == 0) return GERBIL_OK;
   CK(cudaSetDevice(ctx->device));
-  CK(cudaMemcpyAsync(keys, c->keys, c->n * c->W * 8, cudaMemcpyDeviceToHost, ctx->stream));
-  CK(cudaMemcpyAsync(counts, c->counts, c->n * 4, cudaMemcpyDeviceToHost, ctx->stream));
+  if (!c->parts.empty()) {
+    uint64_t at = 0;
+    for (const gerbil_counts* p : c->parts) {
+      if (p->n) {
+        CK(cudaMemcpyAsync(keys + at * c->W, p->keys, p->n * c->W * 8, cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaMemcpyAsync(counts + at, p->counts, p->n * 4, cudaMemcpyDeviceToHost, ctx->stream));
+      }
+      at += p->n;
+    }
+  } else {
+    CK(cudaMemcpyAsync(keys, c->keys, c->n * c->W * 8, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(counts, c->counts, c->n * 4, cudaMemcpyDeviceToHost, ctx->stream));
+  }
   CK(cudaStreamSynchronize(ctx->stream));
   return GERBIL_OK;
 }
@@ -1325,6 +1458,7 @@ int gerbil_counts_to_host(const gerbil_counts* c, uint64_t* keys, uint32_t* coun
 void gerbil_counts_free(gerbil_counts* c) {
   if (!c) return;
   gerbil_ctx* ctx = c->ctx;
+  for (gerbil_counts* p : c->parts) gerbil_counts_free(p);
   cudaSetDevice(ctx->device);
   const uint64_t cap = c->bytes / (c->W * 8 + 4);
   dev_free(ctx, c->keys, cap * c->W * 8);

@@ -37,6 +37,8 @@ ABI_SYMBOLS = (
     "gerbil_bins_export", "gerbil_bins_free", "gerbil_count", "gerbil_count_batch",
     "gerbil_counts_info", "gerbil_counts_view", "gerbil_counts_to_host", "gerbil_counts_free",
     "gerbil_profile", "gerbil_get_phase_times", "gerbil_count_small_noalloc", "gerbil_membench",
+    "gerbil_trim", "gerbil_device_bytes", "gerbil_server_create", "gerbil_server_submit",
+    "gerbil_server_wait", "gerbil_server_get_stats", "gerbil_server_destroy",
 )
 
 
@@ -59,17 +61,18 @@ class gerbil_opts(ctypes.Structure):
                 ("load_factor", ctypes.c_float), ("distinct_ratio", ctypes.c_float),
                 ("overflow_slots", ctypes.c_uint32), ("persistent", ctypes.c_int32),
                 ("ring_slots", ctypes.c_uint32), ("fused", ctypes.c_int32),
-                ("schedule", ctypes.c_int32), ("reserved", ctypes.c_uint32 * 3)]
+                ("schedule", ctypes.c_int32), ("max_table_mib", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32 * 2)]
 
 
 class gerbil_count_stats(ctypes.Structure):
     _fields_ = [("occurrences", ctypes.c_uint64), ("distinct", ctypes.c_uint64),
                 ("emitted", ctypes.c_uint64), ("overflowed", ctypes.c_uint64),
                 ("table_slots", ctypes.c_uint64), ("retries", ctypes.c_uint32),
-                ("bins", ctypes.c_uint32)]
+                ("bins", ctypes.c_uint32), ("groups", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
 
     def as_dict(self):
-        return {name: int(getattr(self, name)) for name, _ in self._fields_}
+        return {name: int(getattr(self, name)) for name, _ in self._fields_ if name != "reserved"}
 
 
 class gerbil_phase_times(ctypes.Structure):
@@ -82,6 +85,26 @@ class gerbil_phase_times(ctypes.Structure):
     def as_dict(self):
         return {name: (float if t is ctypes.c_double else int)(getattr(self, name))
                 for name, t in self._fields_}
+
+
+class gerbil_server_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64),
+                ("failed", ctypes.c_uint64), ("kmers", ctypes.c_uint64),
+                ("max_concurrent", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+                ("kernel_launches", ctypes.c_uint64)]
+
+    def as_dict(self):
+        return {name: int(getattr(self, name)) for name, _ in self._fields_ if name != "reserved"}
+
+
+class gerbil_job_times(ctypes.Structure):
+    _fields_ = [("queue_ms", ctypes.c_double), ("run_ms", ctypes.c_double),
+                ("latency_ms", ctypes.c_double), ("worker", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {"queue_ms": self.queue_ms, "run_ms": self.run_ms, "latency_ms": self.latency_ms,
+                "worker": int(self.worker)}
 
 
 _lib = None
@@ -119,6 +142,14 @@ def load() -> ctypes.CDLL:
         "gerbil_counts_to_host": (I32, [P, P, P, U64]),
         "gerbil_counts_free": (None, [P]),
         "gerbil_profile": (I32, [P, I32]),
+        "gerbil_trim": (I32, [P]),
+        "gerbil_device_bytes": (U64, [P]),
+        "gerbil_server_create": (I32, [PP, I32, U64, I32]),
+        "gerbil_server_submit": (I32, [P, ctypes.POINTER(gerbil_reads), I32, I32, I32, U32,
+                                       ctypes.POINTER(gerbil_opts), ctypes.POINTER(U64)]),
+        "gerbil_server_wait": (I32, [P, U64, ctypes.c_int64, PP, ctypes.POINTER(gerbil_job_times)]),
+        "gerbil_server_get_stats": (I32, [P, ctypes.POINTER(gerbil_server_stats)]),
+        "gerbil_server_destroy": (None, [P]),
         "gerbil_membench": (I32, [P, U64, I32, U64, ctypes.POINTER(ctypes.c_double)]),
         "gerbil_count_small_noalloc": (I32, [P, P, U64, U64, I32, U32, I32, P, P, U64,
                                              ctypes.POINTER(U64), P]),
@@ -304,6 +335,53 @@ def gerbil_count_small_noalloc(seq, offsets, k: int, min_count: int, canonical: 
     return n.value
 
 
+def gerbil_trim(ctx):
+    _check(load().gerbil_trim(ctx), ctx)
+
+
+def gerbil_device_bytes(ctx) -> int:
+    return int(load().gerbil_device_bytes(ctx))
+
+
+def gerbil_server_create(device: int, hbm_budget_bytes: int, slots: int):
+    h = ctypes.c_void_p()
+    _check(load().gerbil_server_create(ctypes.byref(h), device, hbm_budget_bytes, slots))
+    return h
+
+
+def gerbil_server_submit(server, seq, offsets, k, m, nbins, min_count, opts=None, bin_bounds=None):
+    r, keep = _reads_struct(seq, offsets)
+    o = opts if opts is not None else default_opts()
+    bb = None
+    if bin_bounds is not None:
+        bb = np.ascontiguousarray(bin_bounds, dtype=np.uint32)
+        o.bin_bounds = bb.ctypes.data
+    jid = ctypes.c_uint64()
+    st = load().gerbil_server_submit(server, ctypes.byref(r), k, m, nbins, min_count,
+                                     ctypes.byref(o), ctypes.byref(jid))
+    o.bin_bounds = None
+    _check(st)
+    return jid.value
+
+
+def gerbil_server_wait(server, job_id: int, timeout_ms: int = -1):
+    h = ctypes.c_void_p()
+    t = gerbil_job_times()
+    st = load().gerbil_server_wait(server, job_id, timeout_ms, ctypes.byref(h), ctypes.byref(t))
+    _check(st)
+    return h, t.as_dict()
+
+
+def gerbil_server_get_stats(server):
+    s = gerbil_server_stats()
+    _check(load().gerbil_server_get_stats(server, ctypes.byref(s)))
+    return s.as_dict()
+
+
+def gerbil_server_destroy(server):
+    load().gerbil_server_destroy(server)
+
+
 # ---- handle wrappers ----------------------------------------------------------------------
 class _DeviceArray:
     """Exposes a device pointer to torch through __cuda_array_interface__ (no copy)."""
@@ -350,6 +428,60 @@ class Counts:
     def __del__(self):
         try:
             self.free()
+        except Exception:
+            pass
+
+
+class _ServerOwner:
+    """Stands in for a Context as the owner of results handed over by a Server."""
+
+    def __init__(self, server):
+        self._server = server
+        self._children = weakref.WeakSet()
+
+    @property
+    def handle(self):
+        return self._server.handle
+
+    @property
+    def device(self):
+        return self._server.device
+
+
+class Server:
+    """Counting jobs served continuously under an HBM budget (see gerbil_server_create)."""
+
+    def __init__(self, device: int = 0, hbm_budget_bytes: int = 0, slots: int = 4):
+        self.device = device
+        self.handle = gerbil_server_create(device, hbm_budget_bytes, slots)
+        self._owner = _ServerOwner(self)
+        self._keep = {}
+
+    def submit(self, seq, offsets, k, m, nbins, min_count, opts=None, bin_bounds=None) -> int:
+        jid = gerbil_server_submit(self.handle, seq, offsets, k, m, nbins, min_count, opts, bin_bounds)
+        if hasattr(seq, "data_ptr") and seq.is_cuda:
+            self._keep[jid] = (seq, offsets)  # device reads stay alive until the job is waited for
+        return jid
+
+    def wait(self, job_id: int, timeout_ms: int = -1):
+        h, times = gerbil_server_wait(self.handle, job_id, timeout_ms)
+        self._keep.pop(job_id, None)
+        return Counts(h, self._owner), times
+
+    def stats(self):
+        return gerbil_server_get_stats(self.handle)
+
+    def close(self):
+        if self.handle:
+            for child in list(self._owner._children):
+                child.free()
+            gerbil_server_destroy(self.handle)
+            self.handle = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
         except Exception:
             pass
 

@@ -378,3 +378,47 @@ def torch_workload(name: str, scale: float = 1.0, device="cpu"):
     else:
         raise KeyError(name)
     return seq, off, p
+
+
+# Serving stream: Poisson arrivals (mean `rate` jobs/s); each job a 150 bp read set drawn from
+# a random genome of log-uniform size in [1, 200] Mbp at a coverage uniform in [10, 40], both
+# strands, 0.5% substitutions and 0.5% N; k uniform over {32, 65, 127} with m = 7, 9, 11;
+# bins = the power of two nearest to windows / 1e6, clamped to [64, 1024]; min_count 1.
+# Job parameters use streams 50..54 of ``seed``; job j's genome and reads use seeds
+# 100000 + 2j and 100001 + 2j.
+SERVING_K = ((32, 7), (65, 9), (127, 11))
+
+
+def _unit(seed: int, stream: int, n: int):
+    return (draws(seed, stream, 0, n) >> np.uint64(11)).astype(np.float64) * 2.0 ** -53
+
+
+def serving_jobs(n_jobs: int, rate: float = 20.0, seed: int = 5, g_min: float = 1e6,
+                 g_max: float = 200e6, read_len: int = 150):
+    """Parameters of ``n_jobs`` jobs: dicts with arrival_s, genome, coverage, nreads, k, m,
+    nbins, min_count, seeds."""
+    u_gap, u_g, u_cov, u_k = (_unit(seed, 50 + i, n_jobs) for i in range(4))
+    t, jobs = 0.0, []
+    for j in range(n_jobs):
+        t += -math.log(1.0 - u_gap[j]) / rate
+        G = int(round(math.exp(math.log(g_min) + u_g[j] * (math.log(g_max) - math.log(g_min)))))
+        cov = 10.0 + 30.0 * u_cov[j]
+        k, m = SERVING_K[min(2, int(u_k[j] * 3))]
+        nreads = max(1, int(round(cov * G / read_len)))
+        nwin = nreads * (read_len - k + 1)
+        nbins = 1 << max(0, int(round(math.log2(max(1.0, nwin / 1e6)))))
+        nbins = min(1024, max(64, nbins))
+        jobs.append(dict(arrival_s=t, genome=G, coverage=cov, nreads=nreads, read_len=read_len,
+                         k=k, m=m, nbins=nbins, min_count=1,
+                         genome_seed=100000 + 2 * j, read_seed=100001 + 2 * j))
+    return jobs
+
+
+def t_serving_reads(job: dict, device="cuda", scale: float = 1.0):
+    """(seq, offsets) of one serving job on ``device`` (``scale`` shrinks genome and reads)."""
+    G = max(4 * job["read_len"], int(job["genome"] * scale))
+    nreads = max(1, int(round(job["nreads"] * scale)))
+    gen = t_genome(G, job["genome_seed"], device)
+    seq, off = t_sampled_reads(gen, nreads, job["read_len"], 0.005, job["read_seed"], p_n=0.005)
+    del gen
+    return seq, off
