@@ -159,7 +159,9 @@ const char* gerbil_last_error(const gerbil_ctx* ctx);
 
 /* Creates a context on CUDA device `device`.  hbm_budget_bytes bounds the device memory the
  * context may hold at once (0 = no bound).  cuda_stream is a cudaStream_t on that device that
- * every call is ordered on (NULL = the context creates its own non-blocking stream).
+ * every call is ordered on: cudaStreamLegacy ((void*)1) for the legacy default stream,
+ * cudaStreamPerThread ((void*)2) for the per-thread one; NULL makes the context create a
+ * non-blocking stream of its own, which does not wait for work on any other stream.
  * Errors: E_INVAL (bad device), E_CUDA. */
 int gerbil_create(gerbil_ctx** out, int device, uint64_t hbm_budget_bytes, void* cuda_stream);
 
@@ -281,8 +283,9 @@ typedef struct gerbil_job_times {
 /* Errors: E_INVAL (slots outside 1..64), E_CUDA, E_NOMEM. */
 int gerbil_server_create(gerbil_server** out, int device, uint64_t hbm_budget_bytes, int slots);
 
-/* Queues one job.  Host reads are copied at submit; device reads must stay valid until the
- * job's result has been waited for.  opts->bin_bounds is copied.  *job_id receives the id. */
+/* Queues one job.  Host reads are copied at submit; device reads must be complete when this is
+ * called (the workers' streams wait for no other stream) and stay valid until the job's
+ * result has been waited for.  opts->bin_bounds is copied.  *job_id receives the id. */
 int gerbil_server_submit(gerbil_server* s, const gerbil_reads* reads, int k, int m, int nbins,
                          uint32_t min_count, const gerbil_opts* opts, uint64_t* job_id);
 

@@ -6,6 +6,10 @@
 #include "common.cuh"
 #include "kernels.h"
 
+#ifndef GERBIL_LANE_QUEUE
+#define GERBIL_LANE_QUEUE 1
+#endif
+
 namespace gerbil {
 
 // ---- table insert (Alg. 1) -------------------------------------------------------------------
@@ -195,6 +199,107 @@ __device__ __forceinline__ void insert_item(const CountParams& P, uint32_t wi, c
   const uint32_t jb = min(ja + (uint32_t)KPL, j1);
   unsigned long long fwd[W], rc[W], pos = 0;
   uint32_t sidx = 0, send = 0;  // current super-mer and its first k-mer past the end
+#if GERBIL_LANE_QUEUE
+  // Each lane keeps one k-mer in flight and does one probe of it per step; a lane whose k-mer
+  // is placed takes its next one at the start of the following step, while the other lanes go
+  // on probing theirs.  A warp thus waits for the longest sum of probe chains over a lane's
+  // k-mers, not for the longest chain of every k-mer in turn.
+  unsigned long long st[WS];
+  uint32_t tagw = 0, s = 0, t = 0, spins = 0;
+  uint32_t j = ja;
+  bool busy = false;
+#pragma unroll 1
+  for (;;) {
+    if (!busy) {
+      if (j >= jb) break;
+      if (j == ja || j >= send) {  // cut the k-mer in full
+        if (j == ja) {
+          uint32_t lo = 0, hi = ns;
+          while (hi - lo > 1) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (S.koff[mid] <= j) lo = mid; else hi = mid;
+          }
+          sidx = lo;
+        } else {
+          ++sidx;
+        }
+        send = (sidx + 1 < ns) ? S.koff[sidx + 1] : 0xFFFFFFFFu;
+        pos = S.pos[sidx] + (j - S.koff[sidx]);
+        load_kmer<W>(P.packed, pos, k, fwd);
+        revcomp<W>(fwd, k, rc);
+      } else {  // roll by one base
+        const unsigned long long q = pos + (unsigned long long)k;  // the new last base
+        const unsigned long long b = (__ldg(P.packed + (q >> 5)) >> (62 - 2 * (int)(q & 31))) & 3ull;
+#pragma unroll
+        for (int u = 0; u < W - 1; ++u) fwd[u] = (fwd[u] << 2) | (fwd[u + 1] >> 62);
+        fwd[W - 1] = (fwd[W - 1] << 2) | b;
+        fwd[0] &= mask0;
+#pragma unroll
+        for (int u = W - 1; u >= 1; --u) rc[u] = (rc[u] >> 2) | (rc[u - 1] << 62);
+        rc[0] = (rc[0] >> 2) | ((3ull - b) << (2 * nb0 - 2));
+        ++pos;
+      }
+      unsigned long long key[W];
+      const bool use_rc = P.canonical && key_less<W>(rc, fwd);
+#pragma unroll
+      for (int u = 0; u < W; ++u) key[u] = use_rc ? rc[u] : fwd[u];
+      const unsigned long long h = key_hash<W>(key);
+      to_stored<W, WS>(key, st);
+      tagw = META_CLAIMED | (uint32_t)((h >> 34) & META_TAG_MASK);
+      s = slot_of(h, wk.cap);
+      t = 0;
+      spins = 0;
+      busy = true;
+      ++j;
+    }
+    // one probe of slot s (Alg. 1)
+    unsigned long long* slot = tab + (unsigned long long)s * SW;
+    unsigned long long v[SW];
+    load_slot<SW>(slot, v);
+    int why = 0;
+    if (v[0] == 0ull) {
+      if (cas_relaxed(slot, 0ull, ((unsigned long long)tagw << 32) | 1ull) == 0ull) {
+        st_relaxed(slot + 1, st[0]);  // word 1 alone, then 16-byte aligned pairs
+#pragma unroll
+        for (int u = 1; u < WS; u += 2) {
+          if (u + 1 < WS) st_relaxed_v2(slot + 1 + u, st[u], st[u + 1]);
+          else st_relaxed(slot + 1 + u, st[u]);
+        }
+        busy = false;
+      }
+      continue;  // claimed by another lane meanwhile: look at the same slot again
+    }
+    if (((uint32_t)(v[0] >> 32) & ~META_MERGED) == tagw) {
+      bool all = true, eq = true;
+#pragma unroll
+      for (int u = 0; u < WS; ++u) {
+        all &= (v[1 + u] & MARK) != 0ull;
+        eq &= v[1 + u] == st[u];
+      }
+      if (!all) {  // the claimer has not written every key word yet: read the slot again
+        if (++spins > P.spin_limit) {
+          why = 2;
+        } else {
+          if (spins > 8) __nanosleep(32);
+          continue;
+        }
+      } else if (eq) {
+        red_add(slot, 1ull);
+        busy = false;
+        continue;
+      }
+    }
+    if (!why) {
+      s = (s + 1 == wk.cap) ? 0u : s + 1;
+      if (++t < P.theta) continue;
+      why = 1;
+    }
+    unsigned long long key[W];
+    from_stored<W, WS>(st, key);
+    to_overflow<W>(P, wi, key, why);
+    busy = false;
+  }
+#else
 #pragma unroll 1
   for (uint32_t j = ja; j < jb; ++j) {
     if (j == ja || j >= send) {  // cut the k-mer in full
@@ -237,6 +342,7 @@ __device__ __forceinline__ void insert_item(const CountParams& P, uint32_t wi, c
     const int res = table_insert_from<WS>(tab, wk.cap, st, h, P.theta, P.spin_limit, s0, v);
     if (res) to_overflow<W>(P, wi, key, res);
   }
+#endif
   __syncwarp();  // S is reused by the next item
 }
 
@@ -252,8 +358,23 @@ __device__ __forceinline__ void count_item(const CountParams& P, unsigned long l
 // current one runs), so the bins in flight at any moment are few and their tables stay hot in
 // L2; or (schedule 0) each warp strides over the items.  Launched with as many CTAs as fit on
 // the GPU (persistent) or one warp per item.
+#ifndef GERBIL_MINB_SMALL
+#define GERBIL_MINB_SMALL 5
+#endif
+#ifndef GERBIL_MINB_MID
+#define GERBIL_MINB_MID 4
+#endif
+#ifndef GERBIL_MINB_LARGE
+#define GERBIL_MINB_LARGE 1
+#endif
+// Resident CTAs per SM that the register allocation is held to (measured: 5 for keys of up to
+// three words, 4 for four or five).
+constexpr int insert_min_blocks(int W) {
+  return W <= 3 ? GERBIL_MINB_SMALL : (W <= 5 ? GERBIL_MINB_MID : GERBIL_MINB_LARGE);
+}
+
 template <int W, int WS>
-__global__ void __launch_bounds__(256) insert_kernel(CountParams P) {
+__global__ void __launch_bounds__(256, insert_min_blocks(W)) insert_kernel(CountParams P) {
   __shared__ WarpSmem S[8];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (!P.schedule) {  // fixed: warp w takes items base + w, base + w + nw, ...

@@ -1294,14 +1294,39 @@ static int count_impl(gerbil_ctx* ctx, const gerbil_bins* b, const std::vector<i
       op.out_counts = res->counts;
       op.out_cap = out_cap;
       op.ctr = ctx->ctr;
+      // the bins that spilled: only their tables are scanned again (merged with the recount)
+      std::vector<uint32_t> hovf(work.size());
+      CKR(cudaMemcpyAsync(hovf.data(), bin_ovf, work.size() * 4, cudaMemcpyDeviceToHost, st));
+      CKR(cudaStreamSynchronize(st));
+      std::vector<std::pair<size_t, size_t>> spans;  // [first, last] work indices
+      for (size_t i = 0; i < work.size(); ++i) {
+        if (!hovf[i]) continue;
+        if (!spans.empty() && spans.back().second + 1 == i) spans.back().second = i;
+        else spans.push_back({i, i});
+      }
+      while (spans.size() > 32) {  // join the two spans with the fewest slots between them
+        size_t best = 0;
+        uint64_t gap = ~0ull;
+        for (size_t i = 0; i + 1 < spans.size(); ++i) {
+          const uint64_t g = work[spans[i + 1].first].table_off -
+                             (work[spans[i].second].table_off + work[spans[i].second].cap);
+          if (g < gap) { gap = g; best = i; }
+        }
+        spans[best].second = spans[best + 1].second;
+        spans.erase(spans.begin() + best + 1);
+      }
       ph_begin(ctx, PH_OVERFLOW);
       CKR(gerbil::launch_overflow_insert(k, op, ctx->nsm, st));
       xp.mode = 1;
       xp.otab = op.otab;
       xp.ocap = ocap;
-      CKR(gerbil::launch_compact(k, xp, ctx->nsm, st));
+      for (const auto& sp : spans) {
+        xp.slot_lo = work[sp.first].table_off;
+        xp.slot_hi = work[sp.second].table_off + work[sp.second].cap;
+        CKR(gerbil::launch_compact(k, xp, ctx->nsm, st));
+      }
       CKR(gerbil::launch_overflow_emit(k, op, ctx->nsm, st));
-      ctx->times.kernel_launches += 3;
+      ctx->times.kernel_launches += 2 + spans.size();
       ph_end(ctx, PH_OVERFLOW);
       rc = read_counters(ctx);
       dev_free(ctx, otab, obytes);

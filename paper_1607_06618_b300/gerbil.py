@@ -107,6 +107,7 @@ class gerbil_job_times(ctypes.Structure):
                 "worker": int(self.worker)}
 
 
+CUDA_STREAM_LEGACY = 1  # cudaStreamLegacy
 _lib = None
 
 
@@ -458,6 +459,9 @@ class Server:
         self._keep = {}
 
     def submit(self, seq, offsets, k, m, nbins, min_count, opts=None, bin_bounds=None) -> int:
+        if hasattr(seq, "data_ptr") and seq.is_cuda:
+            import torch
+            torch.cuda.current_stream(seq.device).synchronize()  # the workers' streams do not wait
         jid = gerbil_server_submit(self.handle, seq, offsets, k, m, nbins, min_count, opts, bin_bounds)
         if hasattr(seq, "data_ptr") and seq.is_cuda:
             self._keep[jid] = (seq, offsets)  # device reads stay alive until the job is waited for
@@ -517,6 +521,10 @@ class Context:
         if stream is None:
             import torch
             stream = torch.cuda.current_stream(device).cuda_stream
+        if not stream:
+            # torch's default stream is the legacy default stream (handle 0); a NULL handle
+            # would make the context create a stream of its own that does not wait for it
+            stream = CUDA_STREAM_LEGACY
         self.device = device
         self._children = weakref.WeakSet()
         self.handle = gerbil_create(device, hbm_budget_bytes, stream)
