@@ -39,7 +39,7 @@ L2_BYTES = 126 * 2 ** 20
 def _args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
@@ -51,6 +51,9 @@ def _args():
     ap.add_argument("--fused", type=int, default=None,
                     help="phase-two form: 0 all tables, 1 fused queue kernel, 2 waves")
     ap.add_argument("--schedule", type=int, default=None, help="1 device queue, 0 fixed striding")
+    ap.add_argument("--autotune", action="store_true",
+                    help="form, schedule and per-class load factors from the autotuner")
+    ap.add_argument("--graph", action="store_true", help="phase two as one captured CUDA graph")
     ap.add_argument("--serving-jobs", type=int, default=48,
                     help="jobs of the serving stream (--workload %s)" % SERVING_WORKLOAD)
     ap.add_argument("--serving-slots", type=int, default=4)
@@ -236,6 +239,10 @@ def main_ours(a, world, rank, local):
         kw["fused"] = a.fused
     if a.schedule is not None:
         kw["schedule"] = a.schedule
+    if a.autotune:
+        kw["autotune"] = 1
+    if a.graph:
+        kw["graph"] = 1
     opts = gerbil.default_opts(**kw)
 
     info = {}
@@ -334,6 +341,7 @@ def main_ours(a, world, rank, local):
         tc = host_ms(gerbil.default_opts(fused=1))
         ts = host_ms(gerbil.default_opts(schedule=0))
         tw = host_ms(gerbil.default_opts(fused=2))
+        tg = host_ms(gerbil.default_opts(graph=1))
         tp = time.perf_counter()
         for _ in range(a.per_bin_steps):
             for b in range(nbins):
@@ -343,6 +351,7 @@ def main_ours(a, world, rank, local):
         bins.free()
         bvp = {"batched_ms": 1000 * tb, "batched_fused_ms": 1000 * tc,
                "batched_static_schedule_ms": 1000 * ts, "batched_waves_ms": 1000 * tw,
+               "batched_graph_ms": 1000 * tg,
                "per_bin_ms": 1000 * tp,
                "speedup": tp / tb,
                "what": "phase two over all %d bins, host-timed: one count_batch (persistent insert "
@@ -405,6 +414,8 @@ def main_ours(a, world, rank, local):
                            "achieved_gbs": step_bytes / (p2_ms / 1000.0) / 1e9},
             "phase_ms": phase_ms, "cpu_baseline": cpu, "e2e": e2e, "clocks": ck,
             "gpu_launches": int(ph["kernel_launches"]), "batched_vs_per_bin": bvp,
+            "opts": {key: val for key, val in kw.items()},
+            "autotune": ctx.get_tuning(k) if a.autotune else None,
             "membench": membench,
         }
         print(json.dumps(line), flush=True)
@@ -507,6 +518,8 @@ def main_serving(a, world, rank, local):
             "run_ms": {"p50": _pct([r["run_ms"] for r in out], 50),
                        "p99": _pct([r["run_ms"] for r in out], 99)},
             "makespan_s": wall, "last_arrival_s": jobs[-1]["arrival_s"],
+            "offered_kmers_per_s": occ / max(1e-9, jobs[-1]["arrival_s"]),
+            "saturated": wall > 1.1 * jobs[-1]["arrival_s"],
             "server": st, "jobs_grouped": sum(1 for r in out if r["groups"] > 1),
             "clocks": ck, "gpu_launches": int(st["kernel_launches"]),
             "cpu_baseline": None, "e2e": None,

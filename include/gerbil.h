@@ -117,7 +117,16 @@ typedef struct gerbil_opts {
                                   bin, so the groups' rows are joined unchanged).  0 (default):
                                   half of what the context's budget leaves, or half of the
                                   device's free memory when the context has no budget */
-  uint32_t reserved[2];
+  uint32_t autotune;           /* 1: use the context's tuned form, schedule and load factors
+                                  for this key width (gerbil_autotune; run on the first batch
+                                  of 8 bins or more when none is set); load_factor, fused and
+                                  schedule above are then ignored.  0 (default): as given */
+  uint32_t graph;              /* 1: the device steps of a two-grid batch (fused 0) -- table
+                                  clears, work-list upload, item map, insert grid, compaction
+                                  -- are captured into one CUDA graph and launched as one; the
+                                  context keeps the instantiated graph and updates it in place
+                                  for the next batch of the same shape.  0 (default): plain
+                                  launches */
 } gerbil_opts;
 
 /* Per-call statistics of a count. */
@@ -146,7 +155,22 @@ typedef struct gerbil_phase_times {
   uint64_t insert_launches;
   uint64_t kernel_launches; /* kernels of this library launched, counted with profiling off too */
   uint64_t calls;           /* partition + count calls */
+  uint64_t graph_launches;  /* CUDA graph launches (gerbil_opts.graph) */
 } gerbil_phase_times;
+
+/* Settings chosen by the autotuner for one key width (the paper has no autotuner; its table
+ * sizes follow one load factor).  Tables are put in a size class by their bytes at load factor
+ * 0.5: below class_bytes[0], [1], [2], or larger; each class has its own load factor. */
+#define GERBIL_TUNE_CLASSES 4
+typedef struct gerbil_tuning {
+  float load_factor[GERBIL_TUNE_CLASSES];
+  uint64_t class_bytes[GERBIL_TUNE_CLASSES - 1];
+  int32_t fused;       /* phase-two form (gerbil_opts.fused) */
+  int32_t schedule;    /* insert schedule (gerbil_opts.schedule) */
+  int32_t k_words;     /* W = ceil(2k/64) the settings are for */
+  uint32_t samples;    /* configurations timed */
+  double ns_per_kmer;  /* phase-two device time per k-mer of the sample with the chosen form */
+} gerbil_tuning;
 
 /* Fills *opts with the defaults listed above. */
 void gerbil_opts_default(gerbil_opts* opts);
@@ -298,6 +322,23 @@ int gerbil_server_get_stats(gerbil_server* s, gerbil_server_stats* out);
 
 /* Stops the workers after their current jobs and frees every result not yet handed over. */
 void gerbil_server_destroy(gerbil_server* s);
+
+/* Autotuner.  Times phase two on every 16th bin of `bins` (device events around the clears,
+ * inserts, compaction and overflow work, best of two runs per candidate): first the form and
+ * schedule (fused 0 with schedule 1 or 0, fused 1, fused 2) at load factor 0.5, then load
+ * factors 0.35 / 0.5 / 0.65 / 0.8 for each table-size class that holds at least 100,000 k-mers
+ * of the sample (other classes keep 0.5).  The choice is kept in the context for the key width
+ * of k and returned in *out (may be NULL).  Counts do not depend on any of these settings.
+ * Costs about 20 sample counts.  Errors: as gerbil_count_batch. */
+int gerbil_autotune(gerbil_ctx* ctx, const gerbil_bins* bins, int k, uint32_t min_count,
+                    const gerbil_opts* opts, gerbil_tuning* out);
+
+/* Sets (t != NULL, e.g. from a cache of earlier runs) or clears (t == NULL) the tuned settings
+ * the context uses for the key width of k.  Errors: E_INVAL (a value out of range). */
+int gerbil_set_tuning(gerbil_ctx* ctx, int k, const gerbil_tuning* t);
+
+/* Reads the settings held for the key width of k.  Errors: E_INVAL, E_STATE (none held). */
+int gerbil_get_tuning(const gerbil_ctx* ctx, int k, gerbil_tuning* out);
 
 /* Memory-throughput probe (the paper has no counterpart; a measurement helper for the
  * roofline of the insert kernel).  Runs one kernel in which every thread performs per_thread

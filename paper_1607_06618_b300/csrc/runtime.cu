@@ -45,6 +45,14 @@ struct gerbil_ctx {
   cudaEvent_t ev[2 * 8] = {};
   bool pending[8] = {};
   gerbil_phase_times times{};
+  // settings chosen by gerbil_autotune, per key width W
+  std::map<int, gerbil_tuning> tuning;
+  // graph form (gerbil_opts.graph): capture stream, the instantiated graph of the last batch
+  // (updated in place when the next batch's graph has the same shape), pinned work-list copy
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  void* hwork = nullptr;
+  size_t hwork_bytes = 0;
 };
 
 struct gerbil_bins {
@@ -138,12 +146,18 @@ int words_for(int k) { return (2 * k + 63) / 64; }
 
 enum Phase { PH_ENCODE = 0, PH_SUPER0, PH_SUPER1, PH_CLEAR, PH_INSERT, PH_COMPACT, PH_OVERFLOW, PH_N };
 
-void ph_begin(gerbil_ctx* ctx, int ph) {
-  if (ctx->profiling) cudaEventRecord(ctx->ev[2 * ph], ctx->stream);
+// Phase events go on the context's stream, or on `s` while it is being captured into a graph
+// (recorded as event nodes that fire when the graph runs).
+void ph_record(gerbil_ctx* ctx, cudaEvent_t e, cudaStream_t s, bool captured) {
+  if (captured) cudaEventRecordWithFlags(e, s, cudaEventRecordExternal);
+  else cudaEventRecord(e, ctx->stream);
 }
-void ph_end(gerbil_ctx* ctx, int ph) {
+void ph_begin(gerbil_ctx* ctx, int ph, cudaStream_t s = nullptr, bool captured = false) {
+  if (ctx->profiling) ph_record(ctx, ctx->ev[2 * ph], s, captured);
+}
+void ph_end(gerbil_ctx* ctx, int ph, cudaStream_t s = nullptr, bool captured = false) {
   if (!ctx->profiling) return;
-  cudaEventRecord(ctx->ev[2 * ph + 1], ctx->stream);
+  ph_record(ctx, ctx->ev[2 * ph + 1], s, captured);
   ctx->pending[ph] = true;
 }
 // Adds the elapsed time of every finished phase; call only after the stream has synchronized
@@ -269,6 +283,9 @@ void gerbil_destroy(gerbil_ctx* ctx) {
   }
   for (cudaEvent_t e : ctx->ev)
     if (e) cudaEventDestroy(e);
+  if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
+  if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+  if (ctx->hwork) cudaFreeHost(ctx->hwork);
   if (ctx->ctr) cudaFree(ctx->ctr);
   if (ctx->hctr) cudaFreeHost(ctx->hctr);
   if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
@@ -597,6 +614,41 @@ void gerbil_bins_free(gerbil_bins* b) {
 }
 
 // ---- phase two ---------------------------------------------------------------------------------
+// ---- table sizing (Sec. 3.4) ---------------------------------------------------------------------
+// capacity = expected distinct keys / load factor, the load factor taken per table-size class
+// (class = table bytes at load factor 0.5), so that the autotuner can pick denser tables where
+// they stay in L2 and sparser ones where probes go to HBM.
+struct Sizing {
+  double alpha[GERBIL_TUNE_CLASSES];
+  uint64_t bound[GERBIL_TUNE_CLASSES - 1];  // class upper bounds, bytes
+  uint64_t slot_bytes;
+  int cls(double est) const {
+    const double bytes = est / 0.5 * (double)slot_bytes;
+    for (int c = 0; c < GERBIL_TUNE_CLASSES - 1; ++c)
+      if (bytes < (double)bound[c]) return c;
+    return GERBIL_TUNE_CLASSES - 1;
+  }
+  uint64_t cap(double est) const { return (uint64_t)std::ceil(est / alpha[cls(est)]) + 16; }
+};
+
+static const uint64_t kClassBound[GERBIL_TUNE_CLASSES - 1] = {4ull << 20, 64ull << 20, 1ull << 30};
+
+static Sizing make_sizing(const gerbil_ctx* ctx, const gerbil_opts& o, int k) {
+  Sizing z{};
+  z.slot_bytes = 8ull * gerbil::slot_words_for_k(k);
+  const double a = (o.load_factor > 0.05f && o.load_factor <= 0.95f) ? o.load_factor : 0.5;
+  for (int c = 0; c < GERBIL_TUNE_CLASSES; ++c) z.alpha[c] = a;
+  for (int c = 0; c < GERBIL_TUNE_CLASSES - 1; ++c) z.bound[c] = kClassBound[c];
+  if (o.autotune) {
+    auto it = ctx->tuning.find(words_for(k));
+    if (it != ctx->tuning.end())
+      for (int c = 0; c < GERBIL_TUNE_CLASSES; ++c)
+        if (it->second.load_factor[c] > 0.05f && it->second.load_factor[c] <= 0.95f)
+          z.alpha[c] = it->second.load_factor[c];
+  }
+  return z;
+}
+
 // ---- phase two, fused persistent form -----------------------------------------------------------
 // Returns FUSED_FALLBACK when the overflow area was used: the result is then recomputed by the
 // classic form, which merges overflow counts.
@@ -605,7 +657,7 @@ static const int LAG = 5;  // bins between a bin's inserts and its compaction in
 
 static int count_fused(gerbil_ctx* ctx, const gerbil_bins* b, const std::vector<int32_t>& list,
                        int k, uint32_t min_count, const gerbil_opts& opts, double ratio,
-                       double alpha, uint32_t theta, uint32_t spin_limit, gerbil_counts** out) {
+                       const Sizing& sz, uint32_t theta, uint32_t spin_limit, gerbil_counts** out) {
   const int W = words_for(k);
   const int SW = gerbil::slot_words_for_k(k);
   cudaStream_t st = ctx->stream;
@@ -618,7 +670,7 @@ static int count_fused(gerbil_ctx* ctx, const gerbil_bins* b, const std::vector<
     w.n_super = (uint32_t)b->nsuper[bi];
     w.n_kmers = (uint32_t)b->nkmers[bi];
     const double est = std::max(1.0, std::ceil(ratio * (double)w.n_kmers));
-    w.cap = (uint32_t)std::min<uint64_t>((uint64_t)std::ceil(est / alpha) + 16, 0xFFFFF000ull);
+    w.cap = (uint32_t)std::min<uint64_t>(sz.cap(est), 0xFFFFF000ull);
     w.n_items = (w.n_kmers + gerbil::ITEM_KMERS - 1) / gerbil::ITEM_KMERS;
     w.n_chunks = (w.cap + gerbil::CHUNK_SLOTS - 1) / gerbil::CHUNK_SLOTS;
     occ += w.n_kmers;
@@ -837,7 +889,7 @@ static const int WAVES_FALLBACK = -2;
 
 static int count_waves(gerbil_ctx* ctx, const gerbil_bins* b, const std::vector<int32_t>& list,
                        int k, uint32_t min_count, const gerbil_opts& opts, double ratio,
-                       double alpha, uint32_t theta, uint32_t spin_limit, gerbil_counts** out) {
+                       const Sizing& sz, uint32_t theta, uint32_t spin_limit, gerbil_counts** out) {
   const int W = words_for(k);
   const int SW = gerbil::slot_words_for_k(k);
   cudaStream_t st = ctx->stream;
@@ -850,7 +902,7 @@ static int count_waves(gerbil_ctx* ctx, const gerbil_bins* b, const std::vector<
     w.n_super = (uint32_t)b->nsuper[bi];
     w.n_kmers = (uint32_t)b->nkmers[bi];
     const double est = std::max(1.0, std::ceil(ratio * (double)w.n_kmers));
-    w.cap = (uint32_t)std::min<uint64_t>((uint64_t)std::ceil(est / alpha) + 16, 0xFFFFF000ull);
+    w.cap = (uint32_t)std::min<uint64_t>(sz.cap(est), 0xFFFFF000ull);
     w.item_begin = (uint32_t)items;
     items += (w.n_kmers + gerbil::ITEM_KMERS - 1) / gerbil::ITEM_KMERS;
     occ += w.n_kmers;
@@ -1029,11 +1081,28 @@ static void join_part(gerbil_counts* joined, gerbil_counts* part) {
   }
 }
 
+static int autotune_impl(gerbil_ctx* ctx, const gerbil_bins* b, const std::vector<int32_t>& list,
+                         int k, uint32_t min_count, const gerbil_opts& opts, gerbil_tuning* out);
+
 static int count_impl(gerbil_ctx* ctx, const gerbil_bins* b, const std::vector<int32_t>& list,
-                      int k, uint32_t min_count, const gerbil_opts& opts, gerbil_counts** out) {
+                      int k, uint32_t min_count, const gerbil_opts& opts_in, gerbil_counts** out) {
   const int W = words_for(k);
   cudaStream_t st = ctx->stream;
-  const double alpha = (opts.load_factor > 0.05f && opts.load_factor <= 0.95f) ? opts.load_factor : 0.5;
+  gerbil_opts opts = opts_in;
+  if (opts.autotune) {  // the tuned form, schedule and load factors (tuned here on first use)
+    auto it = ctx->tuning.find(W);
+    if (it == ctx->tuning.end() && list.size() >= 8) {
+      gerbil_tuning t{};
+      const int rc = autotune_impl(ctx, b, list, k, min_count, opts, &t);
+      if (rc) return rc;
+      it = ctx->tuning.find(W);
+    }
+    if (it != ctx->tuning.end()) {
+      opts.fused = it->second.fused;
+      opts.schedule = it->second.schedule;
+    }
+  }
+  const Sizing sz = make_sizing(ctx, opts, k);
   double ratio = opts.distinct_ratio > 0.0f ? std::min(1.0, (double)opts.distinct_ratio)
                                             : std::min(1.0, ctx->ratio_known ? ctx->ratio * 1.25 : 1.0);
   uint32_t theta = opts.max_probes ? opts.max_probes : 1024;
@@ -1072,7 +1141,7 @@ static int count_impl(gerbil_ctx* ctx, const gerbil_bins* b, const std::vector<i
     auto bin_bytes = [&](int32_t bi) -> uint64_t {
       if (b->nkmers[bi] == 0) return 0;
       const double est = std::max(1.0, std::ceil(ratio * (double)b->nkmers[bi]));
-      return ((uint64_t)std::ceil(est / alpha) + 16) * slot_bytes;
+      return sz.cap(est) * slot_bytes;
     };
     uint64_t need = 0;
     for (int32_t bi : list) need += bin_bytes(bi);
@@ -1104,10 +1173,10 @@ static int count_impl(gerbil_ctx* ctx, const gerbil_bins* b, const std::vector<i
   }
 
   if (opts.fused == 1) {
-    const int rc = count_fused(ctx, b, list, k, min_count, opts, ratio, alpha, theta, spin_limit, out);
+    const int rc = count_fused(ctx, b, list, k, min_count, opts, ratio, sz, theta, spin_limit, out);
     if (rc != FUSED_FALLBACK) return rc;
   } else if (opts.fused == 2) {
-    const int rc = count_waves(ctx, b, list, k, min_count, opts, ratio, alpha, theta, spin_limit, out);
+    const int rc = count_waves(ctx, b, list, k, min_count, opts, ratio, sz, theta, spin_limit, out);
     if (rc != WAVES_FALLBACK) return rc;
   }
 
@@ -1124,7 +1193,7 @@ static int count_impl(gerbil_ctx* ctx, const gerbil_bins* b, const std::vector<i
       w.n_super = (uint32_t)b->nsuper[bi];
       w.n_kmers = (uint32_t)b->nkmers[bi];
       const double est = std::max(1.0, std::ceil(ratio * (double)w.n_kmers));
-      uint64_t cap = (uint64_t)std::ceil(est / alpha) + 16;
+      uint64_t cap = sz.cap(est);
       cap = std::min<uint64_t>(cap, 0xFFFFFFF0ull);
       w.cap = (uint32_t)cap;
       w.table_off = slots;
@@ -1171,14 +1240,72 @@ static int count_impl(gerbil_ctx* ctx, const gerbil_bins* b, const std::vector<i
     }                                                                                      \
   } while (0)
 
+    // Graph form: the device steps below (clears, work upload, item map, insert, compaction)
+    // are captured on a side stream into one CUDA graph and launched on the context's stream;
+    // the graph of the previous batch is updated in place when the shape allows.
+    const bool graph = opts.graph != 0;
+    bool capturing = false;
+    cudaStream_t ls = st;  // stream the device steps are issued to
+#define CKG(call)                                                                          \
+  do {                                                                                     \
+    cudaError_t e_ = (call);                                                               \
+    if (e_ != cudaSuccess) {                                                               \
+      if (capturing) {                                                                     \
+        cudaGraph_t g_ = nullptr;                                                          \
+        cudaStreamEndCapture(ctx->cap_stream, &g_);                                        \
+        if (g_) cudaGraphDestroy(g_);                                                      \
+        cudaGetLastError();                                                                \
+      }                                                                                    \
+      drop();                                                                              \
+      return fail(ctx, GERBIL_E_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    }                                                                                      \
+  } while (0)
+    auto alloc_res = [&](uint64_t cap) -> int {
+      res = new (std::nothrow) gerbil_counts;
+      if (!res) return GERBIL_E_NOMEM;
+      res->ctx = ctx;
+      res->W = W;
+      res->bytes = cap * (W * 8 + 4);
+      int r;
+      if ((r = dev_alloc(ctx, (void**)&res->keys, cap * W * 8))) {
+        delete res;
+        res = nullptr;
+        return r;
+      }
+      if ((r = dev_alloc(ctx, (void**)&res->counts, cap * 4))) {
+        dev_free(ctx, res->keys, cap * W * 8);
+        delete res;
+        res = nullptr;
+        return r;
+      }
+      return GERBIL_OK;
+    };
+    if (!exact_out && (rc = alloc_res(out_cap))) return rc;  // allocated ahead of the steps
+    const void* work_src = work.data();
+    if (graph) {
+      if (!ctx->cap_stream) CKR(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+      if (work_bytes > ctx->hwork_bytes) {
+        if (ctx->hwork) cudaFreeHost(ctx->hwork);
+        ctx->hwork = nullptr;
+        ctx->hwork_bytes = 0;
+        CKR(cudaMallocHost(&ctx->hwork, work_bytes));
+        ctx->hwork_bytes = work_bytes;
+      }
+      if (work_bytes) std::memcpy(ctx->hwork, work.data(), work_bytes);
+      work_src = ctx->hwork;
+      CKR(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
+      capturing = true;
+      ls = ctx->cap_stream;
+    }
+
     ctx->times.calls++;
-    ph_begin(ctx, PH_CLEAR);
-    CKR(cudaMemsetAsync(ctx->arena, 0, arena_need, st));
+    ph_begin(ctx, PH_CLEAR, ls, capturing);
+    CKG(cudaMemsetAsync(ctx->arena, 0, arena_need, ls));
     ctx->arena_dirty = std::max(ctx->arena_dirty, arena_need);  // tables stay in the arena
-    CKR(cudaMemsetAsync(ctx->ctr, 0, sizeof(Counters), st));
+    CKG(cudaMemsetAsync(ctx->ctr, 0, sizeof(Counters), ls));
     if (!work.empty()) {
-      CKR(cudaMemcpyAsync(dwork, work.data(), work_bytes, cudaMemcpyHostToDevice, st));
-      CKR(cudaMemsetAsync(bin_ovf, 0, work.size() * 4, st));
+      CKG(cudaMemcpyAsync(dwork, work_src, work_bytes, cudaMemcpyHostToDevice, ls));
+      CKG(cudaMemsetAsync(bin_ovf, 0, work.size() * 4, ls));
     }
 
     gerbil::CountParams cp{};
@@ -1202,65 +1329,78 @@ static int count_impl(gerbil_ctx* ctx, const gerbil_bins* b, const std::vector<i
     cp.ctr = ctx->ctr;
     cp.schedule = opts.schedule;
     if (items) {
-      CKR(gerbil::launch_item_map(cp, st));  // preparation: timed with the clears
+      CKG(gerbil::launch_item_map(cp, ls));  // preparation: timed with the clears
       ctx->times.kernel_launches++;
     }
-    ph_end(ctx, PH_CLEAR);
-    ph_begin(ctx, PH_INSERT);
+    ph_end(ctx, PH_CLEAR, ls, capturing);
+    ph_begin(ctx, PH_INSERT, ls, capturing);
     if (items) {
-      CKR(gerbil::launch_insert(k, cp, opts.persistent, ctx->nsm, st));
+      CKG(gerbil::launch_insert(k, cp, opts.persistent, ctx->nsm, ls));
       ctx->times.kernel_launches++;
       ctx->times.insert_launches++;
     }
-    ph_end(ctx, PH_INSERT);
+    ph_end(ctx, PH_INSERT, ls, capturing);
     gerbil::CompactParams xp{};
-    if (exact_out) {  // count the rows (live slots with count >= min_count), then size exactly
-      gerbil::CompactParams cx{};
-      cx.work = dwork;
-      cx.nwork = (uint32_t)work.size();
-      cx.slot_lo = 0;
-      cx.slot_hi = slots;
-      cx.arena = (unsigned long long*)ctx->arena;
-      cx.bin_ovf = bin_ovf;
-      cx.mode = 2;
-      cx.min_count = min_count;
-      cx.ctr = ctx->ctr;
-      CKR(gerbil::launch_compact(k, cx, ctx->nsm, st));
-      ctx->times.kernel_launches++;
-      if ((rc = read_counters(ctx))) return rc;
-      const Counters hc = *ctx->hctr;
-      // deferred bins can add at most one row per overflow k-mer, the overflow table as many
-      out_cap = std::max<uint64_t>(1, hc.out_count + 2 * std::min<uint64_t>(hc.ovf_count, ovf_cap));
-      CKR(cudaMemsetAsync(&ctx->ctr->out_count, 0, 8, st));
-      CKR(cudaMemsetAsync(&ctx->ctr->distinct, 0, 8, st));
-    }
-    res = new (std::nothrow) gerbil_counts;
-    if (!res) return GERBIL_E_NOMEM;
-    res->ctx = ctx;
-    res->W = W;
-    res->bytes = out_cap * (W * 8 + 4);
-    if ((rc = dev_alloc(ctx, (void**)&res->keys, out_cap * W * 8))) { delete res; return rc; }
-    if ((rc = dev_alloc(ctx, (void**)&res->counts, out_cap * 4))) {
-      dev_free(ctx, res->keys, out_cap * W * 8);
-      delete res;
-      return rc;
-    }
     xp.work = dwork;
     xp.nwork = (uint32_t)work.size();
     xp.slot_lo = 0;
     xp.slot_hi = slots;
     xp.arena = (unsigned long long*)ctx->arena;
     xp.bin_ovf = bin_ovf;
-    xp.mode = 0;
     xp.min_count = min_count;
-    xp.out_keys = res->keys;
-    xp.out_counts = res->counts;
-    xp.out_cap = out_cap;
     xp.ctr = ctx->ctr;
-    ph_begin(ctx, PH_COMPACT);
-    CKR(gerbil::launch_compact(k, xp, ctx->nsm, st));
-    if (slots) ctx->times.kernel_launches++;
-    ph_end(ctx, PH_COMPACT);
+    if (exact_out) {  // count the rows (live slots with count >= min_count), then size exactly
+      xp.mode = 2;
+      CKG(gerbil::launch_compact(k, xp, ctx->nsm, ls));
+      ctx->times.kernel_launches++;
+    } else {
+      xp.mode = 0;
+      xp.out_keys = res->keys;
+      xp.out_counts = res->counts;
+      xp.out_cap = out_cap;
+      ph_begin(ctx, PH_COMPACT, ls, capturing);
+      CKG(gerbil::launch_compact(k, xp, ctx->nsm, ls));
+      if (slots) ctx->times.kernel_launches++;
+      ph_end(ctx, PH_COMPACT, ls, capturing);
+    }
+    if (capturing) {
+      cudaGraph_t g = nullptr;
+      capturing = false;
+      CKR(cudaStreamEndCapture(ctx->cap_stream, &g));
+      bool updated = false;
+      if (ctx->gexec) {
+        cudaGraphExecUpdateResultInfo info{};
+        updated = cudaGraphExecUpdate(ctx->gexec, g, &info) == cudaSuccess;
+        if (!updated) {
+          cudaGetLastError();
+          cudaGraphExecDestroy(ctx->gexec);
+          ctx->gexec = nullptr;
+        }
+      }
+      cudaError_t e = updated ? cudaSuccess : cudaGraphInstantiate(&ctx->gexec, g, 0);
+      cudaGraphDestroy(g);
+      CKR(e);
+      CKR(cudaGraphLaunch(ctx->gexec, st));
+      ctx->times.graph_launches++;
+    }
+    if (exact_out) {
+      if ((rc = read_counters(ctx))) return rc;
+      const Counters hc = *ctx->hctr;
+      // deferred bins can add at most one row per overflow k-mer, the overflow table as many
+      out_cap = std::max<uint64_t>(1, hc.out_count + 2 * std::min<uint64_t>(hc.ovf_count, ovf_cap));
+      CKR(cudaMemsetAsync(&ctx->ctr->out_count, 0, 8, st));
+      CKR(cudaMemsetAsync(&ctx->ctr->distinct, 0, 8, st));
+      if ((rc = alloc_res(out_cap))) return rc;
+      xp.mode = 0;
+      xp.out_keys = res->keys;
+      xp.out_counts = res->counts;
+      xp.out_cap = out_cap;
+      ph_begin(ctx, PH_COMPACT);
+      CKR(gerbil::launch_compact(k, xp, ctx->nsm, st));
+      if (slots) ctx->times.kernel_launches++;
+      ph_end(ctx, PH_COMPACT);
+    }
+#undef CKG
     if ((rc = read_counters(ctx))) { drop(); return rc; }
     Counters h = *ctx->hctr;
     if (h.err & gerbil::ERR_OVF_FULL) {
@@ -1368,6 +1508,151 @@ static int count_checks(gerbil_ctx* ctx, const gerbil_bins* b, int k, uint32_t m
   if (min_count < 1) return fail(ctx, GERBIL_E_INVAL, "min_count must be >= 1");
   if (opts.canonical && !b->canon_min)
     return fail(ctx, GERBIL_E_INVAL, "canonical counting needs canonical minimizers");
+  return GERBIL_OK;
+}
+
+// ---- autotuner ---------------------------------------------------------------------------------
+// Picks the phase-two form and schedule, then a load factor per table-size class, by timing
+// candidates on a sample of the batch's bins (every 16th bin) with device events around the
+// clears, inserts, compaction and overflow work.  Every candidate gives the same counts; only
+// time differs.
+static int tune_time(gerbil_ctx* ctx, const gerbil_bins* b, const std::vector<int32_t>& sample, int k,
+                     uint32_t min_count, const gerbil_opts& o, double* ms_out) {
+  double best = 1e30;
+  for (int rep = 0; rep < 2; ++rep) {
+    std::memset(&ctx->times, 0, sizeof(ctx->times));
+    gerbil_counts* tmp = nullptr;
+    const int rc = count_impl(ctx, b, sample, k, min_count, o, &tmp);
+    if (rc) return rc;
+    gerbil_counts_free(tmp);
+    CK(cudaStreamSynchronize(ctx->stream));
+    ph_collect(ctx, true);
+    const gerbil_phase_times& t = ctx->times;
+    best = std::min(best, t.clear_ms + t.insert_ms + t.compact_ms + t.overflow_ms);
+  }
+  *ms_out = best;
+  return GERBIL_OK;
+}
+
+static int autotune_impl(gerbil_ctx* ctx, const gerbil_bins* b, const std::vector<int32_t>& list,
+                         int k, uint32_t min_count, const gerbil_opts& opts_in, gerbil_tuning* out) {
+  const int W = words_for(k);
+  gerbil_opts o = opts_in;
+  o.autotune = 0;
+  o.fused = 0;
+  o.schedule = 1;
+  o.load_factor = 0.5f;
+  std::vector<int32_t> sample;
+  const size_t step = std::max<size_t>(1, list.size() / 16);
+  for (size_t i = 0; i < list.size(); i += step) sample.push_back(list[i]);
+  uint64_t occ = 0;
+  for (int32_t bi : sample) occ += b->nkmers[bi];
+  if (occ == 0) return fail(ctx, GERBIL_E_INVAL, "autotune: the sample holds no k-mers");
+
+  // device timing for the duration of the tuning; the caller's profile is put back after
+  const bool was_profiling = ctx->profiling;
+  const gerbil_phase_times saved = ctx->times;
+  CK(cudaStreamSynchronize(ctx->stream));
+  ph_collect(ctx, true);
+  ctx->profiling = true;
+  gerbil_tuning t{};
+  int rc = GERBIL_OK;
+  auto restore = [&]() {
+    cudaStreamSynchronize(ctx->stream);
+    ph_collect(ctx, true);
+    ctx->profiling = was_profiling;
+    ctx->times = saved;
+  };
+  {  // learn the distinct ratio on the sample first (Sec. 3.4)
+    gerbil_counts* tmp = nullptr;
+    if ((rc = count_impl(ctx, b, sample, k, min_count, o, &tmp))) { restore(); return rc; }
+    gerbil_counts_free(tmp);
+  }
+  // 1. form and schedule at load factor 0.5
+  static const int forms[][2] = {{0, 1}, {0, 0}, {1, 1}, {2, 1}};
+  double best = 1e30;
+  int bf = 0, bs = 1;
+  for (const auto& f : forms) {
+    o.fused = f[0];
+    o.schedule = f[1];
+    double ms = 0;
+    if ((rc = tune_time(ctx, b, sample, k, min_count, o, &ms))) { restore(); return rc; }
+    t.samples++;
+    if (ms < best) { best = ms; bf = f[0]; bs = f[1]; }
+  }
+  o.fused = bf;
+  o.schedule = bs;
+  // 2. load factor per table-size class, on the sample's bins of that class
+  const Sizing z0 = make_sizing(ctx, o, k);
+  const double ratio = std::min(1.0, ctx->ratio_known ? ctx->ratio * 1.25 : 1.0);
+  static const float alphas[] = {0.35f, 0.5f, 0.65f, 0.8f};
+  for (int c = 0; c < GERBIL_TUNE_CLASSES; ++c) {
+    t.load_factor[c] = 0.5f;
+    std::vector<int32_t> sub;
+    uint64_t sub_occ = 0;
+    for (int32_t bi : sample) {
+      if (!b->nkmers[bi]) continue;
+      if (z0.cls(std::max(1.0, std::ceil(ratio * (double)b->nkmers[bi]))) != c) continue;
+      sub.push_back(bi);
+      sub_occ += b->nkmers[bi];
+    }
+    if (sub.empty() || sub_occ < 100000) continue;  // too little to time: keep 0.5
+    double cbest = 1e30;
+    for (float a : alphas) {
+      o.load_factor = a;
+      double ms = 0;
+      if ((rc = tune_time(ctx, b, sub, k, min_count, o, &ms))) { restore(); return rc; }
+      t.samples++;
+      if (ms < cbest) { cbest = ms; t.load_factor[c] = a; }
+    }
+  }
+  o.load_factor = 0.5f;
+  for (int c = 0; c < GERBIL_TUNE_CLASSES - 1; ++c) t.class_bytes[c] = kClassBound[c];
+  t.fused = bf;
+  t.schedule = bs;
+  t.k_words = W;
+  t.ns_per_kmer = best * 1e6 / (double)occ;
+  restore();
+  ctx->tuning[W] = t;
+  if (out) *out = t;
+  return GERBIL_OK;
+}
+
+int gerbil_autotune(gerbil_ctx* ctx, const gerbil_bins* b, int k, uint32_t min_count,
+                    const gerbil_opts* opts_in, gerbil_tuning* out) {
+  if (!ctx || !b) return GERBIL_E_INVAL;
+  gerbil_opts opts;
+  if (opts_in) opts = *opts_in; else gerbil_opts_default(&opts);
+  int rc = count_checks(ctx, b, k, min_count, opts);
+  if (rc) return rc;
+  CK(cudaSetDevice(ctx->device));
+  std::vector<int32_t> list;
+  for (int i = 0; i < b->nbins; ++i) list.push_back(i);
+  return autotune_impl(ctx, b, list, k, min_count, opts, out);
+}
+
+int gerbil_set_tuning(gerbil_ctx* ctx, int k, const gerbil_tuning* t) {
+  if (!ctx || k < GERBIL_MIN_K || k > GERBIL_MAX_K) return GERBIL_E_INVAL;
+  if (!t) {
+    ctx->tuning.erase(words_for(k));
+    return GERBIL_OK;
+  }
+  if (t->fused < 0 || t->fused > 2 || t->schedule < 0 || t->schedule > 1)
+    return fail(ctx, GERBIL_E_INVAL, "tuning: form or schedule out of range");
+  for (int c = 0; c < GERBIL_TUNE_CLASSES; ++c)
+    if (!(t->load_factor[c] > 0.05f && t->load_factor[c] <= 0.95f))
+      return fail(ctx, GERBIL_E_INVAL, "tuning: load factor out of range");
+  gerbil_tuning c = *t;
+  c.k_words = words_for(k);
+  ctx->tuning[c.k_words] = c;
+  return GERBIL_OK;
+}
+
+int gerbil_get_tuning(const gerbil_ctx* ctx, int k, gerbil_tuning* out) {
+  if (!ctx || !out || k < GERBIL_MIN_K || k > GERBIL_MAX_K) return GERBIL_E_INVAL;
+  auto it = ctx->tuning.find(words_for(k));
+  if (it == ctx->tuning.end()) return GERBIL_E_STATE;
+  *out = it->second;
   return GERBIL_OK;
 }
 

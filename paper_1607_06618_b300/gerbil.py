@@ -39,6 +39,7 @@ ABI_SYMBOLS = (
     "gerbil_profile", "gerbil_get_phase_times", "gerbil_count_small_noalloc", "gerbil_membench",
     "gerbil_trim", "gerbil_device_bytes", "gerbil_server_create", "gerbil_server_submit",
     "gerbil_server_wait", "gerbil_server_get_stats", "gerbil_server_destroy",
+    "gerbil_autotune", "gerbil_set_tuning", "gerbil_get_tuning",
 )
 
 
@@ -62,7 +63,37 @@ class gerbil_opts(ctypes.Structure):
                 ("overflow_slots", ctypes.c_uint32), ("persistent", ctypes.c_int32),
                 ("ring_slots", ctypes.c_uint32), ("fused", ctypes.c_int32),
                 ("schedule", ctypes.c_int32), ("max_table_mib", ctypes.c_uint32),
-                ("reserved", ctypes.c_uint32 * 2)]
+                ("autotune", ctypes.c_uint32), ("graph", ctypes.c_uint32)]
+
+
+TUNE_CLASSES = 4
+
+
+class gerbil_tuning(ctypes.Structure):
+    _fields_ = [("load_factor", ctypes.c_float * TUNE_CLASSES),
+                ("class_bytes", ctypes.c_uint64 * (TUNE_CLASSES - 1)),
+                ("fused", ctypes.c_int32), ("schedule", ctypes.c_int32),
+                ("k_words", ctypes.c_int32), ("samples", ctypes.c_uint32),
+                ("ns_per_kmer", ctypes.c_double)]
+
+    def as_dict(self):
+        return {"load_factor": [float(x) for x in self.load_factor],
+                "class_bytes": [int(x) for x in self.class_bytes],
+                "fused": int(self.fused), "schedule": int(self.schedule),
+                "k_words": int(self.k_words), "samples": int(self.samples),
+                "ns_per_kmer": float(self.ns_per_kmer)}
+
+    @classmethod
+    def from_dict(cls, d):
+        t = cls()
+        for i, x in enumerate(d["load_factor"]):
+            t.load_factor[i] = x
+        for i, x in enumerate(d.get("class_bytes", [])):
+            t.class_bytes[i] = x
+        t.fused, t.schedule = d["fused"], d["schedule"]
+        t.k_words, t.samples = d.get("k_words", 0), d.get("samples", 0)
+        t.ns_per_kmer = d.get("ns_per_kmer", 0.0)
+        return t
 
 
 class gerbil_count_stats(ctypes.Structure):
@@ -80,7 +111,7 @@ class gerbil_phase_times(ctypes.Structure):
                 ("clear_ms", ctypes.c_double), ("insert_ms", ctypes.c_double),
                 ("compact_ms", ctypes.c_double), ("overflow_ms", ctypes.c_double),
                 ("insert_launches", ctypes.c_uint64), ("kernel_launches", ctypes.c_uint64),
-                ("calls", ctypes.c_uint64)]
+                ("calls", ctypes.c_uint64), ("graph_launches", ctypes.c_uint64)]
 
     def as_dict(self):
         return {name: (float if t is ctypes.c_double else int)(getattr(self, name))
@@ -144,6 +175,10 @@ def load() -> ctypes.CDLL:
         "gerbil_counts_free": (None, [P]),
         "gerbil_profile": (I32, [P, I32]),
         "gerbil_trim": (I32, [P]),
+        "gerbil_autotune": (I32, [P, P, I32, U32, ctypes.POINTER(gerbil_opts),
+                                  ctypes.POINTER(gerbil_tuning)]),
+        "gerbil_set_tuning": (I32, [P, I32, ctypes.POINTER(gerbil_tuning)]),
+        "gerbil_get_tuning": (I32, [P, I32, ctypes.POINTER(gerbil_tuning)]),
         "gerbil_device_bytes": (U64, [P]),
         "gerbil_server_create": (I32, [PP, I32, U64, I32]),
         "gerbil_server_submit": (I32, [P, ctypes.POINTER(gerbil_reads), I32, I32, I32, U32,
@@ -334,6 +369,27 @@ def gerbil_count_small_noalloc(seq, offsets, k: int, min_count: int, canonical: 
                                            counts_out.data_ptr(), cap, ctypes.byref(n), stream)
     _check(st)
     return n.value
+
+
+def gerbil_autotune(ctx, bins, k: int, min_count: int, opts: gerbil_opts | None = None) -> dict:
+    t = gerbil_tuning()
+    o = opts if opts is not None else default_opts()
+    _check(load().gerbil_autotune(ctx, bins, k, min_count, ctypes.byref(o), ctypes.byref(t)), ctx)
+    return t.as_dict()
+
+
+def gerbil_set_tuning(ctx, k: int, tuning: dict | None):
+    t = gerbil_tuning.from_dict(tuning) if tuning is not None else None
+    _check(load().gerbil_set_tuning(ctx, k, ctypes.byref(t) if t is not None else None), ctx)
+
+
+def gerbil_get_tuning(ctx, k: int) -> dict | None:
+    t = gerbil_tuning()
+    st = load().gerbil_get_tuning(ctx, k, ctypes.byref(t))
+    if st == GERBIL_E_STATE:
+        return None
+    _check(st, ctx)
+    return t.as_dict()
 
 
 def gerbil_trim(ctx):
@@ -534,6 +590,15 @@ class Context:
 
     def count(self, bins: Bins, b: int, k: int, min_count: int, opts=None) -> Counts:
         return Counts(gerbil_count(self.handle, bins.handle, b, k, min_count, opts), self)
+
+    def autotune(self, bins: Bins, k: int, min_count: int, opts=None) -> dict:
+        return gerbil_autotune(self.handle, bins.handle, k, min_count, opts)
+
+    def set_tuning(self, k: int, tuning: dict | None):
+        gerbil_set_tuning(self.handle, k, tuning)
+
+    def get_tuning(self, k: int) -> dict | None:
+        return gerbil_get_tuning(self.handle, k)
 
     def count_batch(self, bins: Bins, bin_list, k: int, min_count: int, opts=None) -> Counts:
         return Counts(gerbil_count_batch(self.handle, bins.handle, bin_list, k, min_count, opts), self)

@@ -59,3 +59,36 @@ def test_no_cpu_fallback_without_gpu(lib):
     assert st == gerbil.GERBIL_E_CUDA and not h.value
     with pytest.raises(gerbil.GerbilError):
         gerbil.gerbil_create(0)
+
+
+def test_struct_layouts_match_header(tmp_path):
+    """The ctypes mirrors have the C structs' sizes and field offsets (gcc on the header)."""
+    import ctypes
+    import shutil
+    import subprocess
+    from paper_1607_06618_b300 import gerbil
+    if shutil.which("gcc") is None:
+        pytest.skip("no gcc")
+    structs = {"gerbil_reads": gerbil.gerbil_reads, "gerbil_opts": gerbil.gerbil_opts,
+               "gerbil_count_stats": gerbil.gerbil_count_stats,
+               "gerbil_phase_times": gerbil.gerbil_phase_times,
+               "gerbil_tuning": gerbil.gerbil_tuning,
+               "gerbil_server_stats": gerbil.gerbil_server_stats,
+               "gerbil_job_times": gerbil.gerbil_job_times}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "gerbil.h"', "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append('printf("%s %%zu\\n", sizeof(%s));' % (name, name))
+        for fname, _ in cls._fields_:
+            lines.append('printf("%s.%s %%zu\\n", offsetof(%s, %s));' % (name, fname, name, fname))
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True)
+    got = dict(line.split() for line in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                       check=True).stdout.splitlines())
+    for name, cls in structs.items():
+        assert int(got[name]) == ctypes.sizeof(cls), name
+        for fname, _ in cls._fields_:
+            assert int(got["%s.%s" % (name, fname)]) == getattr(cls, fname).offset, (name, fname)

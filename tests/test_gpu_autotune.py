@@ -1,0 +1,110 @@
+"""Autotuner: the settings it picks are in range, are kept per key width, and counting with
+them -- or with any other settings in the search space -- gives the oracle's rows exactly."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1607_06618_b300 import synth
+from tests._util import assert_same_rows
+
+pytestmark = pytest.mark.gpu
+
+K, M, NBINS = 65, 9, 64
+
+
+@pytest.fixture(scope="module")
+def data():
+    import torch
+    from paper_1607_06618_b300 import gerbil
+    gen = synth.genome(400_000, 7101)
+    seq, offs = synth.sampled_reads(gen, 30_000, 150, 0.005, 7102)
+    want = oracle.count(seq, offs, K, min_count=2)
+    s = torch.from_numpy(seq).cuda()
+    o = torch.from_numpy(offs.view(np.int64)).cuda()
+    ctx = gerbil.Context(0)
+    bins = ctx.partition(s, o, K, M, NBINS)
+    yield gerbil, ctx, bins, want
+    bins.free()
+    ctx.close()
+
+
+def _rows(ctx, bins, opts):
+    res = ctx.count_batch(bins, None, K, 2, opts)
+    got = res.to_host()
+    res.free()
+    return got
+
+
+def test_autotune_picks_valid_settings_and_counts_match(data):
+    gerbil, ctx, bins, want = data
+    assert ctx.get_tuning(K) is None
+    t = ctx.autotune(bins, K, 2)
+    assert t["fused"] in (0, 1, 2) and t["schedule"] in (0, 1)
+    assert all(a in (0.35, 0.5, 0.65, 0.8) for a in (round(x, 2) for x in t["load_factor"]))
+    assert t["k_words"] == 3 and t["samples"] >= 4 and t["ns_per_kmer"] > 0
+    assert ctx.get_tuning(K) == t and ctx.get_tuning(96) == t  # same key width (3 words)
+    assert ctx.get_tuning(64) is None  # 2 words
+    assert ctx.get_tuning(31) is None
+    assert_same_rows(_rows(ctx, bins, gerbil.default_opts(autotune=1)), want)
+
+
+@pytest.mark.parametrize("fused,schedule,alpha", [(0, 1, 0.8), (0, 0, 0.35), (1, 1, 0.65),
+                                                  (2, 1, 0.8)])
+def test_every_setting_of_the_search_space_counts_exactly(data, fused, schedule, alpha):
+    gerbil, ctx, bins, want = data
+    ctx.set_tuning(K, {"load_factor": [alpha] * gerbil.TUNE_CLASSES, "fused": fused,
+                       "schedule": schedule})
+    assert_same_rows(_rows(ctx, bins, gerbil.default_opts(autotune=1)), want)
+    ctx.set_tuning(K, None)
+    assert ctx.get_tuning(K) is None
+
+
+def test_tuned_on_first_use_and_rejects_bad_settings(data):
+    gerbil, ctx, bins, want = data
+    ctx.set_tuning(K, None)
+    assert_same_rows(_rows(ctx, bins, gerbil.default_opts(autotune=1)), want)
+    assert ctx.get_tuning(K) is not None  # tuned by the first call with autotune set
+    with pytest.raises(gerbil.GerbilError):
+        ctx.set_tuning(K, {"load_factor": [0.99] * 4, "fused": 0, "schedule": 1})
+    with pytest.raises(gerbil.GerbilError):
+        ctx.set_tuning(K, {"load_factor": [0.5] * 4, "fused": 3, "schedule": 1})
+
+
+def test_graph_form_counts_exactly_and_is_reused(data):
+    """Graph form: the captured batch gives the oracle's rows; the second batch of the same shape
+    updates the instantiated graph, a batch of another shape builds a new one."""
+    gerbil, ctx, bins, want = data
+    ctx.profile(True)
+    opts = gerbil.default_opts(graph=1)
+    for _ in range(3):
+        assert_same_rows(_rows(ctx, bins, opts), want)
+    t = ctx.phase_times()
+    assert t["graph_launches"] == 3 and t["insert_launches"] == 3
+    assert t["insert_ms"] > 0 and t["compact_ms"] > 0  # phase events recorded inside the graph
+    # a subset of the bins (another shape), then the full batch again
+    sub = list(range(0, NBINS, 3))
+    res = ctx.count_batch(bins, sub, K, 2, opts)
+    part = res.to_host()
+    res.free()
+    res = ctx.count_batch(bins, sub, K, 2, gerbil.default_opts())
+    assert_same_rows(part, res.to_host())
+    res.free()
+    assert_same_rows(_rows(ctx, bins, opts), want)
+    ctx.profile(False)
+
+
+def test_graph_form_with_overflow_and_retry(data):
+    """Graph form, then the overflow recount after it (theta = 1, small tables), and a retry
+    after the overflow area ran full (a new graph shape)."""
+    gerbil, ctx, bins, want = data
+    opts = gerbil.default_opts(graph=1, max_probes=1, distinct_ratio=0.05, overflow_slots=1 << 22)
+    res = ctx.count_batch(bins, None, K, 2, opts)
+    st = res.info()[2]
+    assert st["overflowed"] > 0 and st["retries"] == 0
+    assert_same_rows(res.to_host(), want)
+    res.free()
+    opts = gerbil.default_opts(graph=1, max_probes=1, distinct_ratio=0.01, overflow_slots=16)
+    res = ctx.count_batch(bins, None, K, 2, opts)
+    assert res.info()[2]["retries"] > 0
+    assert_same_rows(res.to_host(), want)
+    res.free()
