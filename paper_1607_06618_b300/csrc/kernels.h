@@ -43,7 +43,7 @@ cudaError_t launch_boundary(const uint64_t* offsets, uint64_t nreads, uint64_t n
                             unsigned int* err, cudaStream_t st);
 cudaError_t launch_supermer(const SupermerParams& p, cudaStream_t st);
 cudaError_t launch_scatter(const SupermerParams& p, unsigned long long nrec, int nsm, cudaStream_t st);
-size_t supermer_smem_bytes(int tile, int lmax, int k);
+size_t supermer_smem_bytes(int tile, int lmax, int k, int m);
 
 // ---- phase two ------------------------------------------------------------------------------
 // One entry per bin being counted.

@@ -128,21 +128,22 @@ __global__ void __launch_bounds__(256) supermer_kernel(SupermerParams P) {
   const long long wlo = (O >= 0) ? (O >> 5) : -1;  // first staged word
   const int nsw = (int)(((O + NB - 1) >> 5) - wlo) + 2;
 
-  // shared memory: staged words and masks | PRE | SUF (window minima later) | [KEY if w <= 8]
-  // | sparse table over segment minima | V | SB | BB
+  // shared memory: staged words and masks | PRE | SUF | [KEY if w <= 8] | sparse table over
+  // segment minima | SB | BB.  PRE and SUF are indexed through pidx(q) = q + q/32, so that the
+  // eight stores of a thread's segment (stride 8 across the warp) hit distinct banks.
   const int NSEG = (NQ + SEG - 1) / SEG;
+  const int NQP = NQ + (NQ >> 5) + 1;
   const int midmax = ((w - 1) / SEG) + 1;
   const int LEV = 32 - __clz(midmax);
   unsigned long long* sw = reinterpret_cast<unsigned long long*>(smem);
   uint32_t* snm = reinterpret_cast<uint32_t*>(sw + nsw);
   uint32_t* sbm = snm + nsw;
   uint32_t* PRE = sbm + nsw;
-  uint32_t* SUF = PRE + NQ;
-  uint32_t* KEY = SUF + NQ;
+  uint32_t* SUF = PRE + NQP;
+  uint32_t* KEY = SUF + NQP;
   uint32_t* ST = KEY + (w <= SEG ? NQ : 0);
-  uint8_t* V = reinterpret_cast<uint8_t*>(ST + LEV * NSEG);
   const int nbw = (NW + 31) >> 5;
-  uint32_t* SB = reinterpret_cast<uint32_t*>(V + ((NW + 15) & ~15));
+  uint32_t* SB = ST + LEV * NSEG;
   uint32_t* BB = SB + nbw;
 
   const long long nwords = (long long)P.nwords;
@@ -166,8 +167,7 @@ __global__ void __launch_bounds__(256) supermer_kernel(SupermerParams P) {
   const int q_lo = (O < 0) ? 1 : 0;
   const int q_hi = (int)min((long long)NQ, n - m - O + 1);
   const int p_hi = (int)min((long long)NW, nwin - O);
-  __shared__ uint32_t s_omod;
-  if (threadIdx.x == 0) s_omod = (uint32_t)(((O % lmax) + lmax) % lmax);
+  const uint32_t Omod = (uint32_t)(((O % lmax) + lmax) % lmax);
   for (int seg = threadIdx.x; seg < NSEG; seg += blockDim.x) {
     const int q0 = seg * SEG;
     const int lb = lbO + q0;
@@ -176,6 +176,7 @@ __global__ void __launch_bounds__(256) supermer_kernel(SupermerParams P) {
     const uint32_t nm32 = bits32(snm, lb), bm32 = bits32(sbm, lb);
     uint32_t key[SEG];
     uint32_t pre = 0xFFFFFFFFu;
+    const int pq0 = q0 + (q0 >> 5);  // pidx(q0); a segment never crosses a 32-boundary
 #pragma unroll
     for (int d = 0; d < SEG; ++d) {
       const int iq = q0 + d;
@@ -198,7 +199,7 @@ __global__ void __launch_bounds__(256) supermer_kernel(SupermerParams P) {
       key[d] = kk;
       pre = min(pre, kk);
       if (iq < NQ) {
-        PRE[iq] = pre;
+        PRE[pq0 + d] = pre;
         if (w <= SEG) KEY[iq] = kk;
       }
     }
@@ -206,7 +207,7 @@ __global__ void __launch_bounds__(256) supermer_kernel(SupermerParams P) {
 #pragma unroll
     for (int d = SEG - 1; d >= 0; --d) {
       suf = min(suf, key[d]);
-      if (q0 + d < NQ) SUF[q0 + d] = suf;
+      if (q0 + d < NQ) SUF[pq0 + d] = suf;
     }
     ST[seg] = pre;
   }
@@ -220,9 +221,9 @@ __global__ void __launch_bounds__(256) supermer_kernel(SupermerParams P) {
   }
   __syncthreads();
 
-  // window minima (0 = window not counted, else 1 + minimizer rank), written over SUF
-  uint32_t* M = SUF;
-  for (int i = threadIdx.x; i < NW; i += blockDim.x) {
+  // window minimum: 0 = a window with an undetermined base or a read start inside, else
+  // 1 + the minimizer's rank
+  auto wmin = [&](int i) -> uint32_t {
     const int a = i, bq = i + w - 1;
     uint32_t mk;
     if (w <= SEG) {
@@ -230,7 +231,7 @@ __global__ void __launch_bounds__(256) supermer_kernel(SupermerParams P) {
       for (int q = a; q <= bq; ++q) mk = min(mk, KEY[q]);
     } else {
       const int sa = a / SEG, sb = bq / SEG;
-      mk = min(SUF[a], PRE[bq]);
+      mk = min(SUF[a + (a >> 5)], PRE[bq + (bq >> 5)]);
       const int mid = sb - sa - 1;
       if (mid > 0) {
         const int l = 31 - __clz(mid);
@@ -238,51 +239,81 @@ __global__ void __launch_bounds__(256) supermer_kernel(SupermerParams P) {
         mk = min(mk, min(row[sa + 1], row[sb - (1 << l)]));
       }
     }
-    M[i] = mk;
+    return mk;
+  };
+  auto counted = [&](int i, uint32_t mk) -> bool {
     bool ok = i >= q_lo && i < p_hi && mk != 0u;
-    if (ok && m == 1) {  // m = 1: no m-mer straddles a read start, test the window itself
+    if (m == 1 && ok) {  // m = 1: no m-mer straddles a read start, test the window itself
       const int lb = lbO + i;
       for (int c = 1; ok && c < k; c += 32) {
         const int l = min(32, k - c);
         ok = (bits32(sbm, lb + c) >> (32 - l)) == 0u;
       }
     }
-    V[i] = ok;
-  }
-  __syncthreads();
+    return ok;
+  };
 
-  // super-mer starts and boundaries as bit masks (one ballot per 32 windows): window i starts
-  // a super-mer if it is counted and its predecessor is not, or has another minimizer, or i
-  // sits on a multiple of L_max; a boundary is a start or an uncounted window.
+  // window minima and super-mer starts / boundaries as bit masks, one ballot per 32 windows,
+  // each warp over a contiguous run of mask words (the predecessor of a lane's window is the
+  // previous lane's, or the last window of the warp's previous word): window i starts a
+  // super-mer if it is counted and its predecessor is not, or has another minimizer, or i sits
+  // on a multiple of L_max; a boundary is a start or an uncounted window.
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
   {
-    const uint32_t Omod = s_omod;  // written before the barriers above
     const uint32_t lm = (uint32_t)lmax;
     const bool pow2 = (lm & (lm - 1)) == 0;
-    for (int w0 = warp * 32; w0 < nbw * 32; w0 += nwarp * 32) {
-      const int i = w0 + lane;
+    const int per = (nbw + nwarp - 1) / nwarp;
+    const int wd0 = warp * per, wd1 = min(nbw, wd0 + per);
+    uint32_t cm = 0;  // minimum and counted-flag of the window before the current word
+    bool cv = false;
+    if (wd0 < wd1 && wd0 > 0) {
+      const int ip = wd0 * 32 - 1;
+      cm = wmin(ip);
+      cv = counted(ip, cm);
+    }
+    for (int wd = wd0; wd < wd1; ++wd) {
+      const int i = wd * 32 + lane;
+      const bool in = i < NW;
+      const uint32_t mk = in ? wmin(i) : 0u;
+      const bool v = in && counted(i, mk);
+      uint32_t pm = __shfl_up_sync(0xFFFFFFFFu, mk, 1);
+      bool pv = __shfl_up_sync(0xFFFFFFFFu, (int)v, 1) != 0;
+      if (lane == 0) {
+        pm = cm;
+        pv = cv;
+      }
       bool st = false, bd = true;
-      if (i >= 1 && i < NW) {
+      if (i >= 1 && in) {
         const uint32_t r = Omod + (uint32_t)i;
         const bool cut = pow2 ? ((r & (lm - 1)) == 0u) : (r % lm == 0u);
-        st = V[i] && (!V[i - 1] || M[i - 1] != M[i] || cut);
-        bd = !V[i] || st;
+        st = v && (!pv || pm != mk || cut);
+        bd = !v || st;
       }
       const uint32_t sb = __ballot_sync(0xFFFFFFFFu, st);
       const uint32_t bb = __ballot_sync(0xFFFFFFFFu, bd);
       if (lane == 0) {
-        SB[w0 >> 5] = sb;
-        BB[w0 >> 5] = bb;
+        SB[wd] = sb;
+        BB[wd] = bb;
       }
+      cm = __shfl_sync(0xFFFFFFFFu, mk, 31);
+      cv = __shfl_sync(0xFFFFFFFFu, (int)v, 31) != 0;
     }
   }
   __syncthreads();
 
-  // records: count the starts of every thread, take room for all of the CTA's records with one
-  // atomic, then write them (a thread's windows are 1 + tid + 256 r)
+  // records: the starts among this CTA's windows 1..own, counted per mask word; room for all of
+  // the CTA's records is taken with one atomic, then every start is written (its end = the first
+  // boundary after it; a cut every L_max windows bounds the search)
   const int own = (int)(P1 - P0);
+  const int ownw = (own >> 5) + 1;  // mask words holding windows 0..own
+  auto own_bits = [&](int wd) -> uint32_t {
+    uint32_t b = SB[wd];
+    if (wd == 0) b &= ~1u;                           // window 0 belongs to the previous CTA
+    if (wd == (own >> 5)) b &= (2u << (own & 31)) - 1u;  // windows up to own
+    return b;
+  };
   uint32_t mine = 0;
-  for (int i = 1 + threadIdx.x; i <= own; i += blockDim.x) mine += (SB[i >> 5] >> (i & 31)) & 1u;
+  for (int wd = threadIdx.x; wd < ownw; wd += blockDim.x) mine += __popc(own_bits(wd));
   __shared__ uint32_t s_wsum[8];
   __shared__ unsigned long long s_rbase;
   uint32_t incl = mine;
@@ -304,36 +335,39 @@ __global__ void __launch_bounds__(256) supermer_kernel(SupermerParams P) {
   }
   __syncthreads();
   unsigned long long idx = s_rbase + s_wsum[warp] + (incl - mine);
-  for (int i = 1 + threadIdx.x; i <= own; i += blockDim.x) {
-    if (!((SB[i >> 5] >> (i & 31)) & 1u)) continue;
-    // end = first boundary after i (a cut every L_max windows bounds the search)
-    const int j = i + 1;
-    int end = NW;
-    for (int wj = j >> 5; wj < nbw; ++wj) {
-      const uint32_t bits = BB[wj] & (wj == (j >> 5) ? (0xFFFFFFFFu << (j & 31)) : 0xFFFFFFFFu);
-      if (bits) {
-        end = min(NW, (wj << 5) + __ffs(bits) - 1);
-        break;
+  for (int wd = threadIdx.x; wd < ownw; wd += blockDim.x) {
+    uint32_t bits = own_bits(wd);
+    while (bits) {
+      const int i = wd * 32 + __ffs(bits) - 1;
+      bits &= bits - 1u;
+      const int j = i + 1;
+      int end = NW;
+      for (int wj = j >> 5; wj < nbw; ++wj) {
+        const uint32_t bb = BB[wj] & (wj == (j >> 5) ? (0xFFFFFFFFu << (j & 31)) : 0xFFFFFFFFu);
+        if (bb) {
+          end = min(NW, (wj << 5) + __ffs(bb) - 1);
+          break;
+        }
       }
-    }
-    const uint32_t nk = (uint32_t)(end - i);
-    const uint32_t h = fmix32((M[i] - 1u) & vmask);
-    uint32_t bin;
-    if (P.bounds) {
-      uint32_t lo = 0, hi = P.nbins - 1;  // number of split points <= h
-      while (lo < hi) {
-        const uint32_t mid = (lo + hi) >> 1;
-        if (__ldg(P.bounds + mid) <= h) lo = mid + 1; else hi = mid;
+      const uint32_t nk = (uint32_t)(end - i);
+      const uint32_t h = fmix32((wmin(i) - 1u) & vmask);
+      uint32_t bin;
+      if (P.bounds) {
+        uint32_t lo = 0, hi = P.nbins - 1;  // number of split points <= h
+        while (lo < hi) {
+          const uint32_t mid = (lo + hi) >> 1;
+          if (__ldg(P.bounds + mid) <= h) lo = mid + 1; else hi = mid;
+        }
+        bin = lo;
+      } else {
+        bin = h % P.nbins;
       }
-      bin = lo;
-    } else {
-      bin = h % P.nbins;
+      atomicAdd(P.bin_nsuper + bin, 1ull);
+      atomicAdd(P.bin_nkmers + bin, (unsigned long long)nk);
+      if (idx < P.rec_cap)
+        P.rec[idx] = make_ulonglong2((unsigned long long)(O + i), ((unsigned long long)bin << 32) | nk);
+      ++idx;
     }
-    atomicAdd(P.bin_nsuper + bin, 1ull);
-    atomicAdd(P.bin_nkmers + bin, (unsigned long long)nk);
-    if (idx < P.rec_cap)
-      P.rec[idx] = make_ulonglong2((unsigned long long)(O + i), ((unsigned long long)bin << 32) | nk);
-    ++idx;
   }
 }
 
@@ -391,15 +425,17 @@ __global__ void __launch_bounds__(256) scatter_kernel(SupermerParams P, unsigned
   }
 }
 
-size_t supermer_smem_bytes(int tile, int lmax, int k) {
+size_t supermer_smem_bytes(int tile, int lmax, int k, int m) {
   const long long NW = (long long)tile + 1 + lmax;
   const long long NQ = NW + k;  // upper bound (m >= 1)
   const long long NB = NW + k;
   const long long nsw = NB / 32 + 3;
+  const long long NQP = NQ + NQ / 32 + 1;
   const long long nseg = (NQ + SEG - 1) / SEG;
   const long long lev = 32 - __builtin_clz((unsigned)((k - 1) / SEG + 1));
   const long long nbw = (NW + 31) / 32;
-  return nsw * 16 + 3 * NQ * 4 + lev * nseg * 4 + ((NW + 15) & ~15LL) + 2 * nbw * 4 + 64;
+  const long long key = (k - m + 1 <= SEG) ? NQ : 0;  // KEY only when w <= SEG
+  return nsw * 16 + 2 * NQP * 4 + key * 4 + lev * nseg * 4 + 2 * nbw * 4 + 64;
 }
 
 cudaError_t launch_encode(const uint8_t* seq, uint64_t n, unsigned long long* packed,
@@ -430,7 +466,7 @@ static cudaError_t launch_supermer_m(const SupermerParams& p, uint64_t blocks, s
 cudaError_t launch_supermer(const SupermerParams& p, cudaStream_t st) {
   if (p.nwin == 0) return cudaSuccess;
   const uint64_t blocks = (p.nwin + p.tile - 1) / p.tile;
-  const size_t smem = supermer_smem_bytes(p.tile, p.lmax, p.k);
+  const size_t smem = supermer_smem_bytes(p.tile, p.lmax, p.k, p.m);
   switch (p.m) {
     case 1: return launch_supermer_m<1>(p, blocks, smem, st);
     case 2: return launch_supermer_m<2>(p, blocks, smem, st);
