@@ -46,8 +46,10 @@ def _args():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--per-bin-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-sample-reads", type=int, default=40000)
-    ap.add_argument("--ref-sample-reads", type=int, default=5000)
+    ap.add_argument("--cpu-sample-windows", type=int, default=3_500_000,
+                    help="k-mer windows of the oracle's timed sample (cpu_baseline)")
+    ap.add_argument("--ref-sample-windows", type=int, default=400_000,
+                    help="k-mer windows per step of --impl reference")
     ap.add_argument("--fused", type=int, default=None,
                     help="phase-two form: 0 all tables, 1 fused queue kernel, 2 waves")
     ap.add_argument("--schedule", type=int, default=None, help="1 device queue, 0 fixed striding")
@@ -158,9 +160,17 @@ def _model_bytes(occ, n_bases, distinct, emitted, W):
     return insert, step
 
 
-def run_cpu_oracle(seq, offs, p, nreads_sample):
+def _reads_for_windows(offs, k, target):
+    """Smallest n such that the first n reads hold at least ``target`` k-windows (N ignored)."""
+    lens = np.diff(offs.astype(np.int64))
+    cum = np.cumsum(np.maximum(lens - k + 1, 0))
+    return int(min(offs.size - 1, np.searchsorted(cum, target) + 1))
+
+
+def run_cpu_oracle(seq, offs, p, windows_sample):
+    """The oracle on the first reads holding about ``windows_sample`` k-mer windows."""
     import oracle
-    n = min(nreads_sample, offs.size - 1)
+    n = _reads_for_windows(offs, p["k"], windows_sample)
     s, o = seq[: int(offs[n])], offs[: n + 1]
     t0 = time.perf_counter()
     keys, counts = oracle.count(s, o, p["k"], canonical=True, min_count=p["min_count"])
@@ -184,10 +194,10 @@ def main_reference(a, world, rank):
     oracle.build()
     seq, offs, p = _host_workload(a.workload)
     for _ in range(a.warmup):
-        run_cpu_oracle(seq, offs, p, a.ref_sample_reads)
+        run_cpu_oracle(seq, offs, p, a.ref_sample_windows)
     times, occ = [], 0
     for _ in range(a.steps):
-        occ, dt, n = run_cpu_oracle(seq, offs, p, a.ref_sample_reads)
+        occ, dt, n = run_cpu_oracle(seq, offs, p, a.ref_sample_windows)
         times.append(dt)
     total = sum(times)
     value = occ * a.steps / total
@@ -395,7 +405,7 @@ def main_ours(a, world, rank, local):
 
     cpu = None
     if rank == 0 and not a.no_cpu_baseline:
-        occ_s, dt, n = run_cpu_oracle(seq, offs, p, a.cpu_sample_reads)
+        occ_s, dt, n = run_cpu_oracle(seq, offs, p, a.cpu_sample_windows)
         cpu = {"value": occ_s / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": "first %d of %d reads (%d k-mer windows), std::map oracle, %.1f s"
                          % (n, offs.size - 1, occ_s, dt)}
