@@ -368,6 +368,25 @@ def main_ours(a, world, rank, local):
                        "grid + compaction grid), one fused count_batch (queue + L2 table ring), "
                        "%d count calls" % (nbins, nbins)}
 
+    # App. C output records of one step's result, written on the device (event-timed)
+    appc = None
+    if rank == 0:
+        bins = ctx.partition(s_dev, o_dev, k, m, nbins, opts, bb)
+        res = ctx.count_batch(bins, None, k, mc, opts)
+        res.encode_records(k, device=True)  # warm-up
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        buf = res.encode_records(k, device=True)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ems = ev0.elapsed_time(ev1)
+        appc = {"rows": len(res), "bytes": int(buf.numel()), "ms": ems,
+                "what": "size pass + record pass (gerbil_encode_records, device output), "
+                        "including its host synchronisation"}
+        del buf
+        res.free()
+        bins.free()
+
     # end to end through the public API from pinned host buffers, result read back to host
     e2e = None
     if a.e2e_steps > 0:
@@ -424,6 +443,7 @@ def main_ours(a, world, rank, local):
                            "achieved_gbs": step_bytes / (p2_ms / 1000.0) / 1e9},
             "phase_ms": phase_ms, "cpu_baseline": cpu, "e2e": e2e, "clocks": ck,
             "gpu_launches": int(ph["kernel_launches"]), "batched_vs_per_bin": bvp,
+            "appc_records": appc,
             "opts": {key: val for key, val in kw.items()},
             "autotune": ctx.get_tuning(k) if a.autotune else None,
             "membench": membench,

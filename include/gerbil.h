@@ -189,6 +189,13 @@ const char* gerbil_last_error(const gerbil_ctx* ctx);
  * Errors: E_INVAL (bad device), E_CUDA. */
 int gerbil_create(gerbil_ctx** out, int device, uint64_t hbm_budget_bytes, void* cuda_stream);
 
+/* Forgets the distinct/occurrence ratio the context learned from earlier counts (Sec. 3.4
+ * adjusts it at run time within one input).  Call it before counting an unrelated input on the
+ * same context: a ratio learned on a highly repetitive input would size the next input's tables
+ * far too small (still exact, through overflow retries, but slow).  The next batch of more than
+ * 32 bins then samples every 16th bin first.  Errors: E_INVAL. */
+int gerbil_forget_ratio(gerbil_ctx* ctx);
+
 /* Destroys the context and releases its scratch memory (not the caller's stream). */
 void gerbil_destroy(gerbil_ctx* ctx);
 
@@ -267,6 +274,19 @@ int gerbil_counts_to_host(const gerbil_counts* counts, uint64_t* keys, uint32_t*
                           uint64_t cap);
 
 void gerbil_counts_free(gerbil_counts* counts);
+
+/* Output records of App. C ("Output Format") for every row of a result, in the result's row
+ * order: the count -- one byte when below 255, else the byte 0xFF followed by the count as a
+ * big-endian 32-bit integer -- then the k-mer with four bases per byte (A=00 C=01 G=10 T=11,
+ * first base in the two high bits of the first byte; the unused low bits of the last byte, which
+ * App. C leaves undefined, are written as 0).  k must be the k the result was counted with.
+ * *nbytes receives the size of all records.  out == NULL only computes the size; otherwise out
+ * (cap bytes, device memory when out_on_device != 0, else host memory) receives the records.
+ * The work runs on the stream of the context that owns the result and synchronizes it; scratch
+ * comes from that context.  Errors: E_INVAL (k of another key width, cap too small -- *nbytes
+ * is still set), E_NOMEM, E_CUDA. */
+int gerbil_encode_records(const gerbil_counts* counts, int k, void* out, uint64_t cap,
+                          int out_on_device, uint64_t* nbytes);
 
 /* ---- serving: counting jobs admitted continuously under an HBM budget ----------------------
  * The paper has no counterpart (it counts one input at a time).  A server keeps `slots` worker

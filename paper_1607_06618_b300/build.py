@@ -7,7 +7,7 @@ import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
-SOURCES = ["partition.cu", "count.cu", "runtime.cu", "membench.cu", "server.cu"]
+SOURCES = ["partition.cu", "count.cu", "runtime.cu", "membench.cu", "server.cu", "encode.cu"]
 HEADERS = ["common.cuh", "kernels.h"]
 LIB = os.path.join(HERE, "libgerbil.so")
 ROOT = os.path.dirname(HERE)

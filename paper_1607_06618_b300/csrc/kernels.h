@@ -148,4 +148,21 @@ cudaError_t launch_compact(int k, const CompactParams& p, int nsm, cudaStream_t 
 cudaError_t launch_overflow_insert(int k, const OverflowParams& p, int nsm, cudaStream_t st);
 cudaError_t launch_overflow_emit(int k, const OverflowParams& p, int nsm, cudaStream_t st);
 
+// ---- App. C output records (encode.cu) ----
+struct EncodeParams {
+  const unsigned long long* keys;  // [n][W]
+  const uint32_t* counts;          // [n]
+  unsigned long long n;
+  int k;
+  const unsigned long long* tile_long;  // exclusive prefix of long-count rows per tile
+  uint8_t* out;
+  unsigned long long base;  // byte offset of row 0's record in out
+};
+cudaError_t launch_encode_count(const uint32_t* counts, unsigned long long n,
+                                unsigned long long* tile_long, cudaStream_t st);
+cudaError_t launch_encode_scan(unsigned long long* tile_long, unsigned long long ntiles,
+                               unsigned long long* total, cudaStream_t st);
+cudaError_t launch_encode_write(const EncodeParams& p, cudaStream_t st);
+unsigned long long encode_tiles(unsigned long long n);
+
 }  // namespace gerbil

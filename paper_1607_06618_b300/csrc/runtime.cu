@@ -303,8 +303,10 @@ int gerbil_internal_alloc(gerbil_ctx* ctx, void** p, size_t bytes, void** stream
 
 void gerbil_internal_free(gerbil_ctx* ctx, void* p, size_t bytes) { dev_free(ctx, p, bytes); }
 
-void gerbil_internal_forget_ratio(gerbil_ctx* ctx) {
-  if (ctx) ctx->ratio_known = false;
+int gerbil_forget_ratio(gerbil_ctx* ctx) {
+  if (!ctx) return GERBIL_E_INVAL;
+  ctx->ratio_known = false;
+  return GERBIL_OK;
 }
 
 int gerbil_trim(gerbil_ctx* ctx) {
@@ -1694,6 +1696,106 @@ int gerbil_count_batch(gerbil_ctx* ctx, const gerbil_bins* b, const int32_t* bin
   }
   CK(cudaSetDevice(ctx->device));
   return count_impl(ctx, b, list, k, min_count, opts, out);
+}
+
+// App. C records: per part (a joined result has several), count the long-count rows per tile,
+// scan, read the total; then write every part at its byte offset.
+int gerbil_encode_records(const gerbil_counts* c, int k, void* out, uint64_t cap, int out_on_device,
+                          uint64_t* nbytes) {
+  if (!c || !nbytes) return GERBIL_E_INVAL;
+  *nbytes = 0;
+  gerbil_ctx* ctx = c->ctx;
+  if (k < GERBIL_MIN_K || k > GERBIL_MAX_K || words_for(k) != c->W)
+    return fail(ctx, GERBIL_E_INVAL, "k does not match the result's key width");
+  CK(cudaSetDevice(ctx->device));
+  cudaStream_t st = ctx->stream;
+  struct Part { const unsigned long long* keys; const uint32_t* counts; uint64_t n; };
+  std::vector<Part> parts;
+  if (!c->parts.empty()) {
+    for (const gerbil_counts* p : c->parts) parts.push_back({p->keys, p->counts, p->n});
+  } else {
+    parts.push_back({c->keys, c->counts, c->n});
+  }
+  const uint64_t KB = (uint64_t)(k + 3) / 4;
+  uint64_t maxt = 1;
+  for (const Part& p : parts) maxt = std::max<uint64_t>(maxt, gerbil::encode_tiles(p.n));
+  const size_t tbytes = (maxt + 1) * 8 * parts.size();
+  unsigned long long* tl = nullptr;
+  int rc;
+  if ((rc = dev_alloc(ctx, (void**)&tl, tbytes))) return rc;
+  std::vector<uint64_t> part_bytes(parts.size(), 0);
+  std::vector<unsigned long long> totals(parts.size(), 0);
+  uint64_t all = 0;
+  auto cleanup = [&]() { dev_free(ctx, tl, tbytes); };
+#define CKE(call)                                                                          \
+  do {                                                                                     \
+    cudaError_t e_ = (call);                                                               \
+    if (e_ != cudaSuccess) {                                                               \
+      cleanup();                                                                           \
+      return fail(ctx, GERBIL_E_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    }                                                                                      \
+  } while (0)
+  for (size_t i = 0; i < parts.size(); ++i) {
+    if (!parts[i].n) continue;
+    unsigned long long* t = tl + i * (maxt + 1);
+    const uint64_t nt = gerbil::encode_tiles(parts[i].n);
+    CKE(gerbil::launch_encode_count(parts[i].counts, parts[i].n, t, st));
+    CKE(gerbil::launch_encode_scan(t, nt, t + maxt, st));
+    ctx->times.kernel_launches += 2;
+  }
+  for (size_t i = 0; i < parts.size(); ++i)
+    if (parts[i].n) CKE(cudaMemcpyAsync(&totals[i], tl + i * (maxt + 1) + maxt, 8, cudaMemcpyDeviceToHost, st));
+  CKE(cudaStreamSynchronize(st));
+  for (size_t i = 0; i < parts.size(); ++i) {
+    part_bytes[i] = parts[i].n * (KB + 1) + 4 * totals[i];
+    all += part_bytes[i];
+  }
+  *nbytes = all;
+  if (!out) {
+    cleanup();
+    return GERBIL_OK;
+  }
+  if (cap < all) {
+    cleanup();
+    return fail(ctx, GERBIL_E_INVAL, "output buffer smaller than the records");
+  }
+  uint8_t* dst = (uint8_t*)out;
+  uint8_t* stage = nullptr;
+  if (!out_on_device && all) {
+    if ((rc = dev_alloc(ctx, (void**)&stage, all))) {
+      cleanup();
+      return rc;
+    }
+    dst = stage;
+  }
+  uint64_t base = 0;
+  for (size_t i = 0; i < parts.size(); ++i) {
+    if (parts[i].n) {
+      gerbil::EncodeParams ep{};
+      ep.keys = parts[i].keys;
+      ep.counts = parts[i].counts;
+      ep.n = parts[i].n;
+      ep.k = k;
+      ep.tile_long = tl + i * (maxt + 1);
+      ep.out = dst;
+      ep.base = base;
+      cudaError_t e = gerbil::launch_encode_write(ep, st);
+      if (e != cudaSuccess) {
+        dev_free(ctx, stage, all);
+        CKE(e);
+      }
+      ctx->times.kernel_launches++;
+    }
+    base += part_bytes[i];
+  }
+  cudaError_t e = cudaSuccess;
+  if (stage) e = cudaMemcpyAsync(out, stage, all, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  dev_free(ctx, stage, all);
+  CKE(e);
+#undef CKE
+  cleanup();
+  return GERBIL_OK;
 }
 
 int gerbil_counts_info(const gerbil_counts* c, uint64_t* n, int* words, gerbil_count_stats* s) {

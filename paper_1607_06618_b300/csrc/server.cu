@@ -70,8 +70,6 @@ struct gerbil_server {
   std::vector<uint64_t> launches_per_worker;  // kernel launches of each worker's context
 };
 
-// runtime.cu: forget the distinct ratio a context learned, so the next job learns its own.
-extern "C" void gerbil_internal_forget_ratio(gerbil_ctx* ctx);
 
 namespace {
 
@@ -126,7 +124,7 @@ void run_job(gerbil_server* s, int w, Job* j) {
   gerbil_opts o = j->opts;
   if (!j->bounds.empty()) o.bin_bounds = j->bounds.data();
   if (!o.max_table_mib && s->table_cap) o.max_table_mib = (uint32_t)std::max<uint64_t>(1, s->table_cap >> 20);
-  gerbil_internal_forget_ratio(ctx);  // each job learns its own distinct ratio (Sec. 3.4)
+  gerbil_forget_ratio(ctx);  // each job learns its own distinct ratio (Sec. 3.4)
   gerbil_bins* bins = nullptr;
   gerbil_counts* res = nullptr;
   int rc = gerbil_partition(ctx, &r, j->k, j->m, j->nbins, &o, &bins);

@@ -39,7 +39,8 @@ ABI_SYMBOLS = (
     "gerbil_profile", "gerbil_get_phase_times", "gerbil_count_small_noalloc", "gerbil_membench",
     "gerbil_trim", "gerbil_device_bytes", "gerbil_server_create", "gerbil_server_submit",
     "gerbil_server_wait", "gerbil_server_get_stats", "gerbil_server_destroy",
-    "gerbil_autotune", "gerbil_set_tuning", "gerbil_get_tuning",
+    "gerbil_autotune", "gerbil_set_tuning", "gerbil_get_tuning", "gerbil_encode_records",
+    "gerbil_forget_ratio",
 )
 
 
@@ -175,6 +176,8 @@ def load() -> ctypes.CDLL:
         "gerbil_counts_free": (None, [P]),
         "gerbil_profile": (I32, [P, I32]),
         "gerbil_trim": (I32, [P]),
+        "gerbil_forget_ratio": (I32, [P]),
+        "gerbil_encode_records": (I32, [P, I32, P, U64, I32, ctypes.POINTER(U64)]),
         "gerbil_autotune": (I32, [P, P, I32, U32, ctypes.POINTER(gerbil_opts),
                                   ctypes.POINTER(gerbil_tuning)]),
         "gerbil_set_tuning": (I32, [P, I32, ctypes.POINTER(gerbil_tuning)]),
@@ -392,6 +395,13 @@ def gerbil_get_tuning(ctx, k: int) -> dict | None:
     return t.as_dict()
 
 
+def gerbil_encode_records(counts, k: int, out=None, cap: int = 0, out_on_device: int = 0) -> int:
+    """App. C records of a result into ``out`` (a pointer), or only their size when out is None."""
+    nb = ctypes.c_uint64()
+    _check(load().gerbil_encode_records(counts, k, out, cap, out_on_device, ctypes.byref(nb)))
+    return nb.value
+
+
 def gerbil_trim(ctx):
     _check(load().gerbil_trim(ctx), ctx)
 
@@ -462,6 +472,19 @@ class Counts:
 
     def to_host(self):
         return gerbil_counts_to_host(self.handle)
+
+    def encode_records(self, k: int, device: bool = False):
+        """App. C output records of every row: a numpy uint8 array, or a torch uint8 CUDA
+        tensor with device=True."""
+        n = gerbil_encode_records(self.handle, k)
+        if device:
+            import torch
+            buf = torch.empty(max(1, n), dtype=torch.uint8, device=torch.device("cuda", self.ctx.device))
+            gerbil_encode_records(self.handle, k, buf.data_ptr(), n, 1)
+            return buf[:n]
+        buf = np.empty(max(1, n), dtype=np.uint8)
+        gerbil_encode_records(self.handle, k, buf.ctypes.data, n, 0)
+        return buf[:n]
 
     def torch_views(self):
         """(keys int64[n, W], counts int32[n]) torch views of the device result (no copy)."""
@@ -590,6 +613,9 @@ class Context:
 
     def count(self, bins: Bins, b: int, k: int, min_count: int, opts=None) -> Counts:
         return Counts(gerbil_count(self.handle, bins.handle, b, k, min_count, opts), self)
+
+    def forget_ratio(self):
+        _check(load().gerbil_forget_ratio(self.handle), self.handle)
 
     def autotune(self, bins: Bins, k: int, min_count: int, opts=None) -> dict:
         return gerbil_autotune(self.handle, bins.handle, k, min_count, opts)
