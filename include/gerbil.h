@@ -38,8 +38,8 @@ extern "C" {
 #endif
 
 #define GERBIL_ABI_VERSION 1
-/* Largest supported k: W = 8 words (the paper supports k up to 479, App. A flag -k). */
-#define GERBIL_MAX_K 256
+/* Supported k, as in the paper (App. A flag -k: 8 to 479); keys of up to W = 15 words. */
+#define GERBIL_MAX_K 479
 #define GERBIL_MIN_K 8
 
 typedef enum gerbil_status {

@@ -30,16 +30,32 @@ def _stale() -> bool:
 
 
 def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) -> str:
+    """Compiles every source to an object in parallel, then links the shared library."""
     if not (force or _stale()):
         return LIB
+    from concurrent.futures import ThreadPoolExecutor
     nvcc = os.environ.get("NVCC", "nvcc")
-    tmp = LIB + ".tmp%d" % os.getpid()
-    cmd = [nvcc] + NVCC_FLAGS + (["-Xptxas", "-v"] if ptxas_info else [])
-    cmd += [os.path.join(CSRC, f) for f in SOURCES] + ["-o", tmp]
-    if verbose:
-        print(" ".join(cmd), file=sys.stderr)
-    subprocess.check_call(cmd)
-    os.replace(tmp, LIB)
+    tag = "tmp%d" % os.getpid()
+    flags = [f for f in NVCC_FLAGS if f != "-shared"] + (["-Xptxas", "-v"] if ptxas_info else [])
+    objs = [os.path.join(HERE, "_obj_%s_%s.o" % (os.path.splitext(f)[0], tag)) for f in SOURCES]
+    cmds = [[nvcc] + flags + ["-c", os.path.join(CSRC, f), "-o", o] for f, o in zip(SOURCES, objs)]
+    tmp = LIB + "." + tag
+    try:
+        with ThreadPoolExecutor(max_workers=min(len(cmds), os.cpu_count() or 1)) as ex:
+            for cmd, rc in zip(cmds, ex.map(subprocess.call, cmds)):
+                if verbose:
+                    print(" ".join(cmd), file=sys.stderr)
+                if rc != 0:
+                    raise subprocess.CalledProcessError(rc, cmd)
+        link = [nvcc, "-shared", "-gencode", "arch=compute_103a,code=sm_103a"] + objs + ["-o", tmp]
+        if verbose:
+            print(" ".join(link), file=sys.stderr)
+        subprocess.check_call(link)
+        os.replace(tmp, LIB)
+    finally:
+        for o in objs + [tmp]:
+            if os.path.exists(o):
+                os.remove(o)
     return LIB
 
 

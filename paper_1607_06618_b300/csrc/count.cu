@@ -785,23 +785,37 @@ __global__ void __launch_bounds__(256) overflow_emit_kernel(OverflowParams P) {
 // ---- launchers: dispatch on (W, WS) ------------------------------------------------------------
 // W = ceil(2k/64) key words; WS = ceil(2k/63) stored words, W or W+1.
 #define GERBIL_KEY_SWITCH(W, WS, CALL)                 \
-  switch (W * 16 + WS) {                               \
-    case 1 * 16 + 1: CALL(1, 1); break;                \
-    case 1 * 16 + 2: CALL(1, 2); break;                \
-    case 2 * 16 + 2: CALL(2, 2); break;                \
-    case 2 * 16 + 3: CALL(2, 3); break;                \
-    case 3 * 16 + 3: CALL(3, 3); break;                \
-    case 3 * 16 + 4: CALL(3, 4); break;                \
-    case 4 * 16 + 4: CALL(4, 4); break;                \
-    case 4 * 16 + 5: CALL(4, 5); break;                \
-    case 5 * 16 + 5: CALL(5, 5); break;                \
-    case 5 * 16 + 6: CALL(5, 6); break;                \
-    case 6 * 16 + 6: CALL(6, 6); break;                \
-    case 6 * 16 + 7: CALL(6, 7); break;                \
-    case 7 * 16 + 7: CALL(7, 7); break;                \
-    case 7 * 16 + 8: CALL(7, 8); break;                \
-    case 8 * 16 + 8: CALL(8, 8); break;                \
-    case 8 * 16 + 9: CALL(8, 9); break;                \
+  switch (W * 32 + WS) {                               \
+    case 1 * 32 + 1: CALL(1, 1); break;                \
+    case 1 * 32 + 2: CALL(1, 2); break;                \
+    case 2 * 32 + 2: CALL(2, 2); break;                \
+    case 2 * 32 + 3: CALL(2, 3); break;                \
+    case 3 * 32 + 3: CALL(3, 3); break;                \
+    case 3 * 32 + 4: CALL(3, 4); break;                \
+    case 4 * 32 + 4: CALL(4, 4); break;                \
+    case 4 * 32 + 5: CALL(4, 5); break;                \
+    case 5 * 32 + 5: CALL(5, 5); break;                \
+    case 5 * 32 + 6: CALL(5, 6); break;                \
+    case 6 * 32 + 6: CALL(6, 6); break;                \
+    case 6 * 32 + 7: CALL(6, 7); break;                \
+    case 7 * 32 + 7: CALL(7, 7); break;                \
+    case 7 * 32 + 8: CALL(7, 8); break;                \
+    case 8 * 32 + 8: CALL(8, 8); break;                \
+    case 8 * 32 + 9: CALL(8, 9); break;                \
+    case 9 * 32 + 9: CALL(9, 9); break;                \
+    case 9 * 32 + 10: CALL(9, 10); break;              \
+    case 10 * 32 + 10: CALL(10, 10); break;            \
+    case 10 * 32 + 11: CALL(10, 11); break;            \
+    case 11 * 32 + 11: CALL(11, 11); break;            \
+    case 11 * 32 + 12: CALL(11, 12); break;            \
+    case 12 * 32 + 12: CALL(12, 12); break;            \
+    case 12 * 32 + 13: CALL(12, 13); break;            \
+    case 13 * 32 + 13: CALL(13, 13); break;            \
+    case 13 * 32 + 14: CALL(13, 14); break;            \
+    case 14 * 32 + 14: CALL(14, 14); break;            \
+    case 14 * 32 + 15: CALL(14, 15); break;            \
+    case 15 * 32 + 15: CALL(15, 15); break;            \
+    case 15 * 32 + 16: CALL(15, 16); break;            \
     default: return cudaErrorInvalidValue;             \
   }
 

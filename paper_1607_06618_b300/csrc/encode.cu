@@ -165,6 +165,7 @@ cudaError_t launch_encode_write(const EncodeParams& p, cudaStream_t st) {
   switch (W) {
 #define L_ENC(w) case w: encode_write_kernel<w><<<(unsigned)tiles, ENC_THREADS, 0, st>>>(p); break;
     L_ENC(1) L_ENC(2) L_ENC(3) L_ENC(4) L_ENC(5) L_ENC(6) L_ENC(7) L_ENC(8)
+    L_ENC(9) L_ENC(10) L_ENC(11) L_ENC(12) L_ENC(13) L_ENC(14) L_ENC(15)
 #undef L_ENC
     default: return cudaErrorInvalidValue;
   }

@@ -120,7 +120,8 @@ def test_partition_edge_reads(g):
 
 # ---- phase two -------------------------------------------------------------------------
 
-@pytest.mark.parametrize("k", [8, 31, 32, 33, 63, 64, 65, 99, 127, 128, 129, 200, 256])
+# the first and last k of every (key words, stored chunks) pair from k = 8 to the paper's 479
+@pytest.mark.parametrize("k", [8, 31, 32, 33, 63, 64, 65, 94, 95, 96, 97, 99, 126, 127, 128, 129, 157, 158, 160, 161, 189, 190, 192, 193, 200, 220, 221, 224, 225, 252, 253, 256, 257, 283, 284, 288, 289, 300, 315, 316, 320, 321, 346, 347, 352, 353, 378, 379, 384, 385, 409, 410, 416, 417, 441, 442, 448, 449, 472, 473, 479])
 def test_count_matches_oracle_all_word_counts(g, k):
     m = min(11, k - 1)
     seq, offs = synth.random_small(400, max(1, k - 4), k + 300, p_n=0.003, seed=1000 + k,

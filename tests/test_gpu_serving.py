@@ -86,3 +86,46 @@ def test_batch_counted_in_groups_under_table_limit():
     bins.free()
     ctx.close()
     assert_same_rows(want, oracle.count(s.cpu().numpy(), o.cpu().numpy().view(np.uint64), k, min_count=1))
+
+
+def _digest(res):
+    """Order-independent digest of a device result (torch, on the GPU): sum of a mix of every
+    row's key words and count, and the row count."""
+    import torch
+    keys, cnts = res.torch_views()
+    h = torch.zeros(keys.shape[0], dtype=torch.int64, device=keys.device)
+    for j in range(keys.shape[1]):
+        h = (h ^ keys[:, j]) * -7046029254386353131  # 0x9E3779B97F4A7C15 as int64
+        h = h ^ (h >> 29)
+    h = (h ^ cnts.to(torch.int64)) * -4658895280553007687  # 0xBF58476D1CE4E5B9
+    return int(h.sum().item()), int(keys.shape[0])
+
+
+def test_serving_stream_jobs_equal_alone_at_reduced_scale():
+    """The first jobs of the Poisson serving stream (genome and reads scaled by 1/50), submitted
+    at once to a server whose budget admits a few at a time: each job's rows in the mix have the
+    digest of the same job run alone (SURVEY config 5 parity, tolerance 0)."""
+    import torch
+    from paper_1607_06618_b300 import gerbil
+    jobs = synth.serving_jobs(10)
+    reads = [synth.t_serving_reads(j, "cuda", scale=0.02) for j in jobs]
+    torch.cuda.synchronize()
+    server = gerbil.Server(0, hbm_budget_bytes=int(6e9), slots=4)
+    ids = [server.submit(s, o, j["k"], j["m"], j["nbins"], j["min_count"]) for j, (s, o) in zip(jobs, reads)]
+    mixed = []
+    for jid in ids:
+        res, _ = server.wait(jid)
+        mixed.append(_digest(res))
+        res.free()
+    st = server.stats()
+    server.close()
+    assert st["completed"] == len(jobs) and st["max_concurrent"] >= 2
+    ctx = gerbil.Context(0)
+    for j, (s, o), want in zip(jobs, reads, mixed):
+        ctx.forget_ratio()
+        bins = ctx.partition(s, o, j["k"], j["m"], j["nbins"])
+        res = ctx.count_batch(bins, None, j["k"], j["min_count"])
+        assert _digest(res) == want
+        res.free()
+        bins.free()
+    ctx.close()

@@ -120,7 +120,7 @@ def test_bin_map_reading():
 
 # ---- brute force on tiny inputs -------------------------------------------------------
 
-KS = [3, 4, 5, 8, 15, 16, 17, 31, 32, 33, 63, 64, 65, 127, 128, 129, 200]
+KS = [3, 4, 5, 8, 15, 16, 17, 31, 32, 33, 63, 64, 65, 127, 128, 129, 200, 300, 479]
 
 
 @pytest.mark.parametrize("k", KS)
