@@ -370,6 +370,30 @@ def main_ours(a, world, rank, local):
                        "grid + compaction grid), one fused count_batch (queue + L2 table ring), "
                        "%d count calls" % (nbins, nbins)}
 
+    # probe statistics of one step's phase two (Sec. 3.3 compares one-by-one with 128-byte
+    # window probing): share placed at the first slot read / within the first line, and the
+    # most slots / lines any k-mer needed; recorded outside the timed region
+    probes = None
+    if rank == 0:
+        bins = ctx.partition(s_dev, o_dev, k, m, nbins, opts, bb)
+        ctx.probe_stats(True)
+        ctx.count_batch(bins, None, k, mc, opts).free()
+        hs_, hl_ = ctx.get_probe_stats()
+        ctx.probe_stats(False)
+        bins.free()
+        tot = float(hs_.sum())
+
+        def _maxb(h):
+            nz = [i for i in range(33) if h[i]]
+            return (nz[-1] + 1) if nz else 0
+
+        probes = {"first_slot_share": float(hs_[0]) / tot, "first_line_share": float(hl_[0]) / tot,
+                  "max_slots": _maxb(hs_), "max_lines": _maxb(hl_),
+                  "mean_slots": float(sum((i + 1) * int(hs_[i]) for i in range(33))) / tot,
+                  "overflowed": int(hs_[33]),
+                  "what": "per inserted k-mer: slots read until placed (linear probing, one slot "
+                          "per read) and distinct 128-byte lines among them"}
+
     # App. C output records of one step's result, written on the device (event-timed)
     appc = None
     if rank == 0:
@@ -481,7 +505,7 @@ def main_ours(a, world, rank, local):
                            "achieved_gbs": step_bytes / (p2_ms / 1000.0) / 1e9},
             "phase_ms": phase_ms, "cpu_baseline": cpu, "e2e": e2e, "clocks": ck,
             "gpu_launches": int(ph["kernel_launches"]), "batched_vs_per_bin": bvp,
-            "appc_records": appc,
+            "appc_records": appc, "probe_stats": probes,
             "opts": {key: val for key, val in kw.items()},
             "autotune": ctx.get_tuning(k) if a.autotune else None,
             "membench": membench,

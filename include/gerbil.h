@@ -196,6 +196,24 @@ int gerbil_create(gerbil_ctx** out, int device, uint64_t hbm_budget_bytes, void*
  * 32 bins then samples every 16th bin first.  Errors: E_INVAL. */
 int gerbil_forget_ratio(gerbil_ctx* ctx);
 
+/* Probe statistics (Sec. 3.3 reports, for one-by-one and for 128-byte-window probing, the share
+ * of k-mers placed at the first probe and the largest number of probes any k-mer needed).
+ * enable != 0 clears and starts the histograms: every later insert of this context's counts
+ * (two-grid and waves forms; fused 1 does not record) records, once placed, the number of
+ * slots it read and the number of distinct
+ * 128-byte lines those slots lie in (this build probes linearly, one slot per read, so
+ * consecutive probes share lines).  While on, counts run a separate build of the insert kernel
+ * that adds two global atomics per k-mer; the normal build carries no recording code.
+ * enable == 0 stops and frees.  Errors: E_INVAL, E_CUDA. */
+#define GERBIL_PROBE_BUCKETS 34
+int gerbil_probe_stats(gerbil_ctx* ctx, int enable);
+
+/* Reads the histograms (GERBIL_PROBE_BUCKETS entries each): entry i < 32 counts k-mers placed
+ * after reading i+1 slots (slots[]) or touching i+1 lines (lines[]), entry 32 more than 32,
+ * entry 33 k-mers sent to the overflow area (theta probes without room).  Synchronizes the
+ * context's stream.  Errors: E_INVAL, E_STATE (statistics off), E_CUDA. */
+int gerbil_get_probe_stats(const gerbil_ctx* ctx, uint64_t* slots, uint64_t* lines);
+
 /* Destroys the context and releases its scratch memory (not the caller's stream). */
 void gerbil_destroy(gerbil_ctx* ctx);
 

@@ -129,6 +129,28 @@ __device__ __forceinline__ void to_overflow(const CountParams& P, uint32_t widx,
   atomicAdd(P.bin_ovf + widx, 1u);
 }
 
+// Probe statistics of one placed k-mer: t = slots stepped over before the one it was placed in
+// (first slot s - t, cyclic), why = 0 placed, else sent to the overflow area.  The lines count
+// is the number of distinct 128-byte lines among the slots read (the unit of the paper's
+// windowed probing, Sec. 3.3).
+template <int SW>
+__device__ __noinline__ void record_probe(const CountParams& P, const BinWork& wk, uint32_t s,
+                                          uint32_t t, int why) {
+  int b0, b1;
+  if (why) {
+    b0 = b1 = PROBE_BUCKETS - 1;
+  } else {
+    const unsigned long long s0 = (s >= t) ? s - t : s + wk.cap - t;
+    const unsigned long long first = (wk.table_off + s0) * SW * 8 / 128;
+    const unsigned long long last = (wk.table_off + s0 + t) * SW * 8 / 128;
+    const unsigned long long lines = last - first + 1;
+    b0 = (int)(t + 1 < 33 ? t + 1 : 33) - 1;
+    b1 = (int)(lines < 33 ? lines : 33ull) - 1;
+  }
+  atomicAdd(P.probe_hist + b0, 1ull);
+  atomicAdd(P.probe_hist + PROBE_BUCKETS + b1, 1ull);
+}
+
 // ---- warp work items: extract, canonicalise, insert --------------------------------------------
 // The k-mers of a bin are cut into items of ITEM_KMERS consecutive k-mers (bin order).  Item i
 // is done by one warp; imap[i] = (work index << 32 | first super-mer of the item), built by
@@ -164,7 +186,7 @@ struct WarpSmem {
 // super-mer are cut from the packed words in full.
 constexpr int KPL = ITEM_KMERS / 32;
 
-template <int W, int WS>
+template <int W, int WS, bool STATS = false>
 __device__ __forceinline__ void insert_item(const CountParams& P, uint32_t wi, const BinWork& wk,
                                             uint32_t it, uint32_t s_lo, WarpSmem& S, int lane) {
   const uint32_t j0 = it * ITEM_KMERS;
@@ -266,6 +288,7 @@ __device__ __forceinline__ void insert_item(const CountParams& P, uint32_t wi, c
           else st_relaxed(slot + 1 + u, st[u]);
         }
         busy = false;
+        if constexpr (STATS) record_probe<SW>(P, wk, s, t, 0);
       }
       continue;  // claimed by another lane meanwhile: look at the same slot again
     }
@@ -286,6 +309,7 @@ __device__ __forceinline__ void insert_item(const CountParams& P, uint32_t wi, c
       } else if (eq) {
         red_add(slot, 1ull);
         busy = false;
+        if constexpr (STATS) record_probe<SW>(P, wk, s, t, 0);
         continue;
       }
     }
@@ -297,6 +321,7 @@ __device__ __forceinline__ void insert_item(const CountParams& P, uint32_t wi, c
     unsigned long long key[W];
     from_stored<W, WS>(st, key);
     to_overflow<W>(P, wi, key, why);
+    if constexpr (STATS) record_probe<SW>(P, wk, s, t, why);
     busy = false;
   }
 #else
@@ -346,12 +371,12 @@ __device__ __forceinline__ void insert_item(const CountParams& P, uint32_t wi, c
   __syncwarp();  // S is reused by the next item
 }
 
-template <int W, int WS>
+template <int W, int WS, bool STATS>
 __device__ __forceinline__ void count_item(const CountParams& P, unsigned long long item,
                                            unsigned long long entry, WarpSmem& S, int lane) {
   const uint32_t wi = (uint32_t)(entry >> 32), s_lo = (uint32_t)entry;
   const BinWork wk = P.work[wi];
-  insert_item<W, WS>(P, wi, wk, (uint32_t)(item - wk.item_begin), s_lo, S, lane);
+  insert_item<W, WS, STATS>(P, wi, wk, (uint32_t)(item - wk.item_begin), s_lo, S, lane);
 }
 
 // Warps take items in bin order from a device counter (the next one is requested while the
@@ -373,7 +398,8 @@ constexpr int insert_min_blocks(int W) {
   return W <= 3 ? GERBIL_MINB_SMALL : (W <= 5 ? GERBIL_MINB_MID : GERBIL_MINB_LARGE);
 }
 
-template <int W, int WS>
+// STATS: the instantiation that records probe statistics (only launched while they are on).
+template <int W, int WS, bool STATS>
 __global__ void __launch_bounds__(256, insert_min_blocks(W)) insert_kernel(CountParams P) {
   __shared__ WarpSmem S[8];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -381,7 +407,7 @@ __global__ void __launch_bounds__(256, insert_min_blocks(W)) insert_kernel(Count
     const unsigned long long nw = (unsigned long long)gridDim.x * (blockDim.x >> 5);
     for (unsigned long long item = P.item_base + blockIdx.x * (unsigned long long)(blockDim.x >> 5) + warp;
          item < P.nitems; item += nw)
-      count_item<W, WS>(P, item, __ldg(P.imap + item), S[warp], lane);
+      count_item<W, WS, STATS>(P, item, __ldg(P.imap + item), S[warp], lane);
     return;
   }
   unsigned long long* queue = P.queue;
@@ -392,7 +418,7 @@ __global__ void __launch_bounds__(256, insert_min_blocks(W)) insert_kernel(Count
     unsigned long long next = 0;
     if (lane == 0) next = P.item_base + atomicAdd(queue, 1ull);
     const unsigned long long entry = __ldg(P.imap + item);
-    count_item<W, WS>(P, item, entry, S[warp], lane);
+    count_item<W, WS, STATS>(P, item, entry, S[warp], lane);
     item = __shfl_sync(0xFFFFFFFFu, next, 0);
   }
 }
@@ -840,12 +866,13 @@ cudaError_t launch_insert(int k, const CountParams& p, int persistent, int nsm, 
     unsigned long long grid = need;                                                              \
     if (persistent) {                                                                            \
       int per_sm = 0;                                                                            \
-      cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, insert_kernel<w, ws>, \
+      cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, insert_kernel<w, ws, false>, \
                                                                     COUNT_THREADS, 0);           \
       if (e != cudaSuccess) return e;                                                            \
       grid = std::min<unsigned long long>(need, (unsigned long long)nsm * std::max(1, per_sm));  \
     }                                                                                            \
-    insert_kernel<w, ws><<<(unsigned)grid, COUNT_THREADS, 0, st>>>(p);                          \
+    if (p.probe_hist) insert_kernel<w, ws, true><<<(unsigned)grid, COUNT_THREADS, 0, st>>>(p);   \
+    else insert_kernel<w, ws, false><<<(unsigned)grid, COUNT_THREADS, 0, st>>>(p);               \
   }
   GERBIL_KEY_SWITCH(W, WS, L_INSERT)
 #undef L_INSERT

@@ -86,7 +86,12 @@ struct CountParams {
   unsigned long long ovf_cap;
   uint32_t* bin_ovf;             // overflow k-mers per work entry
   Counters* ctr;
+  // probe statistics (NULL: off): per placed k-mer, slots read and 128-byte lines touched
+  unsigned long long* probe_hist;  // [2][PROBE_BUCKETS]
 };
+
+// Probe histogram buckets: [0, 32) = 1..32 probes, 32 = more, 33 = sent to the overflow area.
+constexpr int PROBE_BUCKETS = 34;
 
 constexpr int CHUNK_SLOTS = 2048;  // slots per compaction task of the fused kernel
 

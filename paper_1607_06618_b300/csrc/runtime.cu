@@ -47,6 +47,8 @@ struct gerbil_ctx {
   gerbil_phase_times times{};
   // settings chosen by gerbil_autotune, per key width W
   std::map<int, gerbil_tuning> tuning;
+  // probe statistics (gerbil_probe_stats): device histograms, NULL while off
+  unsigned long long* probe_hist = nullptr;
   // graph form (gerbil_opts.graph): capture stream, the instantiated graph of the last batch
   // (updated in place when the next batch's graph has the same shape), pinned work-list copy
   cudaStream_t cap_stream = nullptr;
@@ -286,6 +288,7 @@ void gerbil_destroy(gerbil_ctx* ctx) {
   if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
   if (ctx->hwork) cudaFreeHost(ctx->hwork);
+  if (ctx->probe_hist) cudaFree(ctx->probe_hist);
   if (ctx->ctr) cudaFree(ctx->ctr);
   if (ctx->hctr) cudaFreeHost(ctx->hctr);
   if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
@@ -302,6 +305,33 @@ int gerbil_internal_alloc(gerbil_ctx* ctx, void** p, size_t bytes, void** stream
 }
 
 void gerbil_internal_free(gerbil_ctx* ctx, void* p, size_t bytes) { dev_free(ctx, p, bytes); }
+
+int gerbil_probe_stats(gerbil_ctx* ctx, int enable) {
+  if (!ctx) return GERBIL_E_INVAL;
+  CK(cudaSetDevice(ctx->device));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (!enable) {
+    if (ctx->probe_hist) cudaFree(ctx->probe_hist);
+    ctx->probe_hist = nullptr;
+    return GERBIL_OK;
+  }
+  const size_t bytes = 2 * gerbil::PROBE_BUCKETS * sizeof(unsigned long long);
+  if (!ctx->probe_hist) CK(cudaMalloc(&ctx->probe_hist, bytes));
+  CK(cudaMemset(ctx->probe_hist, 0, bytes));
+  return GERBIL_OK;
+}
+
+int gerbil_get_probe_stats(const gerbil_ctx* cctx, uint64_t* slots, uint64_t* lines) {
+  if (!cctx || !slots || !lines) return GERBIL_E_INVAL;
+  gerbil_ctx* ctx = const_cast<gerbil_ctx*>(cctx);
+  if (!ctx->probe_hist) return fail(ctx, GERBIL_E_STATE, "probe statistics are off");
+  CK(cudaSetDevice(ctx->device));
+  CK(cudaStreamSynchronize(ctx->stream));
+  CK(cudaMemcpy(slots, ctx->probe_hist, gerbil::PROBE_BUCKETS * 8, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(lines, ctx->probe_hist + gerbil::PROBE_BUCKETS, gerbil::PROBE_BUCKETS * 8,
+                cudaMemcpyDeviceToHost));
+  return GERBIL_OK;
+}
 
 int gerbil_forget_ratio(gerbil_ctx* ctx) {
   if (!ctx) return GERBIL_E_INVAL;
@@ -825,6 +855,7 @@ static int count_fused(gerbil_ctx* ctx, const gerbil_bins* b, const std::vector<
   fp.c.ovf_cap = ovf_cap;
   fp.c.bin_ovf = (uint32_t*)(sm + o_bovf);
   fp.c.ctr = ctx->ctr;
+  fp.c.probe_hist = ctx->probe_hist;
   fp.tasks = (const unsigned long long*)(sm + o_tasks);
   fp.deps = (const uint32_t*)(sm + o_deps);
   fp.ntasks = ntasks;
@@ -988,6 +1019,7 @@ static int count_waves(gerbil_ctx* ctx, const gerbil_bins* b, const std::vector<
   cp.ovf_cap = ovf_cap;
   cp.bin_ovf = (uint32_t*)(sm + o_bovf);
   cp.ctr = ctx->ctr;
+  cp.probe_hist = ctx->probe_hist;
   cp.schedule = opts.schedule;
   if (items) {
     cp.nitems = items;
@@ -1329,6 +1361,7 @@ static int count_impl(gerbil_ctx* ctx, const gerbil_bins* b, const std::vector<i
     cp.ovf_cap = ovf_cap;
     cp.bin_ovf = bin_ovf;
     cp.ctr = ctx->ctr;
+    cp.probe_hist = ctx->probe_hist;
     cp.schedule = opts.schedule;
     if (items) {
       CKG(gerbil::launch_item_map(cp, ls));  // preparation: timed with the clears

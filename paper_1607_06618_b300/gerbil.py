@@ -40,7 +40,7 @@ ABI_SYMBOLS = (
     "gerbil_trim", "gerbil_device_bytes", "gerbil_server_create", "gerbil_server_submit",
     "gerbil_server_wait", "gerbil_server_get_stats", "gerbil_server_destroy",
     "gerbil_autotune", "gerbil_set_tuning", "gerbil_get_tuning", "gerbil_encode_records",
-    "gerbil_forget_ratio",
+    "gerbil_forget_ratio", "gerbil_probe_stats", "gerbil_get_probe_stats",
 )
 
 
@@ -177,6 +177,8 @@ def load() -> ctypes.CDLL:
         "gerbil_profile": (I32, [P, I32]),
         "gerbil_trim": (I32, [P]),
         "gerbil_forget_ratio": (I32, [P]),
+        "gerbil_probe_stats": (I32, [P, I32]),
+        "gerbil_get_probe_stats": (I32, [P, ctypes.POINTER(U64), ctypes.POINTER(U64)]),
         "gerbil_encode_records": (I32, [P, I32, P, U64, I32, ctypes.POINTER(U64)]),
         "gerbil_autotune": (I32, [P, P, I32, U32, ctypes.POINTER(gerbil_opts),
                                   ctypes.POINTER(gerbil_tuning)]),
@@ -613,6 +615,17 @@ class Context:
 
     def count(self, bins: Bins, b: int, k: int, min_count: int, opts=None) -> Counts:
         return Counts(gerbil_count(self.handle, bins.handle, b, k, min_count, opts), self)
+
+    def probe_stats(self, enable: bool = True):
+        _check(load().gerbil_probe_stats(self.handle, 1 if enable else 0), self.handle)
+
+    def get_probe_stats(self):
+        """(slots, lines) histograms: index i < 32 = placed after i+1 slots read / lines
+        touched, 32 = more, 33 = sent to the overflow area."""
+        a = (ctypes.c_uint64 * 34)()
+        b = (ctypes.c_uint64 * 34)()
+        _check(load().gerbil_get_probe_stats(self.handle, a, b), self.handle)
+        return np.array(a[:], dtype=np.uint64), np.array(b[:], dtype=np.uint64)
 
     def forget_ratio(self):
         _check(load().gerbil_forget_ratio(self.handle), self.handle)

@@ -108,3 +108,32 @@ def test_graph_form_with_overflow_and_retry(data):
     assert res.info()[2]["retries"] > 0
     assert_same_rows(res.to_host(), want)
     res.free()
+
+
+def test_probe_statistics_account_for_every_kmer(data):
+    """Probe histograms (Sec. 3.3): every inserted k-mer is recorded once (placed after some
+    number of slots, or sent to the overflow area); lines touched never exceed slots read; the
+    statistics change no count."""
+    gerbil, ctx, bins, want = data
+    ctx.probe_stats(True)
+    got = _rows(ctx, bins, gerbil.default_opts())
+    slots, lines = ctx.get_probe_stats()
+    occ = bins.info()["n_kmers"]
+    assert int(slots.sum()) == occ and int(lines.sum()) == occ
+    assert slots[33] == lines[33] == 0  # nothing overflowed at theta 1024
+    # lines <= slots for every k-mer: the cumulative line histogram dominates the slot one
+    assert np.all(np.cumsum(lines[:33]) >= np.cumsum(slots[:33]))
+    assert slots[0] > occ // 2
+    ctx.probe_stats(False)
+    with pytest.raises(gerbil.GerbilError):
+        ctx.get_probe_stats()
+    assert_same_rows(got, want)
+    # theta = 1 with small tables: k-mers that found no room are counted in the last bucket
+    ctx.probe_stats(True)
+    res = ctx.count_batch(bins, None, K, 2, gerbil.default_opts(max_probes=1, distinct_ratio=0.05,
+                                                                 overflow_slots=1 << 22))
+    st = res.info()[2]
+    res.free()
+    slots, lines = ctx.get_probe_stats()
+    assert int(slots[33]) == st["overflowed"] > 0 and int(slots[:33].sum()) + int(slots[33]) == occ
+    ctx.probe_stats(False)
