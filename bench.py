@@ -58,6 +58,8 @@ def _args():
     ap.add_argument("--autotune", action="store_true",
                     help="form, schedule and per-class load factors from the autotuner")
     ap.add_argument("--graph", action="store_true", help="phase two as one captured CUDA graph")
+    ap.add_argument("--orderings", action="store_true",
+                    help="compare the minimizer orderings (super-mers vs largest bin) instead")
     ap.add_argument("--serving-jobs", type=int, default=48,
                     help="jobs of the serving stream (--workload %s)" % SERVING_WORKLOAD)
     ap.add_argument("--serving-slots", type=int, default=4)
@@ -623,9 +625,44 @@ def main_serving(a, world, rank, local):
     return 0
 
 
+def main_orderings(a, rank, local):
+    """Sec. 3.1's trade-off between the orderings, on the GPU partition of a synthetic read set:
+    super-mers and their packed bytes (the paper's temporary-file size) against the largest
+    k-mer count of one minimizer (with 65,536 bins, about one minimizer per bin for m = 6)."""
+    import torch
+    from paper_1607_06618_b300 import gerbil, synth
+    torch.cuda.set_device(local)
+    seq, offs, p = synth.workload(a.workload)
+    s_dev = torch.from_numpy(seq).cuda()
+    o_dev = torch.from_numpy(offs.view(np.int64)).cuda()
+    ctx = gerbil.Context(local)
+    names = ["kmc2", "lex", "cgat", "roberts", "random"]
+    out = {}
+    for k, m in ((28, 6), (p["k"], p["m"])):
+        nb = 65536
+        for o, name in enumerate(names):
+            bins = ctx.partition(s_dev, o_dev, k, m, nb, gerbil.default_opts(ordering=o))
+            inf = bins.info()
+            per = [gerbil.gerbil_bin_stats(bins.handle, b) for b in range(nb)]  # (super, bases, k-mers)
+            kmers = np.array([x[2] for x in per], dtype=np.float64)
+            nbases = sum(x[1] for x in per)
+            bins.free()
+            out["k%d_m%d_%s" % (k, m, name)] = {
+                "supermers": int(inf["n_supermers"]), "packed_bytes": int(nbases // 4),
+                "max_kmers_per_bin": int(kmers.max()), "mean_kmers_per_nonempty_bin":
+                float(kmers[kmers > 0].mean()), "nonempty_bins": int((kmers > 0).sum())}
+    ctx.close()
+    if rank == 0:
+        print(json.dumps({"experiment": "minimizer orderings (Sec. 3.1, Fig. 3)",
+                          "workload": a.workload, "bins": 65536, "results": out}), flush=True)
+    return 0
+
+
 def main():
     a = _args()
     world, rank, local = _dist()
+    if a.orderings:
+        return main_orderings(a, rank, local)
     if a.workload == SERVING_WORKLOAD:
         if a.impl == "reference":
             if rank == 0:

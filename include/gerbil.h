@@ -56,8 +56,17 @@ typedef enum gerbil_status {
 typedef enum gerbil_ordering {
   GERBIL_ORDER_KMC2 = 0, /* Sec. 3.1 "KMC2": lexicographic, m-mers starting with AAA or ACA or
                             holding AA past position 0 ranked last (Gerbil's choice) */
-  GERBIL_ORDER_LEX = 1   /* plain lexicographic A<C<G<T (the ordering of Fig. 1) */
+  GERBIL_ORDER_LEX = 1,  /* plain lexicographic A<C<G<T (the ordering of Fig. 1) */
+  GERBIL_ORDER_CGAT = 2, /* Sec. 3.1 "CGAT": lexicographic with C<G<A<T */
+  GERBIL_ORDER_ROBERTS = 3, /* Sec. 3.1 "Roberts et al.": the bases at even positions (the
+                            2nd, 4th, ... base) complemented, then lexicographic with C<A<T<G,
+                            so that CGCG... ranks first */
+  GERBIL_ORDER_RANDOM = 4 /* Sec. 3.1 "Random": a fixed permutation of the 4^m m-mers (multiply
+                            by an odd constant and fold the high half of the 2m bits into the
+                            low half, twice) */
 } gerbil_ordering;
+/* With every ordering the minimizer is the canonical m-mer of smallest rank (canonical_minimizer
+ * = 1) and its bin is bin_of(rank mod 4^m): for KMC2 and LEX that is the m-mer's value. */
 
 typedef struct gerbil_ctx gerbil_ctx;       /* device, stream, memory budget, scratch */
 typedef struct gerbil_bins gerbil_bins;     /* device-resident bins of super-mers */

@@ -26,6 +26,9 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 
 ORDER_KMC2 = 0
 ORDER_LEX = 1
+ORDER_CGAT = 2
+ORDER_ROBERTS = 3
+ORDER_RANDOM = 4
 
 
 def build(force: bool = False) -> str:

@@ -38,6 +38,14 @@ bool is_base(uint8_t c) {
 char upper(uint8_t c) { return (c >= 'a' && c <= 'z') ? char(c - 'a' + 'A') : char(c); }
 
 // Sec. 2.4.2: reverse the string and replace A<->T, C<->G (written into r).
+char complement_base(char c) {
+    if (c == 'A') return 'T';
+    if (c == 'C') return 'G';
+    if (c == 'G') return 'C';
+    if (c == 'T') return 'A';
+    return '?';
+}
+
 void reverse_complement_into(const std::string& s, std::string& r) {
     r.resize(s.size());
     for (size_t i = 0; i < s.size(); ++i) {
@@ -144,15 +152,45 @@ uint64_t mmer_value(const std::string& s) {
     return v;
 }
 
-enum { ORDER_KMC2 = 0, ORDER_LEX = 1 };
+enum { ORDER_KMC2 = 0, ORDER_LEX = 1, ORDER_CGAT = 2, ORDER_ROBERTS = 3, ORDER_RANDOM = 4 };
 
-// Rank of an m-mer string under the ordering: smaller rank = preferred minimizer.
+// Base-4 number of the string under an alphabet order given as the rank of A, C, G, T.
+uint64_t alphabet_value(const std::string& s, const int rank_of[4]) {
+    uint64_t v = 0;
+    for (char c : s) v = v * 4 + uint64_t(rank_of[base_code(c)]);
+    return v;
+}
+
+// Rank of an m-mer string under the ordering (Sec. 3.1): smaller rank = preferred minimizer.
 uint64_t mmer_rank(const std::string& s, int ordering) {
     uint64_t v = mmer_value(s);
-    if (ordering == ORDER_LEX) return v;
     uint64_t four_m = 1;
     for (size_t i = 0; i < s.size(); ++i) four_m *= 4;
-    return kmc2_demoted(s) ? v + four_m : v;
+    switch (ordering) {
+        case ORDER_LEX:
+            return v;
+        case ORDER_CGAT: {  // lexicographic with C < G < A < T
+            static const int r[4] = {2, 0, 1, 3};  // A C G T
+            return alphabet_value(s, r);
+        }
+        case ORDER_ROBERTS: {  // the 2nd, 4th, ... base complemented, then C < A < T < G
+            std::string t = s;
+            for (size_t i = 1; i < t.size(); i += 2) t[i] = complement_base(t[i]);
+            static const int r[4] = {1, 0, 3, 2};  // A C G T
+            return alphabet_value(t, r);
+        }
+        case ORDER_RANDOM: {  // a fixed permutation of the 4^m values
+            const uint64_t mask = four_m - 1;
+            const int m = int(s.size());
+            uint64_t x = (v * 0x9E3779B97F4A7C15ull) & mask;
+            x ^= x >> m;
+            x = (x * 0xBF58476D1CE4E5B9ull) & mask;
+            x ^= x >> m;
+            return x;
+        }
+        default:  // KMC2
+            return kmc2_demoted(s) ? v + four_m : v;
+    }
 }
 
 // MurmurHash3's 32-bit finalizer (Appleby), used as the minimizer -> bin mixer.  The paper
@@ -290,7 +328,9 @@ int oracle_partition(const uint8_t* seq, const uint64_t* offsets, uint64_t nread
             if (starts) {
                 res->pos.push_back(gpos);
                 res->nkmers.push_back(1);
-                res->bin.push_back(bin_of(best_value, nbins, bounds));
+                // the bin is a function of the minimizer: of its rank (a bijection of the
+                // m-mer for every ordering; equal to the m-mer's value for KMC2 and LEX)
+                res->bin.push_back(bin_of(best_rank & ((1ull << (2 * m)) - 1), nbins, bounds));
                 res->minimizer.push_back(best_value);
             } else {
                 res->nkmers.back() += 1;

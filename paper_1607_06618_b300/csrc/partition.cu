@@ -100,14 +100,48 @@ __device__ __forceinline__ uint32_t kmc2_demoted(uint32_t v, int m) {
   return d | (pairs != 0u);
 }
 
+// The orderings of Sec. 3.1 on the 2-bit value c of an m-mer (A0 C1 G2 T3, first base high),
+// as ranks (smaller = preferred); every one is a bijection of [0, 4^m) except KMC2, which adds
+// a demotion bit above it.
+//   CGAT: digits C0 G1 A2 T3 -- per base (h, l) -> (not (h xor l), h).
+//   Roberts: bases at even positions counting the first base as position 1 (the 2nd, 4th, ...)
+//     complemented, then digits C0 A1 T2 G3 -- complement is xor 3, the digit map is xor 1; so
+//     CGCG... becomes CCCC..., the smallest, as the ordering intends.
+//   Random: a fixed permutation of [0, 4^m): multiply by an odd constant and fold the high
+//     half into the low half, twice, within 2m bits.
+__device__ __forceinline__ uint32_t order_rank(uint32_t c, int m, int ordering) {
+  const uint32_t lowbits = (m >= 16) ? 0xFFFFFFFFu : ((1u << (2 * m)) - 1u);
+  const uint32_t L = 0x55555555u & lowbits;  // low bit of every base
+  switch (ordering) {
+    case 0: return c | (kmc2_demoted(c, m) << 30);
+    case 2: {
+      const uint32_t h = (c >> 1) & L, l = c & L;
+      return ((~(h ^ l) & L) << 1) | h;
+    }
+    case 3: {
+      uint32_t even = 0;  // both bits of the 2nd, 4th, ... base
+      for (int i = 1; i < m; i += 2) even |= 3u << (2 * (m - 1 - i));
+      return c ^ even ^ L;
+    }
+    case 4: {
+      unsigned long long x = c;
+      x = (x * 0x9E3779B97F4A7C15ull) & lowbits;
+      x ^= x >> m;
+      x = (x * 0xBF58476D1CE4E5B9ull) & lowbits;
+      x ^= x >> m;
+      return (uint32_t)x;
+    }
+    default: return c;
+  }
+}
+
 __device__ __forceinline__ uint32_t mmer_rank(uint32_t v, int m, int ordering, int canon_min) {
   uint32_t c = v;
   if (canon_min) {
     const uint32_t rc = (uint32_t)(rev2(~(unsigned long long)v) >> (64 - 2 * m));
     c = rc < v ? rc : v;
   }
-  if (ordering == 0) c |= kmc2_demoted(c, m) << 30;
-  return c;
+  return order_rank(c, m, ordering);
 }
 
 template <int MLEN>  // the minimizer length, so that every shift below is a constant
@@ -192,8 +226,7 @@ __global__ void __launch_bounds__(256) supermer_kernel(SupermerParams P) {
             const uint32_t rc = (uint32_t)(rcwin >> (2 * d)) & vmask;
             c = rc < v ? rc : v;
           }
-          if (P.ordering == 0) c |= kmc2_demoted(c, m) << 30;
-          kk = c + 1u;
+          kk = order_rank(c, m, P.ordering) + 1u;
         }
       }
       key[d] = kk;

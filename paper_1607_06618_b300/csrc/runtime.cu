@@ -386,7 +386,7 @@ int gerbil_partition(gerbil_ctx* ctx, const gerbil_reads* reads, int k, int m, i
     return fail(ctx, GERBIL_E_INVAL, "k, m or nbins out of range");
   if (opts.supermer_cap < 1 || opts.supermer_cap > 1024)
     return fail(ctx, GERBIL_E_INVAL, "supermer_cap out of range");
-  if (opts.ordering != GERBIL_ORDER_KMC2 && opts.ordering != GERBIL_ORDER_LEX)
+  if (opts.ordering < GERBIL_ORDER_KMC2 || opts.ordering > GERBIL_ORDER_RANDOM)
     return fail(ctx, GERBIL_E_INVAL, "unknown ordering");
   if (reads->nreads > 0 && (!reads->seq || !reads->offsets))
     return fail(ctx, GERBIL_E_INVAL, "null reads");

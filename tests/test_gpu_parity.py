@@ -78,7 +78,9 @@ def _rows(part):
 
 @pytest.mark.parametrize("k,m,lmax,ordering", [
     (32, 7, 256, 0), (32, 7, 7, 0), (65, 9, 256, 0), (65, 9, 1024, 1), (8, 3, 5, 1),
-    (99, 9, 64, 0), (200, 11, 256, 0), (256, 15, 300, 0), (33, 1, 256, 1)])
+    (99, 9, 64, 0), (200, 11, 256, 0), (256, 15, 300, 0), (33, 1, 256, 1),
+    (32, 7, 256, 2), (65, 9, 256, 3), (65, 9, 256, 4), (99, 11, 128, 2), (127, 15, 256, 3),
+    (200, 13, 256, 4), (12, 1, 256, 3), (10, 2, 3, 4)])
 def test_partition_matches_oracle(g, k, m, lmax, ordering):
     nreads = 700 if k < 100 else 120
     seq, offs = synth.random_small(nreads, k - 3, k + 400, p_n=0.004, seed=k * 31 + m)
@@ -266,3 +268,14 @@ def test_genome5m_full_size_total(g, genome5m):
     # each key once
     sk, _ = sort_rows(*got)
     assert not np.any(np.all(sk[1:] == sk[:-1], axis=1))
+
+
+def test_counts_do_not_depend_on_the_ordering(g):
+    """The five orderings move k-mers between bins, never change a count (Sec. 2.1)."""
+    seq, offs = synth.random_small(500, 60, 260, p_n=0.003, seed=4242)
+    seq = np.concatenate([seq, seq[: int(offs[80])]])
+    offs = np.concatenate([offs, offs[1:81] + offs[-1]])
+    want = oracle.count(seq, offs, 41, min_count=1)
+    for ordering in range(5):
+        got, _ = _gpu_count(g, seq, offs, 41, 9, 23, 1, ordering=ordering)
+        assert_same_rows(got, want)

@@ -5,6 +5,7 @@ paper (tests/golden/), brute force on tiny inputs (oracle/brute.py, pure Python)
 form, or an invariant that must hold for the exact histogram.
 """
 import collections
+import itertools
 import os
 
 import numpy as np
@@ -13,6 +14,7 @@ import pytest
 import oracle
 from oracle import brute
 from paper_1607_06618_b300 import synth
+from tests._util import revcomp_reads
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
@@ -268,3 +270,51 @@ def test_invariant_partition_covers_windows_and_bins_agree():
     for x, b in bin_of_kmer.items():
         mz = brute.minimizer(brute.revcomp(x), m)
         assert oracle.bin_of(brute.value(mz), nb) == b
+
+
+# ---- the other orderings of Sec. 3.1 -----------------------------------------------------
+
+def _all_mmers(m):
+    return ["".join(t) for t in itertools.product("ACGT", repeat=m)]
+
+
+@pytest.mark.parametrize("m", [1, 2, 3, 4, 5])
+def test_cgat_ordering_is_lexicographic_in_c_g_a_t(m):
+    mm = _all_mmers(m)
+    by_rank = sorted(mm, key=lambda s: oracle.mmer_rank(s, oracle.ORDER_CGAT))
+    assert by_rank == sorted(mm, key=lambda s: ["CGAT".index(c) for c in s])
+
+
+@pytest.mark.parametrize("m", [1, 2, 3, 4, 5])
+def test_roberts_ordering_complements_even_positions(m):
+    comp = {"A": "T", "C": "G", "G": "C", "T": "A"}
+
+    def key(s):
+        t = [comp[c] if i % 2 == 1 else c for i, c in enumerate(s)]  # 2nd, 4th, ... base
+        return ["CATG".index(c) for c in t]
+
+    mm = _all_mmers(m)
+    assert sorted(mm, key=lambda s: oracle.mmer_rank(s, oracle.ORDER_ROBERTS)) == sorted(mm, key=key)
+    # the property Sec. 3.1 states: rare minimizers like CGCGCG are preferred -- it is the
+    # smallest m-mer of all (it maps to CCCCCC)
+    assert oracle.mmer_rank("CG" * 3, oracle.ORDER_ROBERTS) == 0
+
+
+@pytest.mark.parametrize("m", [1, 2, 3, 5, 7])
+def test_random_ordering_is_a_permutation(m):
+    ranks = sorted(oracle.mmer_rank(s, oracle.ORDER_RANDOM) for s in _all_mmers(m))
+    assert ranks == list(range(4 ** m))
+
+
+@pytest.mark.parametrize("ordering", [0, 1, 2, 3, 4])
+def test_partition_covers_every_window_under_every_ordering(ordering):
+    """Every ordering gives super-mers whose k-mers are exactly the N-free windows, and x and
+    revcomp(x) land in one bin (canonical minimizers)."""
+    seq, offs = synth.random_small(60, 20, 120, p_n=0.01, seed=77 + ordering)
+    k, m = 15, 5
+    part = oracle.partition(seq, offs, k, m, 7, ordering=ordering)
+    assert int(part["nkmers"].sum()) == oracle.windows(seq, offs, k)
+    rseq, roffs = revcomp_reads(seq, offs)
+    rpart = oracle.partition(rseq, roffs, k, m, 7, ordering=ordering)
+    assert np.array_equal(np.bincount(part["bin"], weights=part["nkmers"], minlength=7),
+                          np.bincount(rpart["bin"], weights=rpart["nkmers"], minlength=7))
