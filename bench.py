@@ -77,6 +77,23 @@ def _dist():
     return world, rank, local
 
 
+def _reduce(x: float, dist, device, op: str) -> float:
+    """x reduced over the ranks ("max" or "sum"); x itself on one process."""
+    if not dist:
+        return x
+    import torch
+    t = torch.tensor([x], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def _replica_value(units_per_rank: int, local_ms: float, dist, world: int, device) -> tuple:
+    """Whole-job throughput of independent replicas: the units of all ranks over the slowest
+    rank's time.  Returns (units per second, max ms)."""
+    ms = _reduce(local_ms, dist, device, "max")
+    return units_per_rank * world / (ms / 1000.0), ms
+
+
 def _peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -296,11 +313,7 @@ def main_ours(a, world, rank, local):
     ph = ctx.phase_times()
     ck = clocks.stop()
     ctx.profile(False)
-    if dist:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = occ * a.steps * world / (ms / 1000.0)
+    value, ms = _replica_value(occ * a.steps, ms, dist, world, "cuda")
 
     # roofline of the dominant kernel (insert), from its own event-timed launches
     hbm, peak_kind = _peaks()
@@ -474,11 +487,9 @@ def main_ours(a, world, rank, local):
         for wctx, _, _ in workers:
             if wctx is not ctx:
                 wctx.close()
-        if dist:
-            t = torch.tensor([te], device="cuda", dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            te = float(t.item())
-        e2e = {"value": occ * world / te, "unit": UNIT,
+        e2e_value, te_ms = _replica_value(occ, 1000 * te, dist, world, "cuda")
+        te = te_ms / 1000
+        e2e = {"value": e2e_value, "unit": UNIT,
                "h2d_bytes_per_step": int(seq.nbytes + offs.nbytes),
                "d2h_bytes_per_step": int(nrow * (8 * W + 4)), "ms_per_step": 1000 * te,
                "workers": nw, "steps": a.e2e_steps,
@@ -585,11 +596,7 @@ def main_serving(a, world, rank, local):
     st = server.stats()
     server.close()
     occ = sum(r["occurrences"] for r in out)
-    value = occ / wall
-    if dist:
-        t = torch.tensor([value], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        value = float(t.item())
+    value = _reduce(occ / wall, dist, "cuda", "sum")
     lat = [r["latency_ms"] for r in out]
     if rank == 0:
         line = {
