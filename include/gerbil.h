@@ -61,9 +61,16 @@ typedef enum gerbil_ordering {
   GERBIL_ORDER_ROBERTS = 3, /* Sec. 3.1 "Roberts et al.": the bases at even positions (the
                             2nd, 4th, ... base) complemented, then lexicographic with C<A<T<G,
                             so that CGCG... ranks first */
-  GERBIL_ORDER_RANDOM = 4 /* Sec. 3.1 "Random": a fixed permutation of the 4^m m-mers (multiply
+  GERBIL_ORDER_RANDOM = 4, /* Sec. 3.1 "Random": a fixed permutation of the 4^m m-mers (multiply
                             by an odd constant and fold the high half of the 2m bits into the
                             low half, twice) */
+  GERBIL_ORDER_DFP = 5   /* Sec. 3.1 "distance from pivot", dfp(p): the m-mers sorted by their
+                            frequency in a sample of the reads (ascending; equal frequencies by
+                            value), then by the distance of that place to floor(4^m p) (equal
+                            distances: the smaller place first); p = opts->dfp_pivot, the
+                            sample = every opts->dfp_sample-th read (reads 0, s, 2s, ...), every
+                            m-mer of it without an undetermined base (canonical when the
+                            minimizers are).  m <= 12. */
 } gerbil_ordering;
 /* With every ordering the minimizer is the canonical m-mer of smallest rank (canonical_minimizer
  * = 1) and its bin is bin_of(rank mod 4^m): for KMC2 and LEX that is the m-mer's value. */
@@ -136,6 +143,9 @@ typedef struct gerbil_opts {
                                   context keeps the instantiated graph and updates it in place
                                   for the next batch of the same shape.  0 (default): plain
                                   launches */
+  float dfp_pivot;             /* p of GERBIL_ORDER_DFP, 0..1 (default 0.5) */
+  uint32_t dfp_sample;         /* GERBIL_ORDER_DFP: frequencies from every dfp_sample-th read
+                                  (default 16) */
 } gerbil_opts;
 
 /* Per-call statistics of a count. */

@@ -29,6 +29,7 @@ ORDER_LEX = 1
 ORDER_CGAT = 2
 ORDER_ROBERTS = 3
 ORDER_RANDOM = 4
+ORDER_DFP = 5
 
 
 def build(force: bool = False) -> str:
@@ -68,6 +69,14 @@ def _load():
                                          ctypes.c_uint32, u32p, ctypes.c_int, ctypes.c_int,
                                          ctypes.c_uint32, vpp]
         lib.oracle_partition_size.restype = ctypes.c_uint64
+        lib.oracle_partition_dfp.restype = ctypes.c_int
+        lib.oracle_partition_dfp.argtypes = [u8p, u64p, ctypes.c_uint64, ctypes.c_int, ctypes.c_int,
+                                             ctypes.c_uint32, u32p, ctypes.c_int, ctypes.c_int,
+                                             ctypes.c_uint32, ctypes.c_float, ctypes.c_uint32,
+                                             ctypes.POINTER(ctypes.c_void_p)]
+        lib.oracle_dfp_ranks.restype = ctypes.c_int
+        lib.oracle_dfp_ranks.argtypes = [u8p, u64p, ctypes.c_uint64, ctypes.c_int, ctypes.c_int,
+                                         ctypes.c_float, ctypes.c_uint32, u32p]
         lib.oracle_partition_size.argtypes = [ctypes.c_void_p]
         lib.oracle_partition_copy.restype = None
         lib.oracle_partition_copy.argtypes = [ctypes.c_void_p, u64p, u32p, u32p, u64p]
@@ -133,8 +142,20 @@ def count(seq, offsets, k: int, canonical: bool = True, min_count: int = 1,
     return keys, counts
 
 
+def dfp_ranks(seq, offsets, m: int, p: float = 0.5, every: int = 16, canonical_min: bool = True):
+    """dfp(p) rank of every m-mer value (Sec. 3.1), frequencies from every `every`-th read."""
+    seq, offsets = _reads(seq, offsets)
+    out = np.zeros(4 ** m, np.uint32)
+    rc = _load().oracle_dfp_ranks(_ptr(seq, ctypes.c_uint8), _ptr(offsets, ctypes.c_uint64),
+                                  offsets.size - 1, m, 1 if canonical_min else 0, p, every,
+                                  _ptr(out, ctypes.c_uint32))
+    if rc != 0:
+        raise ValueError("oracle_dfp_ranks rejected its arguments")
+    return out
+
+
 def partition(seq, offsets, k: int, m: int, nbins: int, bounds=None, ordering: int = ORDER_KMC2,
-              canonical_min: bool = True, lmax: int = 256):
+              canonical_min: bool = True, lmax: int = 256, dfp_p: float = 0.5, dfp_every: int = 16):
     """Super-mers by definition: dict of arrays pos, nkmers, bin, minimizer (input order)."""
     seq, offsets = _reads(seq, offsets)
     lib = _load()
@@ -143,9 +164,9 @@ def partition(seq, offsets, k: int, m: int, nbins: int, bounds=None, ordering: i
         bounds = np.ascontiguousarray(bounds, dtype=np.uint32)
         bptr = _ptr(bounds, ctypes.c_uint32)
     h = ctypes.c_void_p()
-    rc = lib.oracle_partition(_ptr(seq, ctypes.c_uint8), _ptr(offsets, ctypes.c_uint64),
-                              offsets.size - 1, k, m, nbins, bptr, ordering,
-                              1 if canonical_min else 0, lmax, ctypes.byref(h))
+    rc = lib.oracle_partition_dfp(_ptr(seq, ctypes.c_uint8), _ptr(offsets, ctypes.c_uint64),
+                                  offsets.size - 1, k, m, nbins, bptr, ordering,
+                                  1 if canonical_min else 0, lmax, dfp_p, dfp_every, ctypes.byref(h))
     if rc != 0:
         raise ValueError("oracle_partition rejected its arguments")
     try:

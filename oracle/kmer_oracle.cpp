@@ -19,6 +19,7 @@
 // of Fig. 1, Sec. 2.4.2 and App. C, brute force on tiny inputs, closed forms, invariants).
 
 #include <algorithm>
+#include <cmath>
 #include <cstdint>
 #include <cstring>
 #include <map>
@@ -152,7 +153,8 @@ uint64_t mmer_value(const std::string& s) {
     return v;
 }
 
-enum { ORDER_KMC2 = 0, ORDER_LEX = 1, ORDER_CGAT = 2, ORDER_ROBERTS = 3, ORDER_RANDOM = 4 };
+enum { ORDER_KMC2 = 0, ORDER_LEX = 1, ORDER_CGAT = 2, ORDER_ROBERTS = 3, ORDER_RANDOM = 4,
+       ORDER_DFP = 5 };
 
 // Base-4 number of the string under an alphabet order given as the rank of A, C, G, T.
 uint64_t alphabet_value(const std::string& s, const int rank_of[4]) {
@@ -294,10 +296,59 @@ void oracle_count_free(void* h) { delete static_cast<CountResult*>(h); }
 // minimizer value.  Readings: a run is also cut before every window whose global start
 // position is a multiple of lmax, which bounds a super-mer at lmax k-mers; the bin of a
 // super-mer is bin_of(minimizer).  Rows are emitted in input order.
-int oracle_partition(const uint8_t* seq, const uint64_t* offsets, uint64_t nreads, int k, int m,
-                     uint32_t nbins, const uint32_t* bounds, int ordering, int canonical_min,
-                     uint32_t lmax, void** out) {
+// Distance from pivot, dfp(p) (Sec. 3.1).  Frequencies of the m-mers are taken from a sample of
+// the input -- our reading: every `every`-th read (reads 0, every, 2*every, ...), every m-mer
+// of it without an undetermined base, canonical when minimizers are -- then the m-mers are
+// sorted by ascending frequency (equal frequencies: by value), and re-sorted by the distance
+// of that position to the pivot floor(4^m * p) (equal distances: the smaller position first).
+// The rank of an m-mer is its place in the second order.
+std::vector<uint32_t> dfp_ranks(const uint8_t* seq, const uint64_t* offsets, uint64_t nreads,
+                                int m, int canonical_min, float p, uint32_t every) {
+    const uint64_t n4 = uint64_t(1) << (2 * m);
+    std::vector<uint64_t> freq(n4, 0);
+    for (uint64_t r = 0; r < nreads; r += every) {
+        const uint8_t* read = seq + offsets[r];
+        const uint64_t len = offsets[r + 1] - offsets[r];
+        for (uint64_t q = 0; q + m <= len; ++q) {
+            if (!window_ok(read, q, m)) continue;
+            std::string s = window_string(read, q, m);
+            if (canonical_min) {
+                std::string t = reverse_complement(s);
+                if (t < s) s = t;
+            }
+            freq[mmer_value(s)] += 1;
+        }
+    }
+    std::vector<uint64_t> by_freq(n4);
+    for (uint64_t v = 0; v < n4; ++v) by_freq[v] = v;
+    std::sort(by_freq.begin(), by_freq.end(), [&](uint64_t a, uint64_t b) {
+        return freq[a] != freq[b] ? freq[a] < freq[b] : a < b;
+    });
+    // p is the 32-bit value of the library's option: the pivot is floor(4^m * p) in doubles
+    double pd = p < 0 ? 0.0 : (p > 1 ? 1.0 : double(p));
+    const uint64_t pivot = std::min<uint64_t>(n4 - 1, uint64_t(std::floor(double(n4) * pd)));
+    std::vector<uint64_t> order(n4);  // positions in the frequency order
+    for (uint64_t i = 0; i < n4; ++i) order[i] = i;
+    auto dist = [&](uint64_t i) { return i > pivot ? i - pivot : pivot - i; };
+    std::sort(order.begin(), order.end(), [&](uint64_t a, uint64_t b) {
+        return dist(a) != dist(b) ? dist(a) < dist(b) : a < b;
+    });
+    std::vector<uint32_t> rank(n4);
+    for (uint64_t r2 = 0; r2 < n4; ++r2) rank[by_freq[order[r2]]] = uint32_t(r2);
+    return rank;
+}
+
+int oracle_partition_dfp(const uint8_t* seq, const uint64_t* offsets, uint64_t nreads, int k,
+                         int m, uint32_t nbins, const uint32_t* bounds, int ordering,
+                         int canonical_min, uint32_t lmax, float dfp_p, uint32_t dfp_every,
+                         void** out) {
     if (m < 1 || m >= k || m > 15 || nbins < 1 || lmax < 1) return 1;
+    if (ordering == ORDER_DFP && (m > 12 || dfp_every < 1)) return 1;
+    std::vector<uint32_t> table;
+    if (ordering == ORDER_DFP) table = dfp_ranks(seq, offsets, nreads, m, canonical_min, dfp_p, dfp_every);
+    auto rank_of = [&](const std::string& s) -> uint64_t {
+        return ordering == ORDER_DFP ? table[mmer_value(s)] : mmer_rank(s, ordering);
+    };
     PartitionResult* res = new PartitionResult;
     for (uint64_t r = 0; r < nreads; ++r) {
         const uint8_t* read = seq + offsets[r];
@@ -317,7 +368,7 @@ int oracle_partition(const uint8_t* seq, const uint64_t* offsets, uint64_t nread
                     std::string t = reverse_complement(s);
                     if (t < s) s = t;
                 }
-                uint64_t rk = mmer_rank(s, ordering);
+                uint64_t rk = rank_of(s);
                 if (rk < best_rank) {
                     best_rank = rk;
                     best_value = mmer_value(s);
@@ -340,6 +391,22 @@ int oracle_partition(const uint8_t* seq, const uint64_t* offsets, uint64_t nread
         }
     }
     *out = res;
+    return 0;
+}
+
+int oracle_partition(const uint8_t* seq, const uint64_t* offsets, uint64_t nreads, int k, int m,
+                     uint32_t nbins, const uint32_t* bounds, int ordering, int canonical_min,
+                     uint32_t lmax, void** out) {
+    return oracle_partition_dfp(seq, offsets, nreads, k, m, nbins, bounds, ordering, canonical_min,
+                                lmax, 0.5f, 16, out);
+}
+
+// dfp ranks of every m-mer value (exposed for pinning the ordering).
+int oracle_dfp_ranks(const uint8_t* seq, const uint64_t* offsets, uint64_t nreads, int m,
+                     int canonical_min, float p, uint32_t every, uint32_t* out) {
+    if (m < 1 || m > 12 || every < 1) return 1;
+    std::vector<uint32_t> t = dfp_ranks(seq, offsets, nreads, m, canonical_min, p, every);
+    std::copy(t.begin(), t.end(), out);
     return 0;
 }
 

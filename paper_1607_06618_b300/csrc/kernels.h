@@ -22,6 +22,7 @@ struct SupermerParams {
   uint32_t lmax;                     // super-mer cap L_max
   uint32_t nbins;
   const uint32_t* bounds;            // device, nbins-1 split points, or NULL
+  const uint32_t* rank_table;        // dfp ordering: rank of every m-mer value (4^m entries)
   int tile;                          // window starts per CTA
   // supermer_kernel: per-bin counts and one record per super-mer
   unsigned long long* bin_nsuper;
@@ -42,6 +43,10 @@ cudaError_t launch_encode(const uint8_t* seq, uint64_t n, unsigned long long* pa
 cudaError_t launch_boundary(const uint64_t* offsets, uint64_t nreads, uint64_t n, uint32_t* bmask,
                             unsigned int* err, cudaStream_t st);
 cudaError_t launch_supermer(const SupermerParams& p, cudaStream_t st);
+// Frequencies of the (canonical) m-mers of every `every`-th read, for the dfp ordering.
+cudaError_t launch_mmer_freq(const unsigned long long* packed, const uint32_t* nmask,
+                             const uint64_t* offsets, uint64_t nreads, uint32_t every, int m,
+                             int canon_min, uint32_t* freq, int nsm, cudaStream_t st);
 cudaError_t launch_scatter(const SupermerParams& p, unsigned long long nrec, int nsm, cudaStream_t st);
 size_t supermer_smem_bytes(int tile, int lmax, int k, int m);
 

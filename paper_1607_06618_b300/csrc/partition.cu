@@ -109,7 +109,9 @@ __device__ __forceinline__ uint32_t kmc2_demoted(uint32_t v, int m) {
 //     CGCG... becomes CCCC..., the smallest, as the ordering intends.
 //   Random: a fixed permutation of [0, 4^m): multiply by an odd constant and fold the high
 //     half into the low half, twice, within 2m bits.
-__device__ __forceinline__ uint32_t order_rank(uint32_t c, int m, int ordering) {
+//   dfp(p): a table of ranks built on the host from sampled m-mer frequencies.
+__device__ __forceinline__ uint32_t order_rank(uint32_t c, int m, int ordering,
+                                               const uint32_t* __restrict__ table) {
   const uint32_t lowbits = (m >= 16) ? 0xFFFFFFFFu : ((1u << (2 * m)) - 1u);
   const uint32_t L = 0x55555555u & lowbits;  // low bit of every base
   switch (ordering) {
@@ -131,17 +133,9 @@ __device__ __forceinline__ uint32_t order_rank(uint32_t c, int m, int ordering) 
       x ^= x >> m;
       return (uint32_t)x;
     }
+    case 5: return __ldg(table + c);
     default: return c;
   }
-}
-
-__device__ __forceinline__ uint32_t mmer_rank(uint32_t v, int m, int ordering, int canon_min) {
-  uint32_t c = v;
-  if (canon_min) {
-    const uint32_t rc = (uint32_t)(rev2(~(unsigned long long)v) >> (64 - 2 * m));
-    c = rc < v ? rc : v;
-  }
-  return order_rank(c, m, ordering);
 }
 
 template <int MLEN>  // the minimizer length, so that every shift below is a constant
@@ -226,7 +220,7 @@ __global__ void __launch_bounds__(256) supermer_kernel(SupermerParams P) {
             const uint32_t rc = (uint32_t)(rcwin >> (2 * d)) & vmask;
             c = rc < v ? rc : v;
           }
-          kk = order_rank(c, m, P.ordering) + 1u;
+          kk = order_rank(c, m, P.ordering, P.rank_table) + 1u;
         }
       }
       key[d] = kk;
@@ -518,6 +512,46 @@ cudaError_t launch_supermer(const SupermerParams& p, cudaStream_t st) {
     case 15: return launch_supermer_m<15>(p, blocks, smem, st);
     default: return cudaErrorInvalidValue;
   }
+}
+
+// One warp per sampled read (reads 0, every, 2 * every, ...), lanes over its m-mer starts; an
+// m-mer with an undetermined base is skipped.
+__global__ void __launch_bounds__(256) mmer_freq_kernel(const unsigned long long* __restrict__ packed,
+                                                       const uint32_t* __restrict__ nmask,
+                                                       const uint64_t* __restrict__ offsets,
+                                                       uint64_t nreads, uint32_t every, int m,
+                                                       int canon_min, uint32_t* __restrict__ freq) {
+  const int lane = threadIdx.x & 31;
+  const uint64_t nwarps = (uint64_t)gridDim.x * (blockDim.x >> 5);
+  const uint64_t w0 = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  for (uint64_t r = w0 * every; r < nreads; r += nwarps * every) {
+    const uint64_t start = offsets[r], end = offsets[r + 1];
+    for (uint64_t q = start + lane; q + m <= end; q += 32) {
+      const uint64_t wq = q >> 5;
+      const int o = (int)(q & 31);
+      const uint32_t nm = o ? ((nmask[wq] << o) | (nmask[wq + 1] >> (32 - o))) : nmask[wq];
+      if (nm >> (32 - m)) continue;
+      const unsigned long long win = o ? ((packed[wq] << (2 * o)) | (packed[wq + 1] >> (64 - 2 * o)))
+                                       : packed[wq];
+      const uint32_t v = (uint32_t)(win >> (64 - 2 * m));
+      uint32_t c = v;
+      if (canon_min) {
+        const uint32_t rc = (uint32_t)(rev2(~(unsigned long long)v) >> (64 - 2 * m));
+        c = rc < v ? rc : v;
+      }
+      atomicAdd(freq + c, 1u);
+    }
+  }
+}
+
+cudaError_t launch_mmer_freq(const unsigned long long* packed, const uint32_t* nmask,
+                             const uint64_t* offsets, uint64_t nreads, uint32_t every, int m,
+                             int canon_min, uint32_t* freq, int nsm, cudaStream_t st) {
+  if (nreads == 0) return cudaSuccess;
+  const uint64_t sampled = (nreads + every - 1) / every;
+  const unsigned blocks = (unsigned)std::min<uint64_t>((sampled + 7) / 8, (uint64_t)nsm * 16);
+  mmer_freq_kernel<<<blocks, 256, 0, st>>>(packed, nmask, offsets, nreads, every, m, canon_min, freq);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_scatter(const SupermerParams& p, unsigned long long nrec, int nsm, cudaStream_t st) {

@@ -205,6 +205,8 @@ void gerbil_opts_default(gerbil_opts* o) {
   o->overflow_slots = 0;
   o->persistent = 1;
   o->ring_slots = 0;
+  o->dfp_pivot = 0.5f;
+  o->dfp_sample = 16;
   o->fused = 0;
   o->schedule = 1;
 }
@@ -386,8 +388,11 @@ int gerbil_partition(gerbil_ctx* ctx, const gerbil_reads* reads, int k, int m, i
     return fail(ctx, GERBIL_E_INVAL, "k, m or nbins out of range");
   if (opts.supermer_cap < 1 || opts.supermer_cap > 1024)
     return fail(ctx, GERBIL_E_INVAL, "supermer_cap out of range");
-  if (opts.ordering < GERBIL_ORDER_KMC2 || opts.ordering > GERBIL_ORDER_RANDOM)
+  if (opts.ordering < GERBIL_ORDER_KMC2 || opts.ordering > GERBIL_ORDER_DFP)
     return fail(ctx, GERBIL_E_INVAL, "unknown ordering");
+  if (opts.ordering == GERBIL_ORDER_DFP &&
+      (m > 12 || opts.dfp_sample < 1 || !(opts.dfp_pivot >= 0.0f && opts.dfp_pivot <= 1.0f)))
+    return fail(ctx, GERBIL_E_INVAL, "dfp ordering: m above 12, sample or pivot out of range");
   if (reads->nreads > 0 && (!reads->seq || !reads->offsets))
     return fail(ctx, GERBIL_E_INVAL, "null reads");
   if (opts.bin_bounds) {
@@ -434,8 +439,10 @@ int gerbil_partition(gerbil_ctx* ctx, const gerbil_reads* reads, int k, int m, i
   uint32_t* dbounds = nullptr;
   unsigned long long* binbuf = nullptr;  // nsuper, nkmers, cursor, sm_begin
   unsigned long long* rec = nullptr;     // super-mer records
+  uint32_t* dtable = nullptr;            // dfp ordering: rank of every m-mer value
   uint64_t rec_cap = 0, nrec = 0;
   size_t seq_bytes = 0, off_bytes = 0, mask_bytes = 0, bounds_bytes = 0, binbuf_bytes = 0;
+  size_t table_bytes = 0;
   std::vector<unsigned long long> hbin;
   int rc = GERBIL_OK;
   auto cleanup = [&]() {
@@ -446,6 +453,7 @@ int gerbil_partition(gerbil_ctx* ctx, const gerbil_reads* reads, int k, int m, i
     dev_free(ctx, dbounds, bounds_bytes);
     dev_free(ctx, binbuf, binbuf_bytes);
     dev_free(ctx, rec, rec_cap * 16);
+    dev_free(ctx, dtable, table_bytes);
   };
 #define TRY(x)                      \
   do {                              \
@@ -505,7 +513,37 @@ int gerbil_partition(gerbil_ctx* ctx, const gerbil_reads* reads, int k, int m, i
   }
   ph_end(ctx, PH_ENCODE);
 
+  // dfp ordering (Sec. 3.1): m-mer frequencies of the sample on the device, rank table on the
+  // host (sorted by frequency, then by the distance of each place to the pivot), back to the
+  // device for the super-mer kernel
+  if (opts.ordering == GERBIL_ORDER_DFP) {
+    const uint64_t n4 = 1ull << (2 * m);
+    table_bytes = n4 * 4;
+    TRY(dev_alloc(ctx, (void**)&dtable, table_bytes));
+    TRYCU(cudaMemsetAsync(dtable, 0, table_bytes, st));
+    TRYCU(gerbil::launch_mmer_freq(b->packed, nmask, offsets, nreads, opts.dfp_sample, m,
+                                   b->canon_min, dtable, ctx->nsm, st));
+    ctx->times.kernel_launches++;
+    std::vector<uint32_t> freq(n4);
+    TRYCU(cudaMemcpyAsync(freq.data(), dtable, table_bytes, cudaMemcpyDeviceToHost, st));
+    TRYCU(cudaStreamSynchronize(st));
+    // place of every value in ascending (frequency, value) order
+    std::vector<uint64_t> key(n4);
+    for (uint64_t v = 0; v < n4; ++v) key[v] = ((uint64_t)freq[v] << 32) | v;
+    std::sort(key.begin(), key.end());
+    const uint64_t pivot = std::min<uint64_t>(n4 - 1, (uint64_t)std::floor((double)n4 * opts.dfp_pivot));
+    // places in ascending (distance to the pivot, place) order; rank = index in that order
+    std::vector<uint64_t> key2(n4);
+    for (uint64_t i = 0; i < n4; ++i) key2[i] = ((i > pivot ? i - pivot : pivot - i) << 32) | i;
+    std::sort(key2.begin(), key2.end());
+    std::vector<uint32_t> rank(n4);
+    for (uint64_t r2 = 0; r2 < n4; ++r2) rank[(uint32_t)key[(uint32_t)key2[r2]]] = (uint32_t)r2;
+    TRYCU(cudaMemcpyAsync(dtable, rank.data(), table_bytes, cudaMemcpyHostToDevice, st));
+    TRYCU(cudaStreamSynchronize(st));  // rank lives on this stack frame
+  }
+
   gerbil::SupermerParams sp{};
+  sp.rank_table = dtable;
   sp.packed = b->packed;
   sp.nmask = nmask;
   sp.bmask = bmask;

@@ -64,7 +64,8 @@ class gerbil_opts(ctypes.Structure):
                 ("overflow_slots", ctypes.c_uint32), ("persistent", ctypes.c_int32),
                 ("ring_slots", ctypes.c_uint32), ("fused", ctypes.c_int32),
                 ("schedule", ctypes.c_int32), ("max_table_mib", ctypes.c_uint32),
-                ("autotune", ctypes.c_uint32), ("graph", ctypes.c_uint32)]
+                ("autotune", ctypes.c_uint32), ("graph", ctypes.c_uint32),
+                ("dfp_pivot", ctypes.c_float), ("dfp_sample", ctypes.c_uint32)]
 
 
 TUNE_CLASSES = 4

@@ -271,11 +271,24 @@ def test_genome5m_full_size_total(g, genome5m):
 
 
 def test_counts_do_not_depend_on_the_ordering(g):
-    """The five orderings move k-mers between bins, never change a count (Sec. 2.1)."""
+    """The six orderings move k-mers between bins, never change a count (Sec. 2.1)."""
     seq, offs = synth.random_small(500, 60, 260, p_n=0.003, seed=4242)
     seq = np.concatenate([seq, seq[: int(offs[80])]])
     offs = np.concatenate([offs, offs[1:81] + offs[-1]])
     want = oracle.count(seq, offs, 41, min_count=1)
-    for ordering in range(5):
+    for ordering in range(6):
         got, _ = _gpu_count(g, seq, offs, 41, 9, 23, 1, ordering=ordering)
         assert_same_rows(got, want)
+
+
+@pytest.mark.parametrize("k,m,p,every", [(32, 7, 0.5, 16), (65, 9, 0.0, 4), (65, 9, 1.0, 1),
+                                         (99, 11, 0.8, 8), (20, 6, 0.5, 3), (127, 12, 0.3, 5)])
+def test_partition_dfp_ordering_matches_oracle(g, k, m, p, every):
+    """dfp(p) (Sec. 3.1): frequencies sampled on the GPU, rank table built by the library; the
+    bins equal the oracle's, which samples and ranks by its own code."""
+    seq, offs = synth.random_small(600, k - 3, k + 300, p_n=0.004, seed=k * 7 + m)
+    seq = np.concatenate([seq, seq[: int(offs[100])]])  # repeats: uneven m-mer frequencies
+    offs = np.concatenate([offs, offs[1:101] + offs[-1]])
+    ex, _, _ = _gpu_bins(g, seq, offs, k, m, 29, ordering=5, dfp_pivot=p, dfp_sample=every)
+    want = oracle.partition(seq, offs, k, m, 29, ordering=5, dfp_p=p, dfp_every=every)
+    assert _rows(ex) == _rows(want)

@@ -318,3 +318,27 @@ def test_partition_covers_every_window_under_every_ordering(ordering):
     rpart = oracle.partition(rseq, roffs, k, m, 7, ordering=ordering)
     assert np.array_equal(np.bincount(part["bin"], weights=part["nkmers"], minlength=7),
                           np.bincount(rpart["bin"], weights=rpart["nkmers"], minlength=7))
+
+
+def test_dfp_ordering_follows_frequencies_and_pivot():
+    """dfp(p) (Sec. 3.1): a permutation; p = 0 ranks the rarest m-mers first, p = 1 the most
+    frequent, p = 0.5 those of middle frequency (checked against a count written here)."""
+    seq, offs = synth.random_small(400, 40, 120, p_n=0.02, seed=909)
+    m, every = 3, 4
+    comp = {"A": "T", "C": "G", "G": "C", "T": "A"}
+    freq = collections.Counter()
+    text = seq.tobytes().decode()
+    for r in range(0, len(offs) - 1, every):
+        read = text[int(offs[r]):int(offs[r + 1])].upper()
+        for q in range(len(read) - m + 1):
+            s = read[q:q + m]
+            if set(s) <= set("ACGT"):
+                rc = "".join(comp[c] for c in reversed(s))
+                freq[min(s, rc)] += 1
+    mm = sorted(_all_mmers(m), key=lambda s: (freq[s], brute.value(s)))  # ascending frequency
+    for p, first in ((0.0, mm[0]), (1.0, mm[-1]), (0.5, mm[len(mm) // 2])):
+        ranks = oracle.dfp_ranks(seq, offs, m, p=p, every=every)
+        assert sorted(ranks.tolist()) == list(range(4 ** m))
+        assert ranks[brute.value(first)] == 0
+    ranks = oracle.dfp_ranks(seq, offs, m, p=0.0, every=every)
+    assert [s for s in sorted(mm, key=lambda s: ranks[brute.value(s)])] == mm
