@@ -643,12 +643,15 @@ def main_orderings(a, rank, local):
     s_dev = torch.from_numpy(seq).cuda()
     o_dev = torch.from_numpy(offs.view(np.int64)).cuda()
     ctx = gerbil.Context(local)
-    names = ["kmc2", "lex", "cgat", "roberts", "random"]
+    variants = [("kmc2", 0, 0.5), ("lex", 1, 0.5), ("cgat", 2, 0.5), ("roberts", 3, 0.5),
+                ("random", 4, 0.5), ("dfp0", 5, 0.0), ("dfp0.5", 5, 0.5), ("dfp0.8", 5, 0.8),
+                ("dfp1", 5, 1.0)]
     out = {}
     for k, m in ((28, 6), (p["k"], p["m"])):
         nb = 65536
-        for o, name in enumerate(names):
-            bins = ctx.partition(s_dev, o_dev, k, m, nb, gerbil.default_opts(ordering=o))
+        for name, o, piv in variants:
+            bins = ctx.partition(s_dev, o_dev, k, m, nb,
+                                 gerbil.default_opts(ordering=o, dfp_pivot=piv))
             inf = bins.info()
             per = [gerbil.gerbil_bin_stats(bins.handle, b) for b in range(nb)]  # (super, bases, k-mers)
             kmers = np.array([x[2] for x in per], dtype=np.float64)

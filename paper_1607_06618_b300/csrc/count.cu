@@ -400,8 +400,7 @@ constexpr int insert_min_blocks(int W) {
 
 // STATS: the instantiation that records probe statistics (only launched while they are on).
 template <int W, int WS, bool STATS>
-__global__ void __launch_bounds__(256, insert_min_blocks(W)) insert_kernel(CountParams P) {
-  __shared__ WarpSmem S[8];
+__device__ __forceinline__ void insert_items(const CountParams& P, WarpSmem* S) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (!P.schedule) {  // fixed: warp w takes items base + w, base + w + nw, ...
     const unsigned long long nw = (unsigned long long)gridDim.x * (blockDim.x >> 5);
@@ -420,6 +419,26 @@ __global__ void __launch_bounds__(256, insert_min_blocks(W)) insert_kernel(Count
     const unsigned long long entry = __ldg(P.imap + item);
     count_item<W, WS, STATS>(P, item, entry, S[warp], lane);
     item = __shfl_sync(0xFFFFFFFFu, next, 0);
+  }
+}
+
+template <int W, int WS, bool STATS>
+__global__ void __launch_bounds__(256, insert_min_blocks(W)) insert_kernel(CountParams P) {
+  __shared__ WarpSmem S[8];
+  if constexpr (STATS) {
+    // probe statistics: summed per CTA in shared memory, added to the global histogram once
+    __shared__ unsigned long long hist[2 * PROBE_BUCKETS];
+    for (int i = threadIdx.x; i < 2 * PROBE_BUCKETS; i += blockDim.x) hist[i] = 0ull;
+    __syncthreads();
+    unsigned long long* global_hist = P.probe_hist;
+    CountParams Q = P;
+    Q.probe_hist = hist;
+    insert_items<W, WS, STATS>(Q, S);
+    __syncthreads();
+    for (int i = threadIdx.x; i < 2 * PROBE_BUCKETS; i += blockDim.x)
+      if (hist[i]) atomicAdd(global_hist + i, hist[i]);
+  } else {
+    insert_items<W, WS, STATS>(P, S);
   }
 }
 
