@@ -77,6 +77,8 @@ __global__ void boundary_kernel(const uint64_t* __restrict__ offsets, uint64_t n
 // appended with one atomic per warp, and counted into its bin.
 
 constexpr int SEG = 8;  // consecutive m-mers per thread in the key pass
+constexpr int SUPER_TILE = 2048;  // window starts per CTA
+constexpr int SUPER_WORDS = SUPER_TILE / 32 + 1;  // mask words holding a CTA's windows 0..tile
 
 __device__ __forceinline__ unsigned long long bases64(const unsigned long long* sw, int lb) {
   const int w = lb >> 5, o = 2 * (lb & 31);
@@ -328,73 +330,78 @@ __global__ void __launch_bounds__(256) supermer_kernel(SupermerParams P) {
   }
   __syncthreads();
 
-  // records: the starts among this CTA's windows 1..own, counted per mask word; room for all of
-  // the CTA's records is taken with one atomic, then every start is written (its end = the first
-  // boundary after it; a cut every L_max windows bounds the search)
+  // records: the starts among this CTA's windows 1..own, counted per mask word (an exclusive
+  // prefix over the words by warp 0); room for all of the CTA's records is taken with one
+  // atomic; then every thread takes starts r, r + 256, ... (records in window order): the word
+  // holding start r, its bit, its end (the first boundary after it; a cut every L_max windows
+  // bounds the search), its minimizer and bin
   const int own = (int)(P1 - P0);
-  const int ownw = (own >> 5) + 1;  // mask words holding windows 0..own
+  const int ownw = (own >> 5) + 1;  // mask words holding windows 0..own (<= SUPER_WORDS)
   auto own_bits = [&](int wd) -> uint32_t {
     uint32_t b = SB[wd];
-    if (wd == 0) b &= ~1u;                           // window 0 belongs to the previous CTA
+    if (wd == 0) b &= ~1u;                               // window 0 belongs to the previous CTA
     if (wd == (own >> 5)) b &= (2u << (own & 31)) - 1u;  // windows up to own
     return b;
   };
-  uint32_t mine = 0;
-  for (int wd = threadIdx.x; wd < ownw; wd += blockDim.x) mine += __popc(own_bits(wd));
-  __shared__ uint32_t s_wsum[8];
+  __shared__ uint32_t s_wpre[SUPER_WORDS + 1];
   __shared__ unsigned long long s_rbase;
-  uint32_t incl = mine;
+  if (warp == 0) {
+    uint32_t carry = 0;
+    for (int base = 0; base < ownw; base += 32) {
+      const int wd = base + lane;
+      const uint32_t c = wd < ownw ? __popc(own_bits(wd)) : 0u;
+      uint32_t incl = c;
 #pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-    if (lane >= o) incl += y;
-  }
-  if (lane == 31) s_wsum[warp] = incl;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    uint32_t acc = 0;
-    for (int x = 0; x < nwarp; ++x) {
-      const uint32_t t = s_wsum[x];
-      s_wsum[x] = acc;
-      acc += t;
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+        if (lane >= o) incl += y;
+      }
+      if (wd < ownw) s_wpre[wd] = carry + incl - c;
+      carry += __shfl_sync(0xFFFFFFFFu, incl, 31);
     }
-    s_rbase = acc ? atomicAdd(P.rec_count, (unsigned long long)acc) : 0ull;
+    if (lane == 0) {
+      s_wpre[ownw] = carry;
+      s_rbase = carry ? atomicAdd(P.rec_count, (unsigned long long)carry) : 0ull;
+    }
   }
   __syncthreads();
-  unsigned long long idx = s_rbase + s_wsum[warp] + (incl - mine);
-  for (int wd = threadIdx.x; wd < ownw; wd += blockDim.x) {
-    uint32_t bits = own_bits(wd);
-    while (bits) {
-      const int i = wd * 32 + __ffs(bits) - 1;
-      bits &= bits - 1u;
-      const int j = i + 1;
-      int end = NW;
-      for (int wj = j >> 5; wj < nbw; ++wj) {
-        const uint32_t bb = BB[wj] & (wj == (j >> 5) ? (0xFFFFFFFFu << (j & 31)) : 0xFFFFFFFFu);
-        if (bb) {
-          end = min(NW, (wj << 5) + __ffs(bb) - 1);
-          break;
-        }
-      }
-      const uint32_t nk = (uint32_t)(end - i);
-      const uint32_t h = fmix32((wmin(i) - 1u) & vmask);
-      uint32_t bin;
-      if (P.bounds) {
-        uint32_t lo = 0, hi = P.nbins - 1;  // number of split points <= h
-        while (lo < hi) {
-          const uint32_t mid = (lo + hi) >> 1;
-          if (__ldg(P.bounds + mid) <= h) lo = mid + 1; else hi = mid;
-        }
-        bin = lo;
-      } else {
-        bin = h % P.nbins;
-      }
-      atomicAdd(P.bin_nsuper + bin, 1ull);
-      atomicAdd(P.bin_nkmers + bin, (unsigned long long)nk);
-      if (idx < P.rec_cap)
-        P.rec[idx] = make_ulonglong2((unsigned long long)(O + i), ((unsigned long long)bin << 32) | nk);
-      ++idx;
+  const uint32_t total = s_wpre[ownw];
+  for (uint32_t r = threadIdx.x; r < total; r += blockDim.x) {
+    int lo = 0, hi = ownw;  // s_wpre[lo] <= r < s_wpre[hi]
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (s_wpre[mid] <= r) lo = mid; else hi = mid;
     }
+    uint32_t bits = own_bits(lo);
+    for (uint32_t n = r - s_wpre[lo]; n > 0; --n) bits &= bits - 1u;  // drop the earlier starts
+    const int i = lo * 32 + __ffs(bits) - 1;
+    const int j = i + 1;
+    int end = NW;
+    for (int wj = j >> 5; wj < nbw; ++wj) {
+      const uint32_t bb = BB[wj] & (wj == (j >> 5) ? (0xFFFFFFFFu << (j & 31)) : 0xFFFFFFFFu);
+      if (bb) {
+        end = min(NW, (wj << 5) + __ffs(bb) - 1);
+        break;
+      }
+    }
+    const uint32_t nk = (uint32_t)(end - i);
+    const uint32_t h = fmix32((wmin(i) - 1u) & vmask);
+    uint32_t bin;
+    if (P.bounds) {
+      uint32_t blo = 0, bhi = P.nbins - 1;  // number of split points <= h
+      while (blo < bhi) {
+        const uint32_t mid = (blo + bhi) >> 1;
+        if (__ldg(P.bounds + mid) <= h) blo = mid + 1; else bhi = mid;
+      }
+      bin = blo;
+    } else {
+      bin = h % P.nbins;
+    }
+    atomicAdd(P.bin_nsuper + bin, 1ull);
+    atomicAdd(P.bin_nkmers + bin, (unsigned long long)nk);
+    const unsigned long long idx = s_rbase + r;
+    if (idx < P.rec_cap)
+      P.rec[idx] = make_ulonglong2((unsigned long long)(O + i), ((unsigned long long)bin << 32) | nk);
   }
 }
 
@@ -492,6 +499,7 @@ static cudaError_t launch_supermer_m(const SupermerParams& p, uint64_t blocks, s
 
 cudaError_t launch_supermer(const SupermerParams& p, cudaStream_t st) {
   if (p.nwin == 0) return cudaSuccess;
+  if (p.tile < 32 || p.tile > SUPER_TILE) return cudaErrorInvalidValue;  // record-word staging
   const uint64_t blocks = (p.nwin + p.tile - 1) / p.tile;
   const size_t smem = supermer_smem_bytes(p.tile, p.lmax, p.k, p.m);
   switch (p.m) {
