@@ -536,6 +536,11 @@ __global__ void __launch_bounds__(256, 3) compact_kernel(CompactParams P) {
       if (take) {
         ++ndist;
         c = (uint32_t)mt;
+        if (P.zero && P.mode != 2) {  // the slot is read (v) and done with: leave it empty
+          ulonglong2* sp = reinterpret_cast<ulonglong2*>(P.arena + slot * SW);
+#pragma unroll
+          for (int i = 0; i < SW / 2; ++i) sp[i] = make_ulonglong2(0ull, 0ull);
+        }
         if (P.mode == 1) {
           unsigned long long key[W];
           from_stored<W, WS>(&v[u][1], key);

@@ -131,6 +131,7 @@ struct CompactParams {
   uint32_t* out_counts;
   unsigned long long out_cap;
   Counters* ctr;
+  int zero;                      // modes 0 and 1: zero every slot taken (the arena stays clean)
 };
 
 struct OverflowParams {

@@ -488,10 +488,16 @@ cudaError_t launch_boundary(const uint64_t* offsets, uint64_t nreads, uint64_t n
   return cudaGetLastError();
 }
 
+// The dynamic shared memory limit is raised to one fixed ceiling (the same value from every
+// host thread, so that concurrent contexts never lower it between another thread's setting
+// and launch); the launch asks for what it needs.
+constexpr int SUPER_SMEM_CEILING = 200 * 1024;
+
 template <int M>
 static cudaError_t launch_supermer_m(const SupermerParams& p, uint64_t blocks, size_t smem, cudaStream_t st) {
+  if (smem > (size_t)SUPER_SMEM_CEILING) return cudaErrorInvalidValue;
   cudaError_t e = cudaFuncSetAttribute(supermer_kernel<M>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
+                                       SUPER_SMEM_CEILING);
   if (e != cudaSuccess) return e;
   supermer_kernel<M><<<(unsigned)blocks, 256, smem, st>>>(p);
   return cudaGetLastError();
@@ -567,8 +573,7 @@ cudaError_t launch_scatter(const SupermerParams& p, unsigned long long nrec, int
   const unsigned long long per = 256ull * SCATTER_RPT;
   const unsigned blocks = (unsigned)std::min<unsigned long long>((nrec + per - 1) / per, (unsigned long long)nsm * 8);
   const size_t smem = p.nbins <= (uint32_t)SCATTER_MAX_BINS ? (size_t)p.nbins * 16 : 0;
-  cudaError_t e = cudaFuncSetAttribute(scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
+  // at most SCATTER_MAX_BINS * 16 = 32 KB: within the default limit, no attribute needed
   scatter_kernel<<<blocks, 256, smem, st>>>(p, nrec);
   return cudaGetLastError();
 }

@@ -1372,8 +1372,10 @@ static int count_impl(gerbil_ctx* ctx, const gerbil_bins* b, const std::vector<i
 
     ctx->times.calls++;
     ph_begin(ctx, PH_CLEAR, ls, capturing);
-    CKG(cudaMemsetAsync(ctx->arena, 0, arena_need, ls));
-    ctx->arena_dirty = std::max(ctx->arena_dirty, arena_need);  // tables stay in the arena
+    // only what earlier calls left non-zero is cleared (the whole dirty prefix of the arena):
+    // a successful compaction zeroes every slot it takes, so repeated batches skip this
+    if (ctx->arena_dirty) CKG(cudaMemsetAsync(ctx->arena, 0, ctx->arena_dirty, ls));
+    ctx->arena_dirty = arena_need;  // dirty until the compaction succeeds
     CKG(cudaMemsetAsync(ctx->ctr, 0, sizeof(Counters), ls));
     if (!work.empty()) {
       CKG(cudaMemcpyAsync(dwork, work_src, work_bytes, cudaMemcpyHostToDevice, ls));
@@ -1422,6 +1424,7 @@ static int count_impl(gerbil_ctx* ctx, const gerbil_bins* b, const std::vector<i
     xp.bin_ovf = bin_ovf;
     xp.min_count = min_count;
     xp.ctr = ctx->ctr;
+    xp.zero = 1;
     if (exact_out) {  // count the rows (live slots with count >= min_count), then size exactly
       xp.mode = 2;
       CKG(gerbil::launch_compact(k, xp, ctx->nsm, ls));
@@ -1563,6 +1566,9 @@ static int count_impl(gerbil_ctx* ctx, const gerbil_bins* b, const std::vector<i
     stats.table_slots = slots;
     res->n = h.out_count;
     res->stats = stats;
+    // every slot of this batch was zeroed by its compaction (mode 0 or, for the bins that
+    // spilled, mode 1), and the rest of the arena was cleared before the inserts
+    ctx->arena_dirty = 0;
     if (occ > 0 && stats.overflowed == 0) {
       ctx->ratio = (double)h.distinct / (double)occ;
       ctx->ratio_known = true;
