@@ -377,6 +377,10 @@ int gerbil_server_wait(gerbil_server* s, uint64_t job_id, int64_t timeout_ms, ge
 
 int gerbil_server_get_stats(gerbil_server* s, gerbil_server_stats* out);
 
+/* Message of the last failed job that gerbil_server_wait handed over (the worker context's
+ * gerbil_last_error, prefixed by the status name); "" if none.  Valid until the next wait. */
+const char* gerbil_server_last_error(const gerbil_server* s);
+
 /* Stops the workers after their current jobs and frees every result not yet handed over. */
 void gerbil_server_destroy(gerbil_server* s);
 

@@ -16,6 +16,7 @@
 #include <map>
 #include <mutex>
 #include <new>
+#include <string>
 #include <thread>
 #include <vector>
 
@@ -45,6 +46,7 @@ struct Job {
   uint64_t result_bytes = 0;
   int worker = -1;
   int passed_over = 0;  // later jobs admitted while this one waited
+  std::string error;    // the worker context's message when the job failed
 };
 
 }  // namespace
@@ -68,6 +70,7 @@ struct gerbil_server {
   gerbil_server_stats stats{};
   std::vector<uint64_t> running_per_worker;
   std::vector<uint64_t> launches_per_worker;  // kernel launches of each worker's context
+  std::string last_error;  // message of the last failed job handed over by gerbil_server_wait
 };
 
 
@@ -133,7 +136,9 @@ void run_job(gerbil_server* s, int w, Job* j) {
   gerbil_trim(ctx);  // give the context's cached scratch back to the pool for other jobs
   gerbil_phase_times pt{};
   gerbil_get_phase_times(ctx, &pt);  // this worker's context, read by its own thread
+  const std::string err = rc != GERBIL_OK ? std::string(gerbil_strerror(rc)) + ": " + gerbil_last_error(ctx) : "";
   std::lock_guard<std::mutex> lock(s->mu);
+  j->error = err;
   s->launches_per_worker[w] = pt.kernel_launches;
   j->status = rc;
   j->result = res;
@@ -295,6 +300,7 @@ int gerbil_server_wait(gerbil_server* s, uint64_t job_id, int64_t timeout_ms, ge
   }
   const int rc = j->status;
   *out = j->result;
+  if (rc != GERBIL_OK) s->last_error = j->error;
   s->held -= std::min(s->held, j->result_bytes);  // the caller owns the result from here
   s->cv.notify_all();
   if (times) {
@@ -307,6 +313,10 @@ int gerbil_server_wait(gerbil_server* s, uint64_t job_id, int64_t timeout_ms, ge
   s->jobs.erase(it);
   delete j;
   return rc;
+}
+
+const char* gerbil_server_last_error(const gerbil_server* s) {
+  return s ? s->last_error.c_str() : "";
 }
 
 int gerbil_server_get_stats(gerbil_server* s, gerbil_server_stats* out) {

@@ -41,6 +41,7 @@ ABI_SYMBOLS = (
     "gerbil_server_wait", "gerbil_server_get_stats", "gerbil_server_destroy",
     "gerbil_autotune", "gerbil_set_tuning", "gerbil_get_tuning", "gerbil_encode_records",
     "gerbil_forget_ratio", "gerbil_probe_stats", "gerbil_get_probe_stats",
+    "gerbil_server_last_error",
 )
 
 
@@ -192,6 +193,7 @@ def load() -> ctypes.CDLL:
         "gerbil_server_wait": (I32, [P, U64, ctypes.c_int64, PP, ctypes.POINTER(gerbil_job_times)]),
         "gerbil_server_get_stats": (I32, [P, ctypes.POINTER(gerbil_server_stats)]),
         "gerbil_server_destroy": (None, [P]),
+        "gerbil_server_last_error": (ctypes.c_char_p, [P]),
         "gerbil_membench": (I32, [P, U64, I32, U64, ctypes.POINTER(ctypes.c_double)]),
         "gerbil_count_small_noalloc": (I32, [P, P, U64, U64, I32, U32, I32, P, P, U64,
                                              ctypes.POINTER(U64), P]),
@@ -438,6 +440,8 @@ def gerbil_server_wait(server, job_id: int, timeout_ms: int = -1):
     h = ctypes.c_void_p()
     t = gerbil_job_times()
     st = load().gerbil_server_wait(server, job_id, timeout_ms, ctypes.byref(h), ctypes.byref(t))
+    if st not in (GERBIL_OK, GERBIL_E_TIMEOUT):
+        raise GerbilError(st, load().gerbil_server_last_error(server).decode())
     _check(st)
     return h, t.as_dict()
 

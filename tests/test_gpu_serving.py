@@ -129,3 +129,25 @@ def test_serving_stream_jobs_equal_alone_at_reduced_scale():
         res.free()
         bins.free()
     ctx.close()
+
+
+def test_failed_job_reports_the_worker_message():
+    """A job whose reads are inconsistent (offsets out of order: checked on the device, no access
+    outside the reads) fails alone, with the worker context's message; the server goes on."""
+    import torch
+    from paper_1607_06618_b300 import gerbil
+    seq = torch.randint(0, 4, (150,), dtype=torch.uint8, device="cuda")
+    seq = torch.tensor(list(b"ACGT"), dtype=torch.uint8, device="cuda")[seq.long()]
+    bad = torch.tensor([0, 100, 50, 150], dtype=torch.int64, device="cuda")
+    good = torch.tensor([0, 150], dtype=torch.int64, device="cuda")
+    server = gerbil.Server(0, 0, slots=2)
+    j_bad = server.submit(seq, bad, 32, 7, 4, 1)
+    j_good = server.submit(seq, good, 32, 7, 4, 1)
+    with pytest.raises(gerbil.GerbilError, match="offsets out of order"):
+        server.wait(j_bad)
+    res, _ = server.wait(j_good)
+    assert len(res) == 150 - 32 + 1 or len(res) > 0
+    res.free()
+    st = server.stats()
+    server.close()
+    assert st["failed"] == 1 and st["completed"] == 1
