@@ -437,6 +437,11 @@ def main_ours(a, world, rank, local):
         import threading
         nrow = info["emitted"]
         nw = max(1, a.e2e_workers)
+        # a second worker needs its own tables: one worker when a step's tables take more than
+        # a quarter of the device (config 4's 126 GB), where two would crowd each other
+        slot_bytes = 8 * (((2 * k + 62) // 63 + 2) & ~1)
+        if info["table_slots"] * slot_bytes > torch.cuda.get_device_properties(local).total_memory / 4:
+            nw = 1
         seq_pin = torch.from_numpy(seq).pin_memory()
         offs_pin = torch.from_numpy(offs.view(np.int64)).pin_memory()
         hs, ho = seq_pin.numpy(), offs_pin.numpy().view(np.uint64)
