@@ -44,7 +44,7 @@ def _args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
     ap.add_argument("--e2e-steps", type=int, default=20)
-    ap.add_argument("--e2e-workers", type=int, default=2,
+    ap.add_argument("--e2e-workers", type=int, default=4,
                     help="host threads (one context and stream each) driving the e2e steps")
     ap.add_argument("--per-bin-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -58,6 +58,13 @@ def _args():
     ap.add_argument("--autotune", action="store_true",
                     help="form, schedule and per-class load factors from the autotuner")
     ap.add_argument("--graph", action="store_true", help="phase two as one captured CUDA graph")
+    ap.add_argument("--ksweep", action="store_true",
+                    help="throughput against k from 32 to 479 on one long-read workload")
+    ap.add_argument("--ks", default=None, help="comma-separated k values of --ksweep (default all)")
+    ap.add_argument("--ksweep-genome", type=int, default=10_000_000,
+                    help="genome length of the --ksweep workload (bases)")
+    ap.add_argument("--ksweep-windows", type=int, default=400_000,
+                    help="k-mer windows of the oracle's sample at every k of --ksweep")
     ap.add_argument("--orderings", action="store_true",
                     help="compare the minimizer orderings (super-mers vs largest bin) instead")
     ap.add_argument("--serving-jobs", type=int, default=48,
@@ -437,11 +444,11 @@ def main_ours(a, world, rank, local):
         import threading
         nrow = info["emitted"]
         nw = max(1, a.e2e_workers)
-        # a second worker needs its own tables: one worker when a step's tables take more than
-        # a quarter of the device (config 4's 126 GB), where two would crowd each other
+        # every worker holds tables of its own: no more workers than sets of tables fit in half
+        # the device (one for the 126 GB tables of the long-read workload)
         slot_bytes = 8 * (((2 * k + 62) // 63 + 2) & ~1)
-        if info["table_slots"] * slot_bytes > torch.cuda.get_device_properties(local).total_memory / 4:
-            nw = 1
+        half = torch.cuda.get_device_properties(local).total_memory // 2
+        nw = max(1, min(nw, half // max(1, info["table_slots"] * slot_bytes)))
         seq_pin = torch.from_numpy(seq).pin_memory()
         offs_pin = torch.from_numpy(offs.view(np.int64)).pin_memory()
         hs, ho = seq_pin.numpy(), offs_pin.numpy().view(np.uint64)
@@ -673,11 +680,120 @@ def main_orderings(a, rank, local):
     return 0
 
 
+KSWEEP = (32, 48, 65, 99, 127, 150, 200, 256, 320, 400, 479)
+
+
+def main_ksweep(a, rank, local):
+    """Throughput against k (Sec. 4 finds the GPU speed-up of the paper's hybrid counter gone
+    beyond k = 150, because fewer wider table entries fit in the parallel window scan).
+    One long-read workload holds every k of the sweep: a 10 Mbp uniform genome (seed 6001;
+    --ksweep-genome changes its length), 20x of 1000 bp reads from both strands with 0.2%
+    substitutions (seed 6002), m = 11, 512 bins, min count 2.  Per k: the whole step on the GPU (event-timed, phase split), the
+    insert kernel's byte model and HBM fraction, and the oracle on one core over a bounded
+    sample, whose reads the GPU also counts for a bit-exact check."""
+    import torch
+    import oracle
+    from paper_1607_06618_b300 import gerbil, synth
+    torch.cuda.set_device(local)
+    G, L = a.ksweep_genome, 1000
+    gen = synth.t_genome(G, 6001, "cuda")
+    s_dev, o_dev = synth.t_sampled_reads(gen, 20 * G // L, L, 0.002, 6002)
+    del gen
+    seq, offs = s_dev.cpu().numpy(), o_dev.cpu().numpy().view(np.uint64)
+    m, nbins, mc = 11, 512, 2
+    stream = torch.cuda.current_stream()
+    ctx = gerbil.Context(local, stream=stream.cuda_stream)
+    opts = gerbil.default_opts()
+    hbm, peak_kind = _peaks()
+    rows = []
+    clocks = Clocks(local)
+    for k in (tuple(int(x) for x in a.ks.split(",")) if a.ks else KSWEEP):
+        W = (2 * k + 63) // 64
+        WS = (2 * k + 62) // 63
+        info = {}
+
+        def step(record=False):
+            bins = ctx.partition(s_dev, o_dev, k, m, nbins, opts)
+            res = ctx.count_batch(bins, None, k, mc, opts)
+            if record:
+                info.update(res.info()[2])
+                info["n_supermers"] = bins.info()["n_supermers"]
+            res.free()
+            bins.free()
+
+        for i in range(max(3, a.warmup)):
+            step(record=(i == 0))
+        occ = info["occurrences"]
+        n_bases = occ + info["n_supermers"] * (k - 1)
+        ctx.profile(True)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(a.steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / a.steps
+        ph = ctx.phase_times()
+        ctx.profile(False)
+        ins_ms = ph["insert_ms"] / max(1, ph["insert_launches"])
+        insert_bytes, _ = _model_bytes(occ, n_bases, info["distinct"], info["emitted"], W)
+
+        # the oracle on the first reads holding about --ksweep-windows windows (timed at the
+        # workload's min count); the GPU counts the same reads and must agree row for row with
+        # every k-mer of them (min count 1: the sample is too thin for repeats)
+        n = _reads_for_windows(offs, k, a.ksweep_windows)
+        ss, so = seq[: int(offs[n])], offs[: n + 1]
+        t0 = time.perf_counter()
+        oracle.count(ss, so, k, canonical=True, min_count=mc)
+        dt = time.perf_counter() - t0
+        occ_s = oracle.windows(ss, so, k)
+        wk, wc = oracle.count(ss, so, k, canonical=True, min_count=1)
+        bins = ctx.partition(ss, so, k, m, nbins, opts)
+        res = ctx.count_batch(bins, None, k, 1, opts)
+        gk, gc = res.to_host()
+        res.free()
+        bins.free()
+        gk = np.asarray(gk, dtype=np.uint64).reshape(len(gc), W)
+        order = np.lexsort(gk.T[::-1]) if len(gc) else np.zeros(0, np.int64)
+        same = (len(gc) == len(wc)
+                and np.array_equal(gk[order], np.asarray(wk, np.uint64).reshape(len(wc), W))
+                and np.array_equal(np.asarray(gc, np.uint64)[order], np.asarray(wc, np.uint64)))
+        if not same:
+            raise SystemExit("k=%d: GPU result differs from the oracle on the sample" % k)
+        slot = 8 * ((WS + 2) & ~1)
+        rows.append({
+            "k": k, "W": W, "slot_bytes": slot, "slots_per_128B_line": round(128 / slot, 3),
+            "occurrences": occ, "distinct": info["distinct"], "emitted": info["emitted"],
+            "gpu_kmers_per_s": occ / (ms / 1000.0), "ms_per_step": ms,
+            "phase_ms": {key[:-3]: ph[key] / a.steps for key in
+                         ("encode_ms", "supermer_ms", "clear_ms", "insert_ms", "compact_ms",
+                          "overflow_ms") if key in ph},
+            "insert_bytes_per_occ": insert_bytes / occ,
+            "insert_hbm_frac": insert_bytes / (ins_ms / 1000.0) / 1e9 / hbm,
+            "oracle_kmers_per_s": occ_s / dt, "oracle_sample_windows": occ_s,
+            "gpu_over_oracle": (occ / (ms / 1000.0)) / (occ_s / dt), "sample_bit_exact": same,
+            "sample_rows_checked": len(wc)})
+        torch.cuda.empty_cache()
+    ck = clocks.stop()
+    ctx.close()
+    if rank == 0:
+        print(json.dumps({"experiment": "throughput against k (Sec. 4, GPU speed-up beyond k = 150)",
+                          "workload": "genome%gM-1000bp-20x, 0.2%% substitutions, m=11, 512 "
+                                      "bins, min count 2" % (G / 1e6), "steps": a.steps,
+                          "hbm_peak_gbs": hbm,
+                          "peak_kind": peak_kind, "oracle_cores": 1, "clocks": ck,
+                          "results": rows}), flush=True)
+    return 0
+
+
 def main():
     a = _args()
     world, rank, local = _dist()
     if a.orderings:
         return main_orderings(a, rank, local)
+    if a.ksweep:
+        return main_ksweep(a, rank, local)
     if a.workload == SERVING_WORKLOAD:
         if a.impl == "reference":
             if rank == 0:

@@ -383,19 +383,28 @@ __device__ __forceinline__ void count_item(const CountParams& P, unsigned long l
 // current one runs), so the bins in flight at any moment are few and their tables stay hot in
 // L2; or (schedule 0) each warp strides over the items.  Launched with as many CTAs as fit on
 // the GPU (persistent) or one warp per item.
+// Resident CTAs per SM that the register allocation is held to, per key width (measured on
+// k = 65, 99 and a 1000 bp read set at k = 150..479).  A cap pays while its spills stay small
+// (about 64 bytes a thread): 5 for keys of up to three words, 4 for four or five, 3 for six or
+// seven, 2 up to fourteen; fifteen-word keys run uncapped (158 registers), since two CTAs would
+// spill 380 bytes a thread.
 #ifndef GERBIL_MINB_SMALL
 #define GERBIL_MINB_SMALL 5
 #endif
 #ifndef GERBIL_MINB_MID
 #define GERBIL_MINB_MID 4
 #endif
-#ifndef GERBIL_MINB_LARGE
-#define GERBIL_MINB_LARGE 1
+#ifndef GERBIL_MINB_WIDE
+#define GERBIL_MINB_WIDE 3
 #endif
-// Resident CTAs per SM that the register allocation is held to (measured: 5 for keys of up to
-// three words, 4 for four or five).
+#ifndef GERBIL_MINB_XWIDE
+#define GERBIL_MINB_XWIDE 2
+#endif
 constexpr int insert_min_blocks(int W) {
-  return W <= 3 ? GERBIL_MINB_SMALL : (W <= 5 ? GERBIL_MINB_MID : GERBIL_MINB_LARGE);
+  return W <= 3 ? GERBIL_MINB_SMALL
+                : W <= 5 ? GERBIL_MINB_MID
+                : W <= 7 ? GERBIL_MINB_WIDE
+                : W <= 14 ? GERBIL_MINB_XWIDE : 1;
 }
 
 // STATS: the instantiation that records probe statistics (only launched while they are on).
