@@ -43,7 +43,7 @@ def _args():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
-    ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--e2e-steps", type=int, default=80)
     ap.add_argument("--e2e-workers", type=int, default=4,
                     help="host threads (one context and stream each) driving the e2e steps")
     ap.add_argument("--per-bin-steps", type=int, default=3)

@@ -431,8 +431,12 @@ __device__ __forceinline__ void insert_items(const CountParams& P, WarpSmem* S) 
   }
 }
 
-template <int W, int WS, bool STATS>
-__global__ void __launch_bounds__(256, insert_min_blocks(W)) insert_kernel(CountParams P) {
+// CAP = false: the same kernel without the register cap, for keys of six or more words whose
+// bins' tables average more than the L2 cache (CountParams::wide_tables).  Their probes go to
+// HBM whatever the warps in flight, so the cap's spills cost time without hiding any more
+// latency (measured: k = 200 with 126 GB of tables, 71.1 ms uncapped against 74.1 ms capped).
+template <int W, int WS, bool STATS, bool CAP = true>
+__global__ void __launch_bounds__(256, CAP ? insert_min_blocks(W) : 1) insert_kernel(CountParams P) {
   __shared__ WarpSmem S[8];
   if constexpr (STATS) {
     // probe statistics: summed per CTA in shared memory, added to the global histogram once
@@ -890,26 +894,40 @@ cudaError_t launch_item_map(const CountParams& p, cudaStream_t st) {
 
 // persistent: as many CTAs as are resident at once (occupancy query), each warp striding over
 // the items; otherwise one warp per item.
+template <int w, int ws, bool CAP>
+static cudaError_t launch_insert_as(const CountParams& p, unsigned long long need, int persistent,
+                                    int nsm, cudaStream_t st) {
+  unsigned long long grid = need;
+  if (persistent) {
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, insert_kernel<w, ws, false, CAP>,
+                                                                  COUNT_THREADS, 0);
+    if (e != cudaSuccess) return e;
+    grid = std::min<unsigned long long>(need, (unsigned long long)nsm * std::max(1, per_sm));
+  }
+  // probe statistics always use the capped form (they time nothing)
+  if (p.probe_hist) insert_kernel<w, ws, true><<<(unsigned)grid, COUNT_THREADS, 0, st>>>(p);
+  else insert_kernel<w, ws, false, CAP><<<(unsigned)grid, COUNT_THREADS, 0, st>>>(p);
+  return cudaGetLastError();
+}
+
+template <int w, int ws>
+static cudaError_t launch_insert_w(const CountParams& p, unsigned long long need, int persistent,
+                                   int nsm, cudaStream_t st) {
+  if constexpr (w >= 6 && insert_min_blocks(w) > 1) {
+    if (p.wide_tables && !p.probe_hist) return launch_insert_as<w, ws, false>(p, need, persistent, nsm, st);
+  }
+  return launch_insert_as<w, ws, true>(p, need, persistent, nsm, st);
+}
+
 cudaError_t launch_insert(int k, const CountParams& p, int persistent, int nsm, cudaStream_t st) {
   const unsigned long long need = (p.nitems - p.item_base + 7) / 8;
   if (need == 0) return cudaSuccess;
   const int W = (2 * k + 63) / 64, WS = stored_words(k);
-#define L_INSERT(w, ws)                                                                          \
-  {                                                                                              \
-    unsigned long long grid = need;                                                              \
-    if (persistent) {                                                                            \
-      int per_sm = 0;                                                                            \
-      cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, insert_kernel<w, ws, false>, \
-                                                                    COUNT_THREADS, 0);           \
-      if (e != cudaSuccess) return e;                                                            \
-      grid = std::min<unsigned long long>(need, (unsigned long long)nsm * std::max(1, per_sm));  \
-    }                                                                                            \
-    if (p.probe_hist) insert_kernel<w, ws, true><<<(unsigned)grid, COUNT_THREADS, 0, st>>>(p);   \
-    else insert_kernel<w, ws, false><<<(unsigned)grid, COUNT_THREADS, 0, st>>>(p);               \
-  }
+#define L_INSERT(w, ws) return launch_insert_w<w, ws>(p, need, persistent, nsm, st)
   GERBIL_KEY_SWITCH(W, WS, L_INSERT)
 #undef L_INSERT
-  return cudaGetLastError();
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_compact(int k, const CompactParams& p, int nsm, cudaStream_t st) {

@@ -93,6 +93,9 @@ struct CountParams {
   Counters* ctr;
   // probe statistics (NULL: off): per placed k-mer, slots read and 128-byte lines touched
   unsigned long long* probe_hist;  // [2][PROBE_BUCKETS]
+  // 1: the bins' tables average more than the L2 cache (keys of six or more words then run the
+  // insert kernel without its register cap)
+  int wide_tables;
 };
 
 // Probe histogram buckets: [0, 32) = 1..32 probes, 32 = more, 33 = sent to the overflow area.

@@ -725,6 +725,15 @@ static Sizing make_sizing(const gerbil_ctx* ctx, const gerbil_opts& o, int k) {
 static const int FUSED_FALLBACK = -1;
 static const int LAG = 5;  // bins between a bin's inserts and its compaction in the queue
 
+// 1 when the bins' tables average more than the L2 cache: their probes then go to HBM however
+// many warps are in flight, and the insert kernel for wide keys runs without its register cap.
+static int tables_beyond_l2(const gerbil_ctx* ctx, const std::vector<BinWork>& work, int SW) {
+  if (work.empty()) return 0;
+  unsigned long long slots = 0;
+  for (const BinWork& w : work) slots += w.cap;
+  return slots * (unsigned long long)SW * 8ull > (unsigned long long)ctx->l2_bytes * work.size() ? 1 : 0;
+}
+
 static int count_fused(gerbil_ctx* ctx, const gerbil_bins* b, const std::vector<int32_t>& list,
                        int k, uint32_t min_count, const gerbil_opts& opts, double ratio,
                        const Sizing& sz, uint32_t theta, uint32_t spin_limit, gerbil_counts** out) {
@@ -1059,6 +1068,7 @@ static int count_waves(gerbil_ctx* ctx, const gerbil_bins* b, const std::vector<
   cp.ctr = ctx->ctr;
   cp.probe_hist = ctx->probe_hist;
   cp.schedule = opts.schedule;
+  cp.wide_tables = tables_beyond_l2(ctx, work, SW);
   if (items) {
     cp.nitems = items;
     CKW(gerbil::launch_item_map(cp, st));
@@ -1403,6 +1413,7 @@ static int count_impl(gerbil_ctx* ctx, const gerbil_bins* b, const std::vector<i
     cp.ctr = ctx->ctr;
     cp.probe_hist = ctx->probe_hist;
     cp.schedule = opts.schedule;
+    cp.wide_tables = tables_beyond_l2(ctx, work, gerbil::slot_words_for_k(k));
     if (items) {
       CKG(gerbil::launch_item_map(cp, ls));  // preparation: timed with the clears
       ctx->times.kernel_launches++;

@@ -136,6 +136,21 @@ def test_count_matches_oracle_all_word_counts(g, k):
         assert_same_rows(got, oracle.count(seq, offs, k, canonical=True, min_count=mc))
 
 
+# keys of six or more words in one table larger than the L2 cache: the insert kernel's form
+# without the register cap
+@pytest.mark.parametrize("k", [200, 400])
+def test_count_wide_keys_tables_beyond_l2(g, k):
+    gerbil, ctx, torch = g
+    seq, offs = synth.uniform_reads(2500, 1000, 0.0, seed=7000 + k)
+    seq = np.concatenate([seq, seq[: int(offs[300])]])  # 300 reads twice: counts of 2
+    offs = np.concatenate([offs, offs[1:301] + offs[-1]])
+    ctx.forget_ratio()
+    got, st = _gpu_count(g, seq, offs, k, 11, 1, 1)
+    slot = 8 * (((2 * k + 62) // 63 + 2) & ~1)
+    assert st["table_slots"] * slot > torch.cuda.get_device_properties(0).L2_cache_size
+    assert_same_rows(got, oracle.count(seq, offs, k, canonical=True, min_count=1))
+
+
 def test_count_config1_full_batch_grid_and_per_bin(g):
     seq, offs, p = synth.workload("uniform-20k-k32")
     want = oracle.count(seq, offs, p["k"], min_count=1)
