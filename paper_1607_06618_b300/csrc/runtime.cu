@@ -1580,7 +1580,9 @@ static int count_impl(gerbil_ctx* ctx, const gerbil_bins* b, const std::vector<i
     // every slot of this batch was zeroed by its compaction (mode 0 or, for the bins that
     // spilled, mode 1), and the rest of the arena was cleared before the inserts
     ctx->arena_dirty = 0;
-    if (occ > 0 && stats.overflowed == 0) {
+    // the distinct count is exact after a spill too (deferred bins are counted by their merge,
+    // overflow-only keys by the overflow emit), so a batch that spilled corrects the ratio
+    if (occ > 0) {
       ctx->ratio = (double)h.distinct / (double)occ;
       ctx->ratio_known = true;
     }

@@ -137,3 +137,38 @@ def test_probe_statistics_account_for_every_kmer(data):
     slots, lines = ctx.get_probe_stats()
     assert int(slots[33]) == st["overflowed"] > 0 and int(slots[:33].sum()) + int(slots[33]) == occ
     ctx.probe_stats(False)
+
+
+def test_ratio_learned_from_a_batch_that_overflowed(data):
+    """Sec. 3.4 sizing: a ratio learned on a repetitive input sizes the tables of a more diverse
+    one too small; that batch spills (and stays exact), and the ratio it measured sizes the
+    next batch, which must not spill again."""
+    gerbil, ctx, _, _ = data
+    import torch
+    rep, roffs = synth.uniform_reads(500, 150, 0.0, seed=7301)
+    rep = np.tile(rep, 8)  # every read 8 times: about 1/8 of the k-mers distinct
+    roffs = np.arange(8 * 500 + 1, dtype=np.uint64) * 150
+    uni, uoffs = synth.uniform_reads(4000, 150, 0.0, seed=7302)  # nearly all distinct
+    want = oracle.count(uni, uoffs, 32, min_count=1)
+    opts = gerbil.default_opts(overflow_slots=1 << 24)
+    ctx.forget_ratio()
+
+    def count(seq, offs):
+        s = torch.from_numpy(seq).cuda()
+        o = torch.from_numpy(offs.view(np.int64)).cuda()
+        bins = ctx.partition(s, o, 32, 7, 16, opts)
+        res = ctx.count_batch(bins, None, 32, 1, opts)
+        got, st = res.to_host(), res.info()[2]
+        res.free()
+        bins.free()
+        return got, st
+
+    _, st = count(rep, roffs)
+    assert st["distinct"] * 6 < st["occurrences"]
+    got, st = count(uni, uoffs)
+    assert st["overflowed"] > 0 and st["retries"] == 0
+    assert_same_rows(got, want)
+    got, st = count(uni, uoffs)
+    assert st["overflowed"] == 0
+    assert_same_rows(got, want)
+    ctx.forget_ratio()
