@@ -104,7 +104,8 @@ def _digest(res):
 def test_serving_stream_jobs_equal_alone_at_reduced_scale():
     """The first jobs of the Poisson serving stream (genome and reads scaled by 1/50), submitted
     at once to a server whose budget admits a few at a time: each job's rows in the mix have the
-    digest of the same job run alone (SURVEY config 5 parity, tolerance 0)."""
+    digest of the same job run alone (a job's result must not depend on what runs beside it:
+    tolerance 0)."""
     import torch
     from paper_1607_06618_b300 import gerbil
     jobs = synth.serving_jobs(10)
