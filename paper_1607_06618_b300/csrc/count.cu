@@ -185,6 +185,11 @@ struct WarpSmem {
 // new base's complement on top.  Only the lane's first k-mer and the first k-mer of every new
 // super-mer are cut from the packed words in full.
 constexpr int KPL = ITEM_KMERS / 32;
+// Key widths whose reverse complement is taken afresh for every k-mer instead of rolled with
+// it: where dropping it from the registers live during the probes buys one more CTA per SM
+// (measured: 8 and 9 words run 3 CTAs instead of 2, k = 256 insert 8.34 -> 7.66 ms; 15 words
+// run 2 instead of 1, k = 479 13.26 -> 10.72 ms; for 10-14 words it bought none and cost 3%).
+__host__ __device__ constexpr bool rc_fresh(int W) { return W == 8 || W == 9 || W == 15; }
 
 template <int W, int WS, bool STATS = false>
 __device__ __forceinline__ void insert_item(const CountParams& P, uint32_t wi, const BinWork& wk,
@@ -230,6 +235,7 @@ __device__ __forceinline__ void insert_item(const CountParams& P, uint32_t wi, c
   uint32_t tagw = 0, s = 0, t = 0, spins = 0;
   uint32_t j = ja;
   bool busy = false;
+  constexpr bool ROLL_RC = !rc_fresh(W);
 #pragma unroll 1
   for (;;) {
     if (!busy) {
@@ -248,7 +254,7 @@ __device__ __forceinline__ void insert_item(const CountParams& P, uint32_t wi, c
         send = (sidx + 1 < ns) ? S.koff[sidx + 1] : 0xFFFFFFFFu;
         pos = S.pos[sidx] + (j - S.koff[sidx]);
         load_kmer<W>(P.packed, pos, k, fwd);
-        revcomp<W>(fwd, k, rc);
+        if constexpr (ROLL_RC) revcomp<W>(fwd, k, rc);
       } else {  // roll by one base
         const unsigned long long q = pos + (unsigned long long)k;  // the new last base
         const unsigned long long b = (__ldg(P.packed + (q >> 5)) >> (62 - 2 * (int)(q & 31))) & 3ull;
@@ -256,11 +262,16 @@ __device__ __forceinline__ void insert_item(const CountParams& P, uint32_t wi, c
         for (int u = 0; u < W - 1; ++u) fwd[u] = (fwd[u] << 2) | (fwd[u + 1] >> 62);
         fwd[W - 1] = (fwd[W - 1] << 2) | b;
         fwd[0] &= mask0;
+        if constexpr (ROLL_RC) {
 #pragma unroll
-        for (int u = W - 1; u >= 1; --u) rc[u] = (rc[u] >> 2) | (rc[u - 1] << 62);
-        rc[0] = (rc[0] >> 2) | ((3ull - b) << (2 * nb0 - 2));
+          for (int u = W - 1; u >= 1; --u) rc[u] = (rc[u] >> 2) | (rc[u - 1] << 62);
+          rc[0] = (rc[0] >> 2) | ((3ull - b) << (2 * nb0 - 2));
+        }
         ++pos;
       }
+      // the widths of rc_fresh take the reverse complement afresh: it is then dead while the
+      // k-mer is probed
+      if constexpr (!ROLL_RC) revcomp<W>(fwd, k, rc);
       unsigned long long key[W];
       const bool use_rc = P.canonical && key_less<W>(rc, fwd);
 #pragma unroll
@@ -385,9 +396,9 @@ __device__ __forceinline__ void count_item(const CountParams& P, unsigned long l
 // the GPU (persistent) or one warp per item.
 // Resident CTAs per SM that the register allocation is held to, per key width (measured on
 // k = 65, 99 and a 1000 bp read set at k = 150..479).  A cap pays while its spills stay small
-// (about 64 bytes a thread): 5 for keys of up to three words, 4 for four or five, 3 for six or
-// seven, 2 up to fourteen; fifteen-word keys run uncapped (158 registers), since two CTAs would
-// spill 380 bytes a thread.
+// (about 64 bytes a thread): 5 for keys of up to three words, 4 for four or five, 3 for six to
+// nine (eight and nine with the reverse complement taken afresh), 2 from ten words on (fifteen
+// with it taken afresh: 128 registers, no spills).
 #ifndef GERBIL_MINB_SMALL
 #define GERBIL_MINB_SMALL 5
 #endif
@@ -403,8 +414,7 @@ __device__ __forceinline__ void count_item(const CountParams& P, unsigned long l
 constexpr int insert_min_blocks(int W) {
   return W <= 3 ? GERBIL_MINB_SMALL
                 : W <= 5 ? GERBIL_MINB_MID
-                : W <= 7 ? GERBIL_MINB_WIDE
-                : W <= 14 ? GERBIL_MINB_XWIDE : 1;
+                : W <= 9 ? GERBIL_MINB_WIDE : GERBIL_MINB_XWIDE;
 }
 
 // STATS: the instantiation that records probe statistics (only launched while they are on).
