@@ -138,7 +138,7 @@ def test_count_matches_oracle_all_word_counts(g, k):
 
 # keys of six or more words in one table larger than the L2 cache: the insert kernel's form
 # without the register cap
-@pytest.mark.parametrize("k", [200, 400])
+@pytest.mark.parametrize("k", [200, 400, 479])
 def test_count_wide_keys_tables_beyond_l2(g, k):
     gerbil, ctx, torch = g
     seq, offs = synth.uniform_reads(2500, 1000, 0.0, seed=7000 + k)
