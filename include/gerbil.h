@@ -110,8 +110,8 @@ typedef struct gerbil_opts {
                                   runs are vanishingly rare, so the overflow area stays empty) */
   float load_factor;           /* target table load (default 0.5) */
   float distinct_ratio;        /* expected distinct/occurrences per bin for table sizing
-                                  (Sec. 3.4 "Estimating table sizes"); 0: use the ratio the
-                                  context measured on earlier calls (1.0 at first) */
+                                  (Sec. 3.4 "Estimating table sizes"); 0: 1.25 x the ratio
+                                  the context measured on its last batch (1.0 at first) */
   uint32_t overflow_slots;     /* capacity of the overflow area in k-mers; 0: automatic */
   int32_t persistent;          /* 1 (default): the insert kernel runs as many CTAs as fit on
                                   the GPU at once, each warp striding over the work items of
@@ -210,9 +210,10 @@ int gerbil_create(gerbil_ctx** out, int device, uint64_t hbm_budget_bytes, void*
 
 /* Forgets the distinct/occurrence ratio the context learned from earlier counts (Sec. 3.4
  * adjusts it at run time within one input).  Call it before counting an unrelated input on the
- * same context: a ratio learned on a highly repetitive input would size the next input's tables
- * far too small (still exact, through overflow retries, but slow).  The next batch of more than
- * 32 bins then samples every 16th bin first.  Errors: E_INVAL. */
+ * same context: a ratio learned on a highly repetitive input sizes the next input's first
+ * batch far too small (still exact, through the overflow path, but slow; that batch's ratio then
+ * sizes the following ones).  The next batch of more than 32 bins then samples every 16th bin
+ * first.  Errors: E_INVAL. */
 int gerbil_forget_ratio(gerbil_ctx* ctx);
 
 /* Probe statistics (Sec. 3.3 reports, for one-by-one and for 128-byte-window probing, the share
