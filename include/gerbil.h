@@ -402,6 +402,15 @@ int gerbil_set_tuning(gerbil_ctx* ctx, int k, const gerbil_tuning* t);
 /* Reads the settings held for the key width of k.  Errors: E_INVAL, E_STATE (none held). */
 int gerbil_get_tuning(const gerbil_ctx* ctx, int k, gerbil_tuning* out);
 
+/* Self-test of the bounded device waits (the paper has no counterpart).  Every wait in the
+ * kernels is bounded, so that a dependency that never arrives ends in an error status rather
+ * than a hung GPU.  This call launches one warp that waits, through the same helper as the fused
+ * phase-two kernel's work-queue waits, for a device flag that nothing sets.  After wait_ns
+ * nanoseconds (0 < wait_ns <= 1e10) the wait runs out and the kernel records it and returns.
+ * The expected result is GERBIL_E_TIMEOUT; the context stays usable.
+ * Errors: E_INVAL, E_NOMEM, E_CUDA, E_STATE (the wait ended without running out). */
+int gerbil_wait_selftest(gerbil_ctx* ctx, uint64_t wait_ns);
+
 /* Memory-throughput probe (the paper has no counterpart; a measurement helper for the
  * roofline of the insert kernel).  Runs one kernel in which every thread performs per_thread
  * operations at pseudo-random 32-byte slots of a device array of `bytes` bytes, allocated from

@@ -660,6 +660,19 @@ __device__ __forceinline__ void warp_wait_at_least(const uint32_t* ctr, uint32_t
   __syncwarp();
 }
 
+// Self-test of the bounded wait above: one warp waits for a flag that nothing sets, so the
+// wait runs out after wait_ns, records ERR_QUEUE and the kernel returns.
+__global__ void __launch_bounds__(32) wait_selftest_kernel(const uint32_t* flag,
+                                                          unsigned long long wait_ns, Counters* c) {
+  warp_wait_at_least(flag, 1u, wait_ns, c, (int)(threadIdx.x & 31));
+}
+
+cudaError_t launch_wait_selftest(const uint32_t* flag, unsigned long long wait_ns, Counters* c,
+                                 cudaStream_t st) {
+  wait_selftest_kernel<<<1, 32, 0, st>>>(flag, wait_ns, c);
+  return cudaGetLastError();
+}
+
 // Every lane makes its writes visible, then lane 0 counts the task as done.
 __device__ __forceinline__ void warp_signal(uint32_t* ctr, int lane) {
   __threadfence();

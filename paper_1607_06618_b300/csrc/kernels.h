@@ -158,6 +158,9 @@ cudaError_t launch_item_map(const CountParams& p, cudaStream_t st);
 cudaError_t launch_task_map(const FusedParams& p, cudaStream_t st);
 cudaError_t launch_fused(int k, const FusedParams& p, int nsm, cudaStream_t st);
 cudaError_t launch_insert(int k, const CountParams& p, int persistent, int nsm, cudaStream_t st);
+// one warp waits (bounded by wait_ns) for *flag >= 1, which nothing sets: records ERR_QUEUE
+cudaError_t launch_wait_selftest(const uint32_t* flag, unsigned long long wait_ns, Counters* c,
+                                 cudaStream_t st);
 cudaError_t launch_compact(int k, const CompactParams& p, int nsm, cudaStream_t st);
 cudaError_t launch_overflow_insert(int k, const OverflowParams& p, int nsm, cudaStream_t st);
 cudaError_t launch_overflow_emit(int k, const OverflowParams& p, int nsm, cudaStream_t st);

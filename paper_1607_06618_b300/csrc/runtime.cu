@@ -341,6 +341,23 @@ int gerbil_forget_ratio(gerbil_ctx* ctx) {
   return GERBIL_OK;
 }
 
+int gerbil_wait_selftest(gerbil_ctx* ctx, uint64_t wait_ns) {
+  if (!ctx || wait_ns == 0 || wait_ns > 10000000000ull) return GERBIL_E_INVAL;
+  CK(cudaSetDevice(ctx->device));
+  void* flag = nullptr;
+  int rc = dev_alloc(ctx, &flag, 256);
+  if (rc) return rc;
+  cudaError_t e = cudaMemsetAsync(flag, 0, 256, ctx->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(ctx->ctr, 0, sizeof(Counters), ctx->stream);
+  if (e == cudaSuccess) e = gerbil::launch_wait_selftest((const uint32_t*)flag, wait_ns, ctx->ctr, ctx->stream);
+  if (e == cudaSuccess) ctx->times.kernel_launches++;
+  rc = (e == cudaSuccess) ? read_counters(ctx) : fail(ctx, GERBIL_E_CUDA, cudaGetErrorString(e));
+  dev_free(ctx, flag, 256);
+  if (rc) return rc;
+  if (ctx->hctr->err & gerbil::ERR_QUEUE) return fail(ctx, GERBIL_E_TIMEOUT, "self-test wait ran out");
+  return fail(ctx, GERBIL_E_STATE, "self-test wait ended without running out");
+}
+
 int gerbil_trim(gerbil_ctx* ctx) {
   if (!ctx) return GERBIL_E_INVAL;
   CK(cudaSetDevice(ctx->device));

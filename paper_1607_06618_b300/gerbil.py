@@ -32,7 +32,7 @@ GERBIL_ORDER_LEX = 1
 
 # every symbol the header declares (checked by tests/test_abi.py)
 ABI_SYMBOLS = (
-    "gerbil_opts_default", "gerbil_strerror", "gerbil_last_error", "gerbil_create",
+    "gerbil_wait_selftest", "gerbil_opts_default", "gerbil_strerror", "gerbil_last_error", "gerbil_create",
     "gerbil_destroy", "gerbil_partition", "gerbil_bins_info", "gerbil_bin_stats",
     "gerbil_bins_export", "gerbil_bins_free", "gerbil_count", "gerbil_count_batch",
     "gerbil_counts_info", "gerbil_counts_view", "gerbil_counts_to_host", "gerbil_counts_free",
@@ -195,6 +195,7 @@ def load() -> ctypes.CDLL:
         "gerbil_server_destroy": (None, [P]),
         "gerbil_server_last_error": (ctypes.c_char_p, [P]),
         "gerbil_membench": (I32, [P, U64, I32, U64, ctypes.POINTER(ctypes.c_double)]),
+        "gerbil_wait_selftest": (I32, [P, U64]),
         "gerbil_count_small_noalloc": (I32, [P, P, U64, U64, I32, U32, I32, P, P, U64,
                                              ctypes.POINTER(U64), P]),
         "gerbil_get_phase_times": (I32, [P, ctypes.POINTER(gerbil_phase_times)]),
@@ -405,6 +406,11 @@ def gerbil_encode_records(counts, k: int, out=None, cap: int = 0, out_on_device:
     nb = ctypes.c_uint64()
     _check(load().gerbil_encode_records(counts, k, out, cap, out_on_device, ctypes.byref(nb)))
     return nb.value
+
+
+def gerbil_wait_selftest(ctx, wait_ns: int) -> int:
+    """Status of one bounded wait on a flag that nothing sets (GERBIL_E_TIMEOUT expected)."""
+    return load().gerbil_wait_selftest(ctx, wait_ns)
 
 
 def gerbil_trim(ctx):

@@ -307,3 +307,17 @@ def test_partition_dfp_ordering_matches_oracle(g, k, m, p, every):
     ex, _, _ = _gpu_bins(g, seq, offs, k, m, 29, ordering=5, dfp_pivot=p, dfp_sample=every)
     want = oracle.partition(seq, offs, k, m, 29, ordering=5, dfp_p=p, dfp_every=every)
     assert _rows(ex) == _rows(want)
+
+
+def test_bounded_wait_runs_out_and_context_stays_usable(g):
+    """Every device wait is bounded: a wait on a flag that nothing sets ends after its limit
+    with GERBIL_E_TIMEOUT, and the same context counts exactly afterwards."""
+    gerbil, ctx, torch = g
+    import time
+    t0 = time.perf_counter()
+    assert gerbil.gerbil_wait_selftest(ctx.handle, 50_000_000) == gerbil.GERBIL_E_TIMEOUT
+    assert 0.04 < time.perf_counter() - t0 < 5.0
+    assert gerbil.gerbil_wait_selftest(ctx.handle, 0) == gerbil.GERBIL_E_INVAL
+    seq, offs = synth.random_small(50, 40, 120, p_n=0.01, seed=77)
+    got, _ = _gpu_count(g, seq, offs, 31, 7, 8, 1)
+    assert_same_rows(got, oracle.count(seq, offs, 31))
