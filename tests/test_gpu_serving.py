@@ -5,7 +5,7 @@ import pytest
 
 import oracle
 from paper_1607_06618_b300 import synth
-from tests._util import assert_same_rows, sort_rows
+from tests._util import assert_same_rows
 
 pytestmark = pytest.mark.gpu
 
