@@ -118,18 +118,21 @@ def _src_sha():
     return h.hexdigest()[:16]
 
 
-def _traffic_from_profile(workload: str):
-    """dram bytes per insert launch from the committed ncu summary, if it matches the source."""
-    path = os.path.join(ROOT, "profiles", "insert_kernel_%s.md" % workload)
+def _traffic_and_source(workload: str):
+    """(dram bytes per insert launch, where they come from) from the committed ncu summary;
+    (None, why) when there is none or the kernel source changed since it was taken."""
+    rel = os.path.join("profiles", "insert_kernel_%s.md" % workload)
     try:
-        text = open(path).read()
+        text = open(os.path.join(ROOT, rel)).read()
     except OSError:
-        return None
+        return None, "no ncu summary for this workload"
     sha = re.search(r"source_sha256_16:\s*([0-9a-f]+)", text)
     tr = re.search(r"traffic_bytes_per_launch:\s*([0-9]+)", text)
-    if not sha or not tr or sha.group(1) != _src_sha():
-        return None
-    return int(tr.group(1))
+    if not sha or not tr:
+        return None, "%s holds no traffic line" % rel
+    if sha.group(1) != _src_sha():
+        return None, "%s was taken on another kernel source" % rel
+    return int(tr.group(1)), "%s (ncu dram__bytes_read + write, source %s)" % (rel, sha.group(1))
 
 
 class Clocks:
@@ -331,7 +334,8 @@ def main_ours(a, world, rank, local):
     achieved = kbytes / (ins_ms / 1000.0) / 1e9
     p2_ms = (ph["clear_ms"] + ph["insert_ms"] + ph["compact_ms"] + ph["overflow_ms"]) / a.steps
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                "frac": achieved / hbm, "traffic": _traffic_from_profile(a.workload),
+                "frac": achieved / hbm, "traffic": _traffic_and_source(a.workload)[0],
+                "traffic_from": _traffic_and_source(a.workload)[1],
                 "kernel": ("fused_kernel<%d,%d>" if fused else "insert_kernel<%d,%d>")
                           % (W, (2 * k + 62) // 63),
                 "peak_kind": peak_kind + " (hbm_gbs, copy bandwidth)",

@@ -39,3 +39,14 @@ def test_k_sweep_spans_every_key_width_band_up_to_479():
     assert list(ks) == sorted(ks) and ks[0] == 32 and ks[-1] == 479
     widths = {(2 * k + 63) // 64 for k in ks}
     assert {1, 3, 4, 7, 8, 15} <= widths
+
+
+def test_traffic_only_from_a_profile_of_the_current_source():
+    """The bench line carries the DRAM bytes of the committed config-2 insert summary only while
+    that summary was taken on the current kernel source; otherwise null, with the reason."""
+    traffic, src = bench._traffic_and_source("genome5M-30x-k65")
+    if bench._src_sha() in src:
+        assert traffic is not None and 2e9 < traffic < 6e9, src
+    else:
+        assert traffic is None and "another kernel source" in src, src
+    assert bench._traffic_and_source("no-such-workload") == (None, "no ncu summary for this workload")
