@@ -191,21 +191,27 @@ typedef struct gerbil_tuning {
   double ns_per_kmer;  /* phase-two device time per k-mer of the sample with the chosen form */
 } gerbil_tuning;
 
-/* Fills *opts with the defaults listed above. */
+/* Fills *opts (not NULL) with the defaults listed above: canonical counting and minimizers,
+ * KMC2 ordering, L_max 256, theta 1024, load factor 0.5 (Sec. 3.1, Alg. 1, Sec. 3.4). */
 void gerbil_opts_default(gerbil_opts* opts);
 
-/* Human-readable name of a status code; never NULL. */
+/* Human-readable name of a status code; never NULL ("unknown status" for other values).
+ * The paper has no counterpart (library plumbing, as are the context and accessor calls
+ * below). */
 const char* gerbil_strerror(int status);
 
-/* Text of the last CUDA or argument error seen on this context ("" if none). */
+/* Text of the last CUDA or argument error seen on this context ("" if none or ctx is NULL).
+ * The string is owned by the context and valid until its next call. */
 const char* gerbil_last_error(const gerbil_ctx* ctx);
 
 /* Creates a context on CUDA device `device`.  hbm_budget_bytes bounds the device memory the
  * context may hold at once (0 = no bound).  cuda_stream is a cudaStream_t on that device that
  * every call is ordered on: cudaStreamLegacy ((void*)1) for the legacy default stream,
  * cudaStreamPerThread ((void*)2) for the per-thread one; NULL makes the context create a
- * non-blocking stream of its own, which does not wait for work on any other stream.
- * Errors: E_INVAL (bad device), E_CUDA. */
+ * non-blocking stream of its own, which does not wait for work on any other stream.  The
+ * paper has no counterpart: its runs own the machine, while a context holds one device's
+ * stream, budget, reusable scratch and the distinct ratio learned so far (Sec. 3.4).
+ * Errors: E_INVAL (bad device or NULL out), E_CUDA. */
 int gerbil_create(gerbil_ctx** out, int device, uint64_t hbm_budget_bytes, void* cuda_stream);
 
 /* Forgets the distinct/occurrence ratio the context learned from earlier counts (Sec. 3.4
@@ -228,27 +234,31 @@ int gerbil_forget_ratio(gerbil_ctx* ctx);
 #define GERBIL_PROBE_BUCKETS 34
 int gerbil_probe_stats(gerbil_ctx* ctx, int enable);
 
-/* Reads the histograms (GERBIL_PROBE_BUCKETS entries each): entry i < 32 counts k-mers placed
+/* Reads the probe histograms of Sec. 3.3's comparison (GERBIL_PROBE_BUCKETS entries each): entry i < 32 counts k-mers placed
  * after reading i+1 slots (slots[]) or touching i+1 lines (lines[]), entry 32 more than 32,
  * entry 33 k-mers sent to the overflow area (theta probes without room).  Synchronizes the
  * context's stream.  Errors: E_INVAL, E_STATE (statistics off), E_CUDA. */
 int gerbil_get_probe_stats(const gerbil_ctx* ctx, uint64_t* slots, uint64_t* lines);
 
-/* Destroys the context and releases its scratch memory (not the caller's stream). */
+/* Destroys the context and releases its scratch memory (not the caller's stream).  Bins and
+ * results it made must be freed first.  NULL is ignored. */
 void gerbil_destroy(gerbil_ctx* ctx);
 
 /* Releases the context's cached scratch (table arena, overflow area, work lists) back to the
- * device pool; the next count allocates it again.  Results and bins are not affected. */
+ * device pool; the next count allocates it again.  Results and bins are not affected.
+ * Errors: E_INVAL (NULL), E_CUDA. */
 int gerbil_trim(gerbil_ctx* ctx);
 
-/* Device bytes the context currently holds (scratch, bins, results). */
+/* Device bytes the context currently holds (scratch, bins, results); 0 for NULL. */
 uint64_t gerbil_device_bytes(const gerbil_ctx* ctx);
 
 /* Enables (1) or disables (0) per-step event timing and resets the accumulated times and
- * launch counters.  Timing adds two event records per step; results are unchanged. */
+ * launch counters.  Timing adds two event records per step; results are unchanged.
+ * Synchronizes the context's stream.  Errors: E_INVAL (NULL), E_CUDA. */
 int gerbil_profile(gerbil_ctx* ctx, int enable);
 
-/* Copies the accumulated step times and launch counters (see gerbil_phase_times). */
+/* Copies the accumulated step times and launch counters (see gerbil_phase_times) into *out.
+ * Errors: E_INVAL (NULL ctx or out). */
 int gerbil_get_phase_times(const gerbil_ctx* ctx, gerbil_phase_times* out);
 
 /* Phase one (Sec. 2.1, Fig. 1; Sec. 2.3 Phase One steps 2-4): encodes the reads to 2 bits
@@ -263,20 +273,25 @@ int gerbil_get_phase_times(const gerbil_ctx* ctx, gerbil_phase_times* out);
 int gerbil_partition(gerbil_ctx* ctx, const gerbil_reads* reads, int k, int m, int nbins,
                      const gerbil_opts* opts, gerbil_bins** out);
 
-/* Totals of a bins object (any pointer may be NULL). */
+/* Totals of a bins object (any out pointer may be NULL).  Errors: E_INVAL (NULL bins). */
 int gerbil_bins_info(const gerbil_bins* bins, int* k, int* m, int* nbins, uint64_t* n_supermers,
                      uint64_t* n_kmers);
 
-/* binStatFile row of one bin: super-mers, bases (sum of super-mer lengths), k-mers. */
+/* binStatFile row of one bin (App. A flag -x; Sec. 3.4 sizes tables from it): super-mers,
+ * bases (sum of super-mer lengths), k-mers.  Any out pointer may be NULL.
+ * Errors: E_INVAL (NULL bins, bin outside [0, nbins)). */
 int gerbil_bin_stats(const gerbil_bins* bins, int bin, uint64_t* n_super, uint64_t* n_bases,
                      uint64_t* n_kmers);
 
-/* Copies the super-mer descriptors to host arrays of capacity cap (>= n_supermers):
+/* Copies the super-mer descriptors -- what the paper's temporary files hold (Sec. 2.3 Phase One
+ * step 4) -- to host arrays of capacity cap (>= n_supermers):
  * global start position of the super-mer's first base in the input, its number of
  * k-mers, and its bin.  Order within a bin is unspecified.  Errors: E_INVAL (cap). */
 int gerbil_bins_export(const gerbil_bins* bins, uint64_t* pos, uint32_t* nkmers, uint32_t* bin,
                        uint64_t cap);
 
+/* Releases a bins object and its device memory (the reads it was made from are the caller's).
+ * NULL is ignored. */
 void gerbil_bins_free(gerbil_bins* bins);
 
 /* Phase two for one bin (Sec. 2.3 Phase Two; Alg. 1; Sec. 3.4): splits the bin's super-mers
@@ -288,29 +303,33 @@ void gerbil_bins_free(gerbil_bins* bins);
 int gerbil_count(gerbil_ctx* ctx, const gerbil_bins* bins, int bin, int k, uint32_t min_count,
                  const gerbil_opts* opts, gerbil_counts** out);
 
-/* Phase two for many bins at once: the bins listed in bin_list (host array of nb distinct
- * bin indices; NULL = all bins, nb ignored) are counted together and their rows returned in
- * one result.  Because bins partition the k-mers, the rows are the union of the per-bin
+/* Phase two for many bins at once (Sec. 2.3 Phase Two over several temporary files; bins are
+ * independent, Sec. 2.1): the bins listed in bin_list (host array of nb distinct bin indices;
+ * NULL = all bins, nb ignored) are counted together and their rows returned in one result.  Because bins partition the k-mers, the rows are the union of the per-bin
  * results.  With opts->persistent (default) one persistent kernel pops tiles of all bins
  * from a device work queue.  Errors: as gerbil_count. */
 int gerbil_count_batch(gerbil_ctx* ctx, const gerbil_bins* bins, const int32_t* bin_list,
                        int nb, int k, uint32_t min_count, const gerbil_opts* opts,
                        gerbil_counts** out);
 
-/* Size and statistics of a result (any pointer may be NULL). */
+/* Size and statistics of a result (any out pointer may be NULL).  Errors: E_INVAL (NULL). */
 int gerbil_counts_info(const gerbil_counts* counts, uint64_t* n, int* words,
                        gerbil_count_stats* stats);
 
-/* Device pointers of a result: keys[n][W] (row-major, layout above) and counts[n] (u32).
- * Valid until gerbil_counts_free. */
+/* Device pointers of a result: keys[n][W] (row-major, layout above) and counts[n] (u32), the
+ * rows App. C writes out.  Owned by the result and valid until gerbil_counts_free; a result
+ * counted in bin groups is joined into one buffer on the first view.
+ * Errors: E_INVAL (NULL), E_NOMEM, E_CUDA. */
 int gerbil_counts_view(const gerbil_counts* counts, const uint64_t** keys_dev,
                        const uint32_t** counts_dev);
 
-/* Copies a result to host arrays: keys (cap*W words) and counts (cap entries).
- * Errors: E_INVAL if cap < n. */
+/* Copies a result to host arrays owned by the caller: keys (cap*W words, layout above) and
+ * counts (cap entries); plain or pinned host memory.  Synchronizes the context's stream.
+ * Errors: E_INVAL (NULL result, cap < n, NULL arrays for a non-empty result), E_CUDA. */
 int gerbil_counts_to_host(const gerbil_counts* counts, uint64_t* keys, uint32_t* counts_out,
                           uint64_t cap);
 
+/* Releases a result and its device memory.  NULL is ignored. */
 void gerbil_counts_free(gerbil_counts* counts);
 
 /* Output records of App. C ("Output Format") for every row of a result, in the result's row
@@ -365,27 +384,37 @@ typedef struct gerbil_job_times {
 /* Errors: E_INVAL (slots outside 1..64), E_CUDA, E_NOMEM. */
 int gerbil_server_create(gerbil_server** out, int device, uint64_t hbm_budget_bytes, int slots);
 
-/* Queues one job.  Host reads are copied at submit; device reads must be complete when this is
- * called (the workers' streams wait for no other stream) and stay valid until the job's
- * result has been waited for.  opts->bin_bounds is copied.  *job_id receives the id. */
+/* Queues one job: gerbil_partition and gerbil_count_batch over all bins of its reads (Sec. 2.3
+ * Phase One and Phase Two), with the arguments of those calls.  Host reads are copied at
+ * submit; device reads must be complete when this is called (the workers' streams wait for no
+ * other stream) and stay valid until the job's result has been waited for.  opts->bin_bounds
+ * is copied.  *job_id receives the id.  Errors: E_INVAL (NULL arguments, k, m, nbins or
+ * min_count out of range), E_NOMEM (host), E_CUDA (copying host reads).  A job's own failure is
+ * reported by gerbil_server_wait. */
 int gerbil_server_submit(gerbil_server* s, const gerbil_reads* reads, int k, int m, int nbins,
                          uint32_t min_count, const gerbil_opts* opts, uint64_t* job_id);
 
 /* Waits for a job (timeout_ms < 0: no limit) and hands over its result (*out, NULL if the job
- * failed) and times; returns the job's status, or E_TIMEOUT (the job stays queued/running). */
+ * failed; the caller frees it with gerbil_counts_free) and times (times may be NULL); returns
+ * the job's status, or E_TIMEOUT (the job stays queued/running), or E_INVAL (NULL s or out, an
+ * unknown or already handed-over job id). */
 int gerbil_server_wait(gerbil_server* s, uint64_t job_id, int64_t timeout_ms, gerbil_counts** out,
                        gerbil_job_times* times);
 
+/* Totals since the server was created.  Errors: E_INVAL (NULL). */
 int gerbil_server_get_stats(gerbil_server* s, gerbil_server_stats* out);
 
 /* Message of the last failed job that gerbil_server_wait handed over (the worker context's
  * gerbil_last_error, prefixed by the status name); "" if none.  Valid until the next wait. */
 const char* gerbil_server_last_error(const gerbil_server* s);
 
-/* Stops the workers after their current jobs and frees every result not yet handed over. */
+/* Stops the workers after their current jobs and frees every result not yet handed over.
+ * NULL is ignored. */
 void gerbil_server_destroy(gerbil_server* s);
 
-/* Autotuner.  Times phase two on every 16th bin of `bins` (device events around the clears,
+/* Autotuner.  The paper sizes every table with one load factor (Sec. 3.4) and has no tuner;
+ * here the load factor and the phase-two form are chosen by measurement.  Times phase two on
+ * every 16th bin of `bins` (device events around the clears,
  * inserts, compaction and overflow work, best of two runs per candidate): first the form and
  * schedule (fused 0 with schedule 1 or 0, fused 1, fused 2) at load factor 0.5, then load
  * factors 0.35 / 0.5 / 0.65 / 0.8 for each table-size class that holds at least 100,000 k-mers
