@@ -238,8 +238,8 @@ def main_reference(a, world, rank):
         "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1000 * total / a.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
         "data": "synthetic", "config": _config(a.workload, p, seq, offs),
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "nproc": os.cpu_count(),
+                         "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -516,7 +516,8 @@ def main_ours(a, world, rank, local):
     cpu = None
     if rank == 0 and not a.no_cpu_baseline:
         occ_s, dt, n = run_cpu_oracle(seq, offs, p, a.cpu_sample_windows)
-        cpu = {"value": occ_s / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+        cpu = {"value": occ_s / dt, "unit": UNIT, "cores": 1, "nproc": os.cpu_count(),
+               "kind": "oracle",
                "sample": "first %d of %d reads (%d k-mer windows), std::map oracle, %.1f s"
                          % (n, offs.size - 1, occ_s, dt)}
 
