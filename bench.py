@@ -58,6 +58,11 @@ def _args():
     ap.add_argument("--autotune", action="store_true",
                     help="form, schedule and per-class load factors from the autotuner")
     ap.add_argument("--graph", action="store_true", help="phase two as one captured CUDA graph")
+    ap.add_argument("--probe-scheme", type=int, default=None,
+                    help="0 linear probing (default), 1 windowed double hashing (Sec. 3.3)")
+    ap.add_argument("--item-kmers", type=int, default=None,
+                    help="k-mers per insert work item: 64, 128 or 256 (default)")
+    ap.add_argument("--load-factor", type=float, default=None, help="table load factor (0.5)")
     ap.add_argument("--ksweep", action="store_true",
                     help="throughput against k from 32 to 479 on one long-read workload")
     ap.add_argument("--ks", default=None, help="comma-separated k values of --ksweep (default all)")
@@ -74,6 +79,13 @@ def _args():
     ap.add_argument("--serving-scale", type=float, default=1.0,
                     help="shrink every serving job's genome and reads by this factor")
     ap.add_argument("--serving-rate", type=float, default=20.0, help="mean arrivals per second")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the configs block (the other workloads and the serving stream)")
+    ap.add_argument("--config-steps", type=int, default=5,
+                    help="timed steps of every workload of the configs block")
+    ap.add_argument("--config-sample-windows", type=int, default=300_000,
+                    help="k-mer windows of each config's oracle-checked read sample")
+    ap.add_argument("--no-serving", action="store_true", help="configs block without serving")
     return ap.parse_args()
 
 
@@ -118,10 +130,11 @@ def _src_sha():
     return h.hexdigest()[:16]
 
 
-def _traffic_and_source(workload: str):
-    """(dram bytes per insert launch, where they come from) from the committed ncu summary;
-    (None, why) when there is none or the kernel source changed since it was taken."""
-    rel = os.path.join("profiles", "insert_kernel_%s.md" % workload)
+def _traffic_and_source(workload: str, kernel: str = "insert_kernel"):
+    """(dram bytes per launch of the kernel, where they come from) from the committed ncu
+    summary profiles/<kernel>_<workload>.md; (None, why) when there is none or the kernel
+    source changed since it was taken."""
+    rel = os.path.join("profiles", "%s_%s.md" % (kernel, workload))
     try:
         text = open(os.path.join(ROOT, rel)).read()
     except OSError:
@@ -218,6 +231,199 @@ def _host_workload(name):
     return synth.workload(name)
 
 
+CONFIG_WORKLOADS = ("uniform-20k-k32", "genome100M-repeats-30x-k99", "genome50M-longreads-20x-k200")
+
+
+def _device_workload(name):
+    """(seq uint8, offsets int64) CUDA tensors and the parameters of a named workload."""
+    import torch
+    from paper_1607_06618_b300 import synth
+    if name in synth.TORCH_WORKLOADS:
+        return synth.torch_workload(name, device="cuda")
+    seq, offs, p = synth.workload(name)
+    return torch.from_numpy(seq).cuda(), torch.from_numpy(offs.view(np.int64)).cuda(), p
+
+
+def _insert_kernel_name(k, opts, fused):
+    W, WS = (2 * k + 63) // 64, (2 * k + 62) // 63
+    return ("fused_kernel<%d,%d>" if fused else "insert_kernel<%d,%d>") % (W, WS)
+
+
+def _roofline(ph, steps, occ, n_bases, info, k, workload, hbm, peak_kind, opts):
+    """Roofline of the dominant kernel (insert, or the fused kernel) from its event-timed
+    launches: the byte model per launch / average launch time, against the HBM peak."""
+    W = (2 * k + 63) // 64
+    insert_bytes, step_bytes = _model_bytes(occ, n_bases, info["distinct"], info["emitted"], W)
+    ins_ms = ph["insert_ms"] / max(1, ph["insert_launches"])
+    fused = ph["compact_ms"] == 0.0  # fused form: one kernel inserts and compacts
+    kbytes = step_bytes if fused else insert_bytes
+    achieved = kbytes / (ins_ms / 1000.0) / 1e9
+    kname = _insert_kernel_name(k, opts, fused)
+    traffic, traffic_from = _traffic_and_source(workload, kname.split("<")[0])
+    return {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+            "frac": achieved / hbm, "traffic": traffic, "traffic_from": traffic_from,
+            "kernel": kname,
+            "peak_kind": peak_kind + " (hbm_gbs, copy bandwidth)",
+            "bytes_per_launch": kbytes, "launch_ms": ins_ms}, step_bytes
+
+
+def _time_steps(ctx, stream, s_dev, o_dev, p, opts, steps, warmup, dist=None, clocks_dev=None):
+    """Warm-up, then ``steps`` event-timed steps (gerbil_partition + gerbil_count_batch over all
+    bins) with the context's phase events on, bracketed by a barrier (under torchrun) and a
+    device synchronisation on both sides; nvidia-smi samples the clocks meanwhile.  Returns
+    (info of a warm-up step, ms per step, phase times summed over the steps, clocks)."""
+    import torch
+    k, m, nbins, mc = p["k"], p["m"], p["nbins"], p["min_count"]
+    bb = p.get("bin_bounds")
+    info = {}
+
+    def step(record=False):
+        bins = ctx.partition(s_dev, o_dev, k, m, nbins, opts, bb)
+        res = ctx.count_batch(bins, None, k, mc, opts)
+        st = res.info()[2]
+        if record:
+            info.update(st)
+            info["n_supermers"] = bins.info()["n_supermers"]
+        res.free()
+        bins.free()
+        return st
+
+    nwarm = max(3, warmup)
+    for i in range(nwarm):
+        step(record=(i == nwarm - 1))
+    ctx.profile(True)
+    clocks = Clocks(clocks_dev if clocks_dev is not None else torch.cuda.current_device())
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        st = step()
+        assert st["emitted"] == info["emitted"] and st["occurrences"] == info["occurrences"]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ck = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    ph = ctx.phase_times()
+    ctx.profile(False)
+    return info, ms / steps, ph, ck
+
+
+def _batched_vs_per_bin(gerbil, torch, ctx, s_dev, o_dev, p, opts, reps, variants):
+    """Phase two over all bins, host-timed per call with a device synchronisation: one
+    count_batch per variant (default: the persistent insert grid + compaction grid) against
+    one gerbil_count call per bin.  The autotuned variant is tuned by an untimed first call."""
+    k, m, nbins, mc = p["k"], p["m"], p["nbins"], p["min_count"]
+    bins = ctx.partition(s_dev, o_dev, k, m, nbins, opts, p.get("bin_bounds"))
+    torch.cuda.synchronize()
+
+    def host_ms(o):
+        ctx.count_batch(bins, None, k, mc, o).free()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            ctx.count_batch(bins, None, k, mc, o).free()
+        torch.cuda.synchronize()
+        return 1000 * (time.perf_counter() - t0) / reps
+
+    out = {}
+    for name, o in variants:
+        t0 = time.perf_counter()
+        if name == "batched_autotune_ms":
+            out["autotune_s"] = 0.0
+            ctx.count_batch(bins, None, k, mc, o).free()  # tunes on first use
+            torch.cuda.synchronize()
+            out["autotune_s"] = time.perf_counter() - t0
+            out["autotune"] = ctx.get_tuning(k)
+        out[name] = host_ms(o)
+    ctx.count(bins, 0, k, mc, opts).free()
+    torch.cuda.synchronize()
+    tp = time.perf_counter()
+    for _ in range(reps):
+        for b in range(nbins):
+            ctx.count(bins, b, k, mc, opts).free()
+    torch.cuda.synchronize()
+    out["per_bin_ms"] = 1000 * (time.perf_counter() - tp) / reps
+    out["speedup"] = out["per_bin_ms"] / out["batched_ms"]
+    bins.free()
+    return out
+
+
+def _sample_check(gerbil, ctx, s_dev, o_dev, p, opts, windows_sample):
+    """The oracle (one core) on the first reads holding about ``windows_sample`` k-mer windows,
+    timed, and the same reads counted on the GPU (min_count 1, host buffers): row for row
+    equality and the oracle's rate."""
+    import oracle
+    k = p["k"]
+    offs = o_dev.cpu().numpy().view(np.uint64)
+    n = _reads_for_windows(offs, k, windows_sample)
+    so = offs[: n + 1].copy()
+    ss = s_dev[: int(so[-1])].cpu().numpy()
+    t0 = time.perf_counter()
+    oracle.count(ss, so, k, canonical=True, min_count=p["min_count"])
+    dt = time.perf_counter() - t0
+    occ_s = oracle.windows(ss, so, k)
+    wk, wc = oracle.count(ss, so, k, canonical=True, min_count=1)
+    bins = ctx.partition(ss, so, k, p["m"], p["nbins"], opts, p.get("bin_bounds"))
+    res = ctx.count_batch(bins, None, k, 1, opts)
+    gk, gc = res.to_host()
+    res.free()
+    bins.free()
+    W = (2 * k + 63) // 64
+    gk = np.asarray(gk, dtype=np.uint64).reshape(len(gc), W)
+    order = np.lexsort(gk.T[::-1]) if len(gc) else np.zeros(0, np.int64)
+    same = bool(len(gc) == len(wc)
+                and np.array_equal(gk[order], np.asarray(wk, np.uint64).reshape(len(wc), W))
+                and np.array_equal(np.asarray(gc, np.uint64)[order], np.asarray(wc, np.uint64)))
+    return {"sample_bit_exact": same, "sample_rows": int(len(wc)), "sample_windows": int(occ_s),
+            "sample_reads": int(n), "oracle_kmers_per_s": occ_s / dt, "oracle_cores": 1,
+            "oracle_s": dt}
+
+
+def run_config(a, name, local, hbm, peak_kind):
+    """One config of the configs block: event-timed steps with the insert kernel's roofline,
+    batched vs per-bin phase two, and an oracle-checked read sample."""
+    import torch
+    from paper_1607_06618_b300 import gerbil
+    t_gen = time.perf_counter()
+    s_dev, o_dev, p = _device_workload(name)
+    torch.cuda.synchronize()
+    t_gen = time.perf_counter() - t_gen
+    k = p["k"]
+    stream = torch.cuda.current_stream()
+    ctx = gerbil.Context(local, stream=stream.cuda_stream)
+    opts = gerbil.default_opts()
+    try:
+        info, ms, ph, ck = _time_steps(ctx, stream, s_dev, o_dev, p, opts, a.config_steps, 3,
+                                       clocks_dev=local)
+        occ = info["occurrences"]
+        n_bases = occ + info["n_supermers"] * (k - 1)
+        roof, step_bytes = _roofline(ph, a.config_steps, occ, n_bases, info, k, name, hbm, peak_kind,
+                                     opts)
+        variants = [("batched_ms", opts), ("batched_graph_ms", gerbil.default_opts(graph=1))]
+        if name == "genome100M-repeats-30x-k99":
+            variants.append(("batched_autotune_ms", gerbil.default_opts(autotune=1)))
+        bvp = _batched_vs_per_bin(gerbil, torch, ctx, s_dev, o_dev, p, opts, a.per_bin_steps, variants)
+        chk = _sample_check(gerbil, ctx, s_dev, o_dev, p, opts, a.config_sample_windows)
+    finally:
+        ctx.close()
+    out = {"value": occ / (ms / 1000.0), "unit": UNIT, "ms_per_step": ms, "steps": a.config_steps,
+           "warmup": 3, "config": _config(name, p, s_dev, o_dev), "generation_s": t_gen,
+           "occurrences_per_step": occ, "distinct": info["distinct"], "emitted": info["emitted"],
+           "supermers": info["n_supermers"], "table_slots": info["table_slots"],
+           "overflowed": info["overflowed"], "groups": info["groups"], "roofline": roof,
+           "phase_ms": {key[:-3]: ph[key] / a.config_steps for key in ph if key.endswith("_ms")},
+           "gpu_launches": int(ph["kernel_launches"]), "batched_vs_per_bin": bvp, "clocks": ck}
+    out.update(chk)
+    del s_dev, o_dev
+    torch.cuda.empty_cache()
+    return out
+
+
+
 def main_reference(a, world, rank):
     if rank != 0:
         return 0
@@ -247,11 +453,16 @@ def main_reference(a, world, rank):
 
 
 def _config(name, p, seq, offs):
+    nreads = int(offs.numel() if hasattr(offs, "numel") else offs.size) - 1
+    nbases = int(seq.numel() if hasattr(seq, "numel") else seq.size)
     return {"workload": name, "k": p["k"], "m": p["m"], "nbins": p["nbins"],
             "bins": "log-normal shares (sigma 1)" if p.get("bin_bounds") is not None else "uniform",
-            "min_count": p["min_count"], "reads": int(offs.size - 1),
-            "bases": int(seq.size), "mode": "count_batch over all bins (persistent insert grid)",
-            "l2": "inputs larger than L2 (%.0f MB ASCII reads > 126 MB)" % (seq.size / 1e6)}
+            "min_count": p["min_count"], "reads": nreads,
+            "bases": nbases, "mode": "count_batch over all bins (persistent insert grid)",
+            "l2": ("inputs larger than L2 (%.0f MB ASCII reads > 126 MB)" % (nbases / 1e6)
+                   if nbases > L2_BYTES else
+                   "inputs smaller than L2 (%.1f MB); tables and bins rewritten every step"
+                   % (nbases / 1e6))}
 
 
 def main_ours(a, world, rank, local):
@@ -284,62 +495,27 @@ def main_ours(a, world, rank, local):
         kw["autotune"] = 1
     if a.graph:
         kw["graph"] = 1
+    if a.probe_scheme is not None:
+        kw["probe_scheme"] = a.probe_scheme
+    if a.item_kmers is not None:
+        kw["item_kmers"] = a.item_kmers
+    if a.load_factor is not None:
+        kw["load_factor"] = a.load_factor
     opts = gerbil.default_opts(**kw)
 
-    info = {}
-
-    def step(record=False):
-        bins = ctx.partition(s_dev, o_dev, k, m, nbins, opts, bb)
-        res = ctx.count_batch(bins, None, k, mc, opts)
-        st = res.info()[2]
-        if record:
-            info.update(st)
-            info["n_supermers"] = bins.info()["n_supermers"]
-        res.free()
-        bins.free()
-        return st
-
-    nwarm = max(3, a.warmup)
-    for i in range(nwarm):
-        step(record=(i == nwarm - 1))
+    # warm-up steps, then exactly a.steps event-timed steps between device synchronisations
+    info, ms1, ph, ck = _time_steps(ctx, stream, s_dev, o_dev, p, opts, a.steps, a.warmup, dist,
+                                    local)
     occ = info["occurrences"]
     n_bases = occ + info["n_supermers"] * (k - 1)
-
-    clocks = Clocks(local)
-    ctx.profile(True)
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(a.steps):
-        st = step()
-        assert st["emitted"] == info["emitted"] and st["occurrences"] == occ
-    e1.record(stream)
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    ms = e0.elapsed_time(e1)
-    ph = ctx.phase_times()
-    ck = clocks.stop()
-    ctx.profile(False)
-    value, ms = _replica_value(occ * a.steps, ms, dist, world, "cuda")
+    value, ms = _replica_value(occ * a.steps, ms1 * a.steps, dist, world, "cuda")
 
     # roofline of the dominant kernel (insert), from its own event-timed launches
     hbm, peak_kind = _peaks()
-    insert_bytes, step_bytes = _model_bytes(occ, n_bases, info["distinct"], info["emitted"], W)
-    ins_ms = ph["insert_ms"] / max(1, ph["insert_launches"])
-    fused = ph["compact_ms"] == 0.0  # fused form: one kernel inserts and compacts
-    kbytes = step_bytes if fused else insert_bytes
-    achieved = kbytes / (ins_ms / 1000.0) / 1e9
+    roofline, step_bytes = _roofline(ph, a.steps, occ, n_bases, info, k, a.workload, hbm, peak_kind,
+                                     opts)
+    ins_ms = roofline["launch_ms"]
     p2_ms = (ph["clear_ms"] + ph["insert_ms"] + ph["compact_ms"] + ph["overflow_ms"]) / a.steps
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                "frac": achieved / hbm, "traffic": _traffic_and_source(a.workload)[0],
-                "traffic_from": _traffic_and_source(a.workload)[1],
-                "kernel": ("fused_kernel<%d,%d>" if fused else "insert_kernel<%d,%d>")
-                          % (W, (2 * k + 62) // 63),
-                "peak_kind": peak_kind + " (hbm_gbs, copy bandwidth)",
-                "bytes_per_launch": kbytes, "launch_ms": ins_ms}
     phase_ms = {key[:-3]: ph[key] / a.steps for key in ph if key.endswith("_ms")}
 
     # ceilings of the operations the insert kernel is made of (random 32-byte slot load, then
@@ -361,64 +537,55 @@ def main_ours(a, world, rank, local):
     # batched (one persistent launch) vs one count call per bin, phase two only
     bvp = None
     if a.per_bin_steps > 0 and rank == 0:
-        bins = ctx.partition(s_dev, o_dev, k, m, nbins, opts, bb)
-        torch.cuda.synchronize()
-        tb = time.perf_counter()
-        for _ in range(a.per_bin_steps):
-            ctx.count_batch(bins, None, k, mc, opts).free()
-        torch.cuda.synchronize()
-        tb = (time.perf_counter() - tb) / a.per_bin_steps
-        def host_ms(o):
-            ctx.count_batch(bins, None, k, mc, o).free()
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            for _ in range(a.per_bin_steps):
-                ctx.count_batch(bins, None, k, mc, o).free()
-            torch.cuda.synchronize()
-            return (time.perf_counter() - t0) / a.per_bin_steps
-        tc = host_ms(gerbil.default_opts(fused=1))
-        ts = host_ms(gerbil.default_opts(schedule=0))
-        tw = host_ms(gerbil.default_opts(fused=2))
-        tg = host_ms(gerbil.default_opts(graph=1))
-        tp = time.perf_counter()
-        for _ in range(a.per_bin_steps):
-            for b in range(nbins):
-                ctx.count(bins, b, k, mc, opts).free()
-        torch.cuda.synchronize()
-        tp = (time.perf_counter() - tp) / a.per_bin_steps
-        bins.free()
-        bvp = {"batched_ms": 1000 * tb, "batched_fused_ms": 1000 * tc,
-               "batched_static_schedule_ms": 1000 * ts, "batched_waves_ms": 1000 * tw,
-               "batched_graph_ms": 1000 * tg,
-               "per_bin_ms": 1000 * tp,
-               "speedup": tp / tb,
-               "what": "phase two over all %d bins, host-timed: one count_batch (persistent insert "
-                       "grid + compaction grid), one fused count_batch (queue + L2 table ring), "
-                       "%d count calls" % (nbins, nbins)}
+        variants = [("batched_ms", opts), ("batched_fused_ms", gerbil.default_opts(fused=1)),
+                    ("batched_static_schedule_ms", gerbil.default_opts(schedule=0)),
+                    ("batched_waves_ms", gerbil.default_opts(fused=2)),
+                    ("batched_graph_ms", gerbil.default_opts(graph=1)),
+                    ("batched_autotune_ms", gerbil.default_opts(autotune=1))]
+        bvp = _batched_vs_per_bin(gerbil, torch, ctx, s_dev, o_dev, p, opts, a.per_bin_steps, variants)
+        bvp["what"] = ("phase two over all %d bins, host-timed: one count_batch per variant "
+                       "(default: persistent insert grid + compaction grid; fused queue kernel; "
+                       "static schedule; waves; CUDA graph; autotuned) against %d count calls"
+                       % (nbins, nbins))
 
-    # probe statistics of one step's phase two (Sec. 3.3 compares one-by-one with 128-byte
-    # window probing): share placed at the first slot read / within the first line, and the
-    # most slots / lines any k-mer needed; recorded outside the timed region
+    # probe statistics of one step's phase two under both probe schemes, on the same bins and
+    # table sizes (Sec. 3.3 compares one-by-one probing, 90.37% at the first probe and at most
+    # 29, with 128-byte window probing, 99.94% and at most 7): share placed at the first slot
+    # read / within the first line or window, the most slots / lines any k-mer needed, and the
+    # phase-two time of each scheme; recorded outside the timed region
     probes = None
     if rank == 0:
         bins = ctx.partition(s_dev, o_dev, k, m, nbins, opts, bb)
-        ctx.probe_stats(True)
-        ctx.count_batch(bins, None, k, mc, opts).free()
-        hs_, hl_ = ctx.get_probe_stats()
-        ctx.probe_stats(False)
-        bins.free()
-        tot = float(hs_.sum())
 
         def _maxb(h):
             nz = [i for i in range(33) if h[i]]
             return (nz[-1] + 1) if nz else 0
 
-        probes = {"first_slot_share": float(hs_[0]) / tot, "first_line_share": float(hl_[0]) / tot,
-                  "max_slots": _maxb(hs_), "max_lines": _maxb(hl_),
-                  "mean_slots": float(sum((i + 1) * int(hs_[i]) for i in range(33))) / tot,
-                  "overflowed": int(hs_[33]),
-                  "what": "per inserted k-mer: slots read until placed (linear probing, one slot "
-                          "per read) and distinct 128-byte lines among them"}
+        probes = {}
+        for name, scheme in (("linear", 0), ("windowed", 1)):
+            o = gerbil.default_opts(**dict(kw, probe_scheme=scheme))
+            ctx.probe_stats(True)
+            ctx.count_batch(bins, None, k, mc, o).free()
+            hs_, hl_ = ctx.get_probe_stats()
+            ctx.probe_stats(False)
+            tot = float(hs_.sum())
+            ctx.profile(True)
+            for _ in range(3):
+                ctx.count_batch(bins, None, k, mc, o).free()
+            php = ctx.phase_times()
+            ctx.profile(False)
+            probes[name] = {
+                "first_slot_share": float(hs_[0]) / tot, "first_line_share": float(hl_[0]) / tot,
+                "max_slots": _maxb(hs_), "max_lines": _maxb(hl_),
+                "mean_slots": float(sum((i + 1) * int(hs_[i]) for i in range(33))) / tot,
+                "mean_lines": float(sum((i + 1) * int(hl_[i]) for i in range(33))) / tot,
+                "overflowed": int(hs_[33]),
+                "insert_ms": php["insert_ms"] / 3, "phase2_ms": (php["clear_ms"] + php["insert_ms"] +
+                                                                php["compact_ms"] + php["overflow_ms"]) / 3}
+        probes["what"] = ("per inserted k-mer: slots read until placed and 128-byte lines (linear "
+                          "probing) or windows (windowed double hashing) among them; a bucket "
+                          "of 33 means 33 or more")
+        bins.free()
 
     # App. C output records of one step's result, written on the device (event-timed)
     appc = None
@@ -513,13 +680,29 @@ def main_ours(a, world, rank, local):
                        "memory, gerbil_partition + gerbil_count_batch, rows copied to pinned host "
                        "memory; %d host threads with a context (stream) each" % nw}
 
+    # the oracle on one core over a bounded sample (cpu_baseline), and the same reads counted
+    # on the GPU: row-for-row equality
     cpu = None
     if rank == 0 and not a.no_cpu_baseline:
-        occ_s, dt, n = run_cpu_oracle(seq, offs, p, a.cpu_sample_windows)
-        cpu = {"value": occ_s / dt, "unit": UNIT, "cores": 1, "nproc": os.cpu_count(),
-               "kind": "oracle",
+        chk = _sample_check(gerbil, ctx, s_dev, o_dev, p, opts, a.cpu_sample_windows)
+        cpu = {"value": chk["oracle_kmers_per_s"], "unit": UNIT, "cores": 1,
+               "nproc": os.cpu_count(), "kind": "oracle",
                "sample": "first %d of %d reads (%d k-mer windows), std::map oracle, %.1f s"
-                         % (n, offs.size - 1, occ_s, dt)}
+                         % (chk["sample_reads"], offs.size - 1, chk["sample_windows"], chk["oracle_s"]),
+               "sample_bit_exact": chk["sample_bit_exact"], "sample_rows": chk["sample_rows"]}
+    tuning = ctx.get_tuning(k) if (a.autotune or bvp) else None
+    ctx.close()
+    del s_dev, o_dev
+    torch.cuda.empty_cache()
+
+    # the other workloads (configs 1, 3, 4) and the serving stream, each measured on its own
+    configs = None
+    if rank == 0 and not a.no_configs:
+        configs = {}
+        for name in CONFIG_WORKLOADS:
+            configs[name] = run_config(a, name, local, hbm, peak_kind)
+        if not a.no_serving:
+            configs[SERVING_WORKLOAD] = run_serving(a, local, None, 3)
 
     if rank == 0:
         cfg = _config(a.workload, p, seq, offs)
@@ -537,11 +720,11 @@ def main_ours(a, world, rank, local):
             "gpu_launches": int(ph["kernel_launches"]), "batched_vs_per_bin": bvp,
             "appc_records": appc, "probe_stats": probes,
             "opts": {key: val for key, val in kw.items()},
-            "autotune": ctx.get_tuning(k) if a.autotune else None,
+            "autotune": tuning,
             "membench": membench,
+            "configs": configs,
         }
         print(json.dumps(line), flush=True)
-    ctx.close()
     if dist:
         dist.destroy_process_group()
     return 0
@@ -555,24 +738,21 @@ def _pct(xs, q):
     return xs[i]
 
 
-def main_serving(a, world, rank, local):
+def run_serving(a, local, dist=None, warmup=3):
     """Counting jobs arriving as a Poisson stream, served by gerbil.Server under an HBM budget:
     aggregate k-mers/s over the whole stream (first arrival to last result) and the p50/p99
     of the job latency (arrival to result on the device), host wall clock.  Every job's reads
     are drawn on the device before the clock starts; results stay on the device and are freed
-    once waited for.  Each rank serves its own stream (replicas)."""
+    once waited for.  Each rank serves its own stream (replicas).  Returns a dict."""
     import threading
     import torch
     from paper_1607_06618_b300 import gerbil, synth
 
-    torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    t_gen = time.perf_counter()
     jobs = synth.serving_jobs(a.serving_jobs, rate=a.serving_rate)
     reads = [synth.t_serving_reads(j, "cuda", a.serving_scale) for j in jobs]
     torch.cuda.synchronize()
+    t_gen = time.perf_counter() - t_gen
     budget = int(a.serving_budget_gb * 1e9)
 
     def run_stream(server, order, arrivals):
@@ -603,7 +783,7 @@ def main_serving(a, world, rank, local):
 
     # warm-up: the smallest jobs, all at once
     server = gerbil.Server(local, budget, a.serving_slots)
-    small = sorted(range(len(jobs)), key=lambda j: jobs[j]["nreads"])[:max(3, a.warmup)]
+    small = sorted(range(len(jobs)), key=lambda j: jobs[j]["nreads"])[:max(3, warmup)]
     run_stream(server, small, [0.0] * len(small))
     if dist:
         dist.barrier()
@@ -612,37 +792,58 @@ def main_serving(a, world, rank, local):
     ck = clocks.stop()
     st = server.stats()
     server.close()
+    bases = int(sum(int(r[0].numel()) for r in reads))
+    del reads
+    torch.cuda.empty_cache()
     occ = sum(r["occurrences"] for r in out)
-    value = _reduce(occ / wall, dist, "cuda", "sum")
     lat = [r["latency_ms"] for r in out]
+    return {
+        "workload": SERVING_WORKLOAD, "value": occ / wall, "unit": UNIT, "jobs": len(jobs),
+        "warmup_jobs": len(small), "rate_jobs_per_s": a.serving_rate, "slots": a.serving_slots,
+        "hbm_budget_bytes": budget, "scale": a.serving_scale, "bases_total": bases,
+        "occurrences_total": occ,
+        "k_mix": {str(k): sum(1 for j in jobs if j["k"] == k) for k, _ in synth.SERVING_K},
+        "latency_ms": {"p50": _pct(lat, 50), "p99": _pct(lat, 99), "mean": statistics.mean(lat),
+                       "max": max(lat)},
+        "queue_ms": {"p50": _pct([r["queue_ms"] for r in out], 50),
+                     "p99": _pct([r["queue_ms"] for r in out], 99)},
+        "run_ms": {"p50": _pct([r["run_ms"] for r in out], 50),
+                   "p99": _pct([r["run_ms"] for r in out], 99)},
+        "makespan_s": wall, "last_arrival_s": jobs[-1]["arrival_s"],
+        "offered_kmers_per_s": occ / max(1e-9, jobs[-1]["arrival_s"]),
+        "saturated": wall > 1.1 * jobs[-1]["arrival_s"],
+        "server": st, "jobs_grouped": sum(1 for r in out if r["groups"] > 1), "clocks": ck,
+        "generation_s": t_gen,
+        "timing": "host wall clock from the first arrival to the last result; device-resident reads",
+    }
+
+
+def main_serving(a, world, rank, local):
+    """The serving stream alone, as its own JSON line."""
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    r = run_serving(a, local, dist, a.warmup)
+    value = _reduce(r["value"], dist, "cuda", "sum")
     if rank == 0:
         line = {
             "metric": "serving: aggregate canonical k-mers counted/sec, p50/p99 job latency",
-            "value": value, "unit": UNIT, "n_gpus": world, "steps": len(jobs),
-            "warmup": len(small), "ms_per_step": 1000 * wall / len(jobs),
+            "value": value, "unit": UNIT, "n_gpus": world, "steps": r["jobs"],
+            "warmup": r["warmup_jobs"], "ms_per_step": 1000 * r["makespan_s"] / r["jobs"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
             "data": "synthetic",
-            "config": {"workload": SERVING_WORKLOAD, "jobs": len(jobs),
-                       "rate_jobs_per_s": a.serving_rate, "slots": a.serving_slots,
-                       "hbm_budget_bytes": budget, "scale": a.serving_scale,
-                       "bases_total": int(sum(int(r[0].numel()) for r in reads)),
-                       "occurrences_total": occ,
-                       "k_mix": {str(k): sum(1 for j in jobs if j["k"] == k) for k, _ in synth.SERVING_K},
-                       "l2": "each job's reads are read once; inputs far larger than L2"},
-            "latency_ms": {"p50": _pct(lat, 50), "p99": _pct(lat, 99), "mean": statistics.mean(lat),
-                           "max": max(lat)},
-            "queue_ms": {"p50": _pct([r["queue_ms"] for r in out], 50),
-                         "p99": _pct([r["queue_ms"] for r in out], 99)},
-            "run_ms": {"p50": _pct([r["run_ms"] for r in out], 50),
-                       "p99": _pct([r["run_ms"] for r in out], 99)},
-            "makespan_s": wall, "last_arrival_s": jobs[-1]["arrival_s"],
-            "offered_kmers_per_s": occ / max(1e-9, jobs[-1]["arrival_s"]),
-            "saturated": wall > 1.1 * jobs[-1]["arrival_s"],
-            "server": st, "jobs_grouped": sum(1 for r in out if r["groups"] > 1),
-            "clocks": ck, "gpu_launches": int(st["kernel_launches"]),
+            "config": {key: r[key] for key in ("workload", "jobs", "rate_jobs_per_s", "slots",
+                                               "hbm_budget_bytes", "scale", "bases_total",
+                                               "occurrences_total", "k_mix")},
+            "clocks": r["clocks"], "gpu_launches": int(r["server"]["kernel_launches"]),
             "cpu_baseline": None, "e2e": None,
-            "timing": "host wall clock from the first arrival to the last result; device-resident reads",
         }
+        line.update({key: r[key] for key in ("latency_ms", "queue_ms", "run_ms", "makespan_s",
+                                             "last_arrival_s", "offered_kmers_per_s", "saturated",
+                                             "server", "jobs_grouped", "timing")})
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

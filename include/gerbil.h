@@ -146,6 +146,24 @@ typedef struct gerbil_opts {
   float dfp_pivot;             /* p of GERBIL_ORDER_DFP, 0..1 (default 0.5) */
   uint32_t dfp_sample;         /* GERBIL_ORDER_DFP: frequencies from every dfp_sample-th read
                                   (default 16) */
+  int32_t probe_scheme;        /* hash-table probing of the insert kernel (two-grid form,
+                                  fused 0): 0 (default): linear probing from a fastrange slot;
+                                  1: windowed double hashing as in Sec. 3.3-3.4 -- windows of
+                                  one 128-byte line of slots (16- and 32-byte slots; wider
+                                  slots: as many whole slots as fit, at least one), the first
+                                  window and the window step taken from the key's hash, each
+                                  window scanned from its first slot; max_probes then counts
+                                  windows.  The other forms always probe linearly */
+  uint32_t item_kmers;         /* k-mers per insert work item, i.e. 32 threads per item_kmers
+                                  consecutive k-mers of a bin (two-grid form): 64, 128 or 256;
+                                  0 (default): 256.  64 and 128 are built for keys of up to
+                                  four words (k <= 128); wider keys: GERBIL_E_UNSUPPORTED */
+  int32_t sorted_output;       /* 1: the rows of gerbil_count / gerbil_count_batch in
+                                  ascending key order (numeric order of the 2k-bit keys = the
+                                  lexicographic order of the k-mers, A < C < G < T), sorted on
+                                  the device; a grouped result is joined first.  0 (default):
+                                  unordered */
+  int32_t reserved_opts;       /* zero */
 } gerbil_opts;
 
 /* Per-call statistics of a count. */
@@ -159,7 +177,7 @@ typedef struct gerbil_count_stats {
   uint32_t bins;        /* bins counted */
   uint32_t groups;      /* groups of bins counted one after another because the tables of
                            the whole batch did not fit under the table limit (0: one batch) */
-  uint32_t reserved;
+  uint32_t sorted;      /* 1: the rows are in ascending key order (gerbil_opts.sorted_output) */
 } gerbil_count_stats;
 
 /* Device time of each step of the path, accumulated over the calls made since profiling was
@@ -179,7 +197,9 @@ typedef struct gerbil_phase_times {
 
 /* Settings chosen by the autotuner for one key width (the paper has no autotuner; its table
  * sizes follow one load factor).  Tables are put in a size class by their bytes at load factor
- * 0.5: below class_bytes[0], [1], [2], or larger; each class has its own load factor. */
+ * 0.5: below class_bytes[0], [1], [2], or larger; each class has its own load factor.  The
+ * probe scheme and the work-item size hold for every table of the key width (each is a
+ * compile-time form of the insert kernel, and one launch runs one form). */
 #define GERBIL_TUNE_CLASSES 4
 typedef struct gerbil_tuning {
   float load_factor[GERBIL_TUNE_CLASSES];
@@ -189,6 +209,8 @@ typedef struct gerbil_tuning {
   int32_t k_words;     /* W = ceil(2k/64) the settings are for */
   uint32_t samples;    /* configurations timed */
   double ns_per_kmer;  /* phase-two device time per k-mer of the sample with the chosen form */
+  int32_t probe_scheme; /* gerbil_opts.probe_scheme for every table of this key width */
+  uint32_t item_kmers;  /* gerbil_opts.item_kmers (64, 128 or 256) */
 } gerbil_tuning;
 
 /* Fills *opts (not NULL) with the defaults listed above: canonical counting and minimizers,
@@ -413,14 +435,22 @@ const char* gerbil_server_last_error(const gerbil_server* s);
 void gerbil_server_destroy(gerbil_server* s);
 
 /* Autotuner.  The paper sizes every table with one load factor (Sec. 3.4) and has no tuner;
- * here the load factor and the phase-two form are chosen by measurement.  Times phase two on
- * every 16th bin of `bins` (device events around the clears,
- * inserts, compaction and overflow work, best of two runs per candidate): first the form and
- * schedule (fused 0 with schedule 1 or 0, fused 1, fused 2) at load factor 0.5, then load
- * factors 0.35 / 0.5 / 0.65 / 0.8 for each table-size class that holds at least 100,000 k-mers
- * of the sample (other classes keep 0.5).  The choice is kept in the context for the key width
- * of k and returned in *out (may be NULL).  Counts do not depend on any of these settings.
- * Costs about 20 sample counts.  Errors: as gerbil_count_batch. */
+ * here the phase-two form, the probe scheme, the work-item size (threads per k-mer) and the
+ * load factor of each table-size class are chosen by measurement.  Times phase two on every
+ * 16th bin of `bins` -- or every 8th, 4th, 2nd or every bin, until the sample's tables take
+ * four times the L2 cache, so that they do not all stay in L2 as no large batch's would --
+ * with device events around the clears, inserts, compaction and overflow work (best of two
+ * runs per candidate): first the form and schedule (fused 0 with schedule 1 or 0, fused 1,
+ * fused 2) with the defaults; then probe scheme 0 / 1; then work items of 256 / 128 / 64
+ * k-mers (keys of up to four words); then, for each table-size class that holds at least
+ * 100,000 k-mers of the sample (other classes keep 0.5), load factors 0.35 / 0.5 / 0.65 /
+ * 0.8; each step keeps the best of the previous ones.  A candidate
+ * whose time is not below the defaults' by 2% or more is not taken.  Finally the tuned
+ * settings and the defaults are timed on the whole batch, and the defaults are kept unless the
+ * tuned settings are faster there.  The choice is kept in the context for the key width of k
+ * and returned in *out (may be NULL).  Counts do not depend on any of these settings.  Costs
+ * about 20 sample counts and 4 counts of the batch.
+ * Errors: as gerbil_count_batch. */
 int gerbil_autotune(gerbil_ctx* ctx, const gerbil_bins* bins, int k, uint32_t min_count,
                     const gerbil_opts* opts, gerbil_tuning* out);
 
@@ -465,13 +495,15 @@ int gerbil_membench(gerbil_ctx* ctx, uint64_t bytes, int op, uint64_t per_thread
  * words per slot (about 1.05 million windows for k <= 31, 524 thousand for k = 65), are
  * rejected with GERBIL_E_INVAL before any GPU work.  The first call on a device resolves the
  * array's address (cudaGetSymbolAddress) for that device; make that first call before any
- * stream capture.  Every call clears the part of the array it uses, runs on cuda_stream (NULL:
- * the default stream) and synchronises it; calls whose GPU work overlaps (other streams or
- * other host threads on the same device) race on the shared array and must be serialised by
- * the caller.  No cudaMalloc, cudaFree or allocating library routine is called.
+ * stream capture.  The address is kept for the life of the process: after a cudaDeviceReset
+ * of that device it is stale, so do not call this entry point again in that process.  Every
+ * call clears the part of the array it uses, runs on cuda_stream (NULL: the default stream)
+ * and synchronises it; calls whose GPU work overlaps (other streams or other host threads on
+ * the same device) race on the shared array and must be serialised by the caller.  No
+ * cudaMalloc, cudaFree or allocating library routine is called.
  * Errors: E_INVAL (arguments, input too large, or *n_out > out_cap: *n_out then holds the
  * number of rows needed), E_UNSUPPORTED (k > GERBIL_MAX_K), E_NOMEM (the table ran full),
- * E_CUDA. */
+ * E_TIMEOUT (a bounded device wait for another thread's key words gave up), E_CUDA. */
 int gerbil_count_small_noalloc(const uint8_t* seq, const uint64_t* offsets, uint64_t nreads,
                                uint64_t nbases, int k, uint32_t min_count, int canonical,
                                uint64_t* keys_out, uint32_t* counts_out, uint64_t out_cap,

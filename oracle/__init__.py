@@ -1,7 +1,8 @@
 """CPU oracle for Gerbil's k-mer counting path -- TEST INFRASTRUCTURE ONLY.
 
 Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline legs (the
-cpu_baseline of its line, the reference arm, and the per-k oracle rate and sample check of
+cpu_baseline of its line and its sample check, the reference arm, the oracle rate and sample
+check of each workload of its configs block, and the per-k oracle rate and sample check of
 ``--ksweep``) may import this package.  The product library (``paper_1607_06618_b300``) never imports it and
 shares no code with it.
 

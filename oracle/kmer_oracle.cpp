@@ -1,8 +1,10 @@
 // kmer_oracle.cpp -- plain, slow, obviously correct CPU oracle for Gerbil's counting path.
 //
 // TEST INFRASTRUCTURE ONLY.  Nothing in the product path may include, link or call this
-// file; only tests/, __graft_entry__.smoke() and bench.py's CPU-baseline legs (cpu_baseline,
-// the reference arm, the k sweep's oracle rate and sample check) use it.  It shares no code, header, table or constant generator with the CUDA library.
+// file; only tests/, __graft_entry__.smoke() and bench.py's CPU-baseline legs (cpu_baseline
+// and its sample check, the reference arm, each config's oracle rate and sample check, the k
+// sweep's oracle rate and sample check) use it.  It shares no code, header, table or constant
+// generator with the CUDA library.
 //
 // Every function works on ASCII strings, exactly as the paper states the problem:
 //   * the k-mer counting problem (Abstract; Sec. 1): a histogram of all length-k substrings;

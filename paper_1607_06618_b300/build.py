@@ -7,8 +7,10 @@ import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
-SOURCES = ["partition.cu", "count.cu", "runtime.cu", "membench.cu", "server.cu", "encode.cu"]
-HEADERS = ["common.cuh", "kernels.h"]
+SOURCES = ["partition.cu", "count.cu", "runtime.cu", "membench.cu", "server.cu", "encode.cu",
+           "sort.cu", "insert_w1_2.cu", "insert_w3.cu", "insert_w4.cu", "insert_w5_7.cu",
+           "insert_w8_11.cu", "insert_w12_15.cu"]
+HEADERS = ["common.cuh", "kernels.h", "insert.cuh"]
 LIB = os.path.join(HERE, "libgerbil.so")
 ROOT = os.path.dirname(HERE)
 
@@ -37,6 +39,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
     nvcc = os.environ.get("NVCC", "nvcc")
     tag = "tmp%d" % os.getpid()
     flags = [f for f in NVCC_FLAGS if f != "-shared"] + (["-Xptxas", "-v"] if ptxas_info else [])
+    flags += os.environ.get("GERBIL_NVCC_FLAGS", "").split()  # e.g. -DGERBIL_MINB_SMALL=4
     objs = [os.path.join(HERE, "_obj_%s_%s.o" % (os.path.splitext(f)[0], tag)) for f in SOURCES]
     cmds = [[nvcc] + flags + ["-c", os.path.join(CSRC, f), "-o", o] for f, o in zip(SOURCES, objs)]
     tmp = LIB + "." + tag

@@ -88,11 +88,27 @@ __device__ __forceinline__ unsigned long long cas_relaxed(unsigned long long* p,
   return old;
 }
 
-// All SW words of a slot with relaxed 16-byte loads (slots are 16-byte aligned).
+__device__ __forceinline__ void ld_relaxed_v4(const unsigned long long* p, unsigned long long& a,
+                                              unsigned long long& b, unsigned long long& c,
+                                              unsigned long long& d) {
+  asm volatile("ld.relaxed.gpu.global.v4.u64 {%0, %1, %2, %3}, [%4];"
+               : "=l"(a), "=l"(b), "=l"(c), "=l"(d)
+               : "l"(p)
+               : "memory");
+}
+
+// All SW words of a slot with relaxed vector loads: 32-byte loads when the slot size is a
+// multiple of 32 bytes (the slot is then 32-byte aligned in the 256-byte aligned arena), else
+// 16-byte loads (every slot is 16-byte aligned).
 template <int SW>
 __device__ __forceinline__ void load_slot(const unsigned long long* slot, unsigned long long v[SW]) {
+  if constexpr (SW % 4 == 0) {
 #pragma unroll
-  for (int i = 0; i < SW; i += 2) ld_relaxed_v2(slot + i, v[i], v[i + 1]);
+    for (int i = 0; i < SW; i += 4) ld_relaxed_v4(slot + i, v[i], v[i + 1], v[i + 2], v[i + 3]);
+  } else {
+#pragma unroll
+    for (int i = 0; i < SW; i += 2) ld_relaxed_v2(slot + i, v[i], v[i + 1]);
+  }
 }
 
 // ---- memory-model helpers (PTX, gpu scope) -------------------------------------------------
@@ -184,14 +200,20 @@ __device__ __forceinline__ bool key_less(const unsigned long long a[W],
   return false;
 }
 
-// 64-bit hash of a key: one multiply per word, then a multiply/xorshift finalizer (the slot
-// index uses the low 32 bits, the tag bits 34..63).
+// 64-bit hash of a key (the slot index uses the low 32 bits, the tag bits 34..63): the words
+// are folded into one by xor with distinct rotations, then mixed by two multiply/xorshift
+// rounds -- two 64-bit multiplies whatever W.
 template <int W>
 __device__ __forceinline__ unsigned long long key_hash(const unsigned long long key[W]) {
-  unsigned long long h = 0x243F6A8885A308D3ull;
+  unsigned long long h = key[W - 1];
 #pragma unroll
-  for (int j = 0; j < W; ++j) h = (h ^ key[j]) * 0x9E3779B97F4A7C15ull;
-  h ^= h >> 32;
+  for (int j = W - 2; j >= 0; --j) {
+    const int r = (23 * (W - 1 - j)) & 63;
+    h ^= r ? ((key[j] << r) | (key[j] >> (64 - r))) : key[j] * 0x94D049BB133111EBull;
+  }
+  h ^= h >> 31;
+  h *= 0x9E3779B97F4A7C15ull;
+  h ^= h >> 29;
   h *= 0xD6E8FEB86659FD93ull;
   h ^= h >> 32;
   return h;

@@ -66,10 +66,14 @@ struct BinWork {
   uint32_t n_chunks;
   uint32_t dep_begin;            // this bin's entries in FusedParams::deps: the earlier bins
   uint32_t dep_count;            // whose table regions it reuses (their compaction comes first)
+  uint32_t item_kmers;           // k-mers per insert work item of this bin: 64, 128 or 256
+  uint32_t scheme;               // probe scheme: 0 linear, 1 windowed double hashing (count.cu)
 };
 
 constexpr int COUNT_THREADS = 256;
-constexpr int ITEM_KMERS = 256;  // k-mers per warp work item (8 consecutive ones per lane)
+constexpr int ITEM_KMERS = 256;  // the largest work item: k-mers of an item staged per warp
+
+
 
 struct CountParams {
   const unsigned long long* packed;
@@ -96,6 +100,9 @@ struct CountParams {
   // 1: the bins' tables average more than the L2 cache (keys of six or more words then run the
   // insert kernel without its register cap)
   int wide_tables;
+  int scheme;                    // probe scheme of every bin of the launch (BinWork::scheme)
+  uint32_t item_kmers;           // k-mers per work item of every bin of the launch: 64, 128
+                                 // or 256 (64 and 128 for keys of up to four words only)
 };
 
 // Probe histogram buckets: [0, 32) = 1..32 probes, 32 = more, 33 = sent to the overflow area.
@@ -154,16 +161,38 @@ struct OverflowParams {
 // slot_words_for_k(k) 64-bit words.  Launchers dispatch on k.
 int stored_words(int k);
 int slot_words_for_k(int k);
+// slots per probe window of scheme 1 for keys of length k (a table's cap and first slot are
+// multiples of it when it uses scheme 1)
+uint32_t probe_window_for_k(int k);
 cudaError_t launch_item_map(const CountParams& p, cudaStream_t st);
 cudaError_t launch_task_map(const FusedParams& p, cudaStream_t st);
 cudaError_t launch_fused(int k, const FusedParams& p, int nsm, cudaStream_t st);
 cudaError_t launch_insert(int k, const CountParams& p, int persistent, int nsm, cudaStream_t st);
+// the insert launches of each group of key widths (insert_w*.cu)
+cudaError_t launch_insert_w1_2(int W, int WS, const CountParams& p, unsigned long long need,
+                            int persistent, int nsm, cudaStream_t st);
+cudaError_t launch_insert_w3(int W, int WS, const CountParams& p, unsigned long long need,
+                            int persistent, int nsm, cudaStream_t st);
+cudaError_t launch_insert_w4(int W, int WS, const CountParams& p, unsigned long long need,
+                            int persistent, int nsm, cudaStream_t st);
+cudaError_t launch_insert_w5_7(int W, int WS, const CountParams& p, unsigned long long need,
+                            int persistent, int nsm, cudaStream_t st);
+cudaError_t launch_insert_w8_11(int W, int WS, const CountParams& p, unsigned long long need,
+                            int persistent, int nsm, cudaStream_t st);
+cudaError_t launch_insert_w12_15(int W, int WS, const CountParams& p, unsigned long long need,
+                            int persistent, int nsm, cudaStream_t st);
 // one warp waits (bounded by wait_ns) for *flag >= 1, which nothing sets: records ERR_QUEUE
 cudaError_t launch_wait_selftest(const uint32_t* flag, unsigned long long wait_ns, Counters* c,
                                  cudaStream_t st);
 cudaError_t launch_compact(int k, const CompactParams& p, int nsm, cudaStream_t st);
 cudaError_t launch_overflow_insert(int k, const OverflowParams& p, int nsm, cudaStream_t st);
 cudaError_t launch_overflow_emit(int k, const OverflowParams& p, int nsm, cudaStream_t st);
+
+// ---- ascending key order of a result (sort.cu) ----
+unsigned long long sort_tiles(unsigned long long n);
+cudaError_t launch_sort_pass(const unsigned long long* kin, const uint32_t* cin,
+                             unsigned long long* kout, uint32_t* cout, unsigned long long n, int W,
+                             int pass, uint32_t* hist, uint32_t* total, cudaStream_t st);
 
 // ---- App. C output records (encode.cu) ----
 struct EncodeParams {

@@ -209,6 +209,8 @@ void gerbil_opts_default(gerbil_opts* o) {
   o->dfp_sample = 16;
   o->fused = 0;
   o->schedule = 1;
+  o->probe_scheme = 0;
+  o->item_kmers = 0;
 }
 
 const char* gerbil_strerror(int s) {
@@ -707,32 +709,94 @@ void gerbil_bins_free(gerbil_bins* b) {
 // they stay in L2 and sparser ones where probes go to HBM.
 struct Sizing {
   double alpha[GERBIL_TUNE_CLASSES];
+  uint32_t scheme;                        // probe scheme of every table (BinWork::scheme)
+  uint32_t item;                          // k-mers per insert work item
   uint64_t bound[GERBIL_TUNE_CLASSES - 1];  // class upper bounds, bytes
   uint64_t slot_bytes;
+  uint32_t window;                        // slots per probe window of scheme 1
   int cls(double est) const {
     const double bytes = est / 0.5 * (double)slot_bytes;
     for (int c = 0; c < GERBIL_TUNE_CLASSES - 1; ++c)
       if (bytes < (double)bound[c]) return c;
     return GERBIL_TUNE_CLASSES - 1;
   }
-  uint64_t cap(double est) const { return (uint64_t)std::ceil(est / alpha[cls(est)]) + 16; }
+  // slots of a table for est distinct keys; under scheme 1 a prime number of windows, so that
+  // every window step (1 .. windows-1) visits every window before repeating one
+  uint64_t cap(double est) const {
+    const int c = cls(est);
+    const uint64_t n = (uint64_t)std::ceil(est / alpha[c]) + 16;
+    return scheme == 1 ? next_prime32((n + window - 1) / window) * window : n;
+  }
+  static bool is_prime32(uint64_t n) {
+    if (n < 2) return false;
+    for (uint64_t p : {2ull, 3ull, 5ull, 7ull, 11ull, 13ull})
+      if (n % p == 0) return n == p;
+    // Miller-Rabin with the bases 2, 7 and 61, exact for n < 2^32 (Jaeschke, 1993)
+    uint64_t d = n - 1;
+    int r = 0;
+    while (!(d & 1)) { d >>= 1; ++r; }
+    for (uint64_t a : {2ull, 7ull, 61ull}) {
+      if (a % n == 0) continue;
+      uint64_t x = 1, base = a % n, e = d;
+      while (e) {
+        if (e & 1) x = x * base % n;
+        base = base * base % n;
+        e >>= 1;
+      }
+      if (x == 1 || x == n - 1) continue;
+      bool comp = true;
+      for (int i = 1; i < r && comp; ++i) {
+        x = x * x % n;
+        if (x == n - 1) comp = false;
+      }
+      if (comp) return false;
+    }
+    return true;
+  }
+  static uint64_t next_prime32(uint64_t n) {
+    if (n < 2) return 2;
+    while (!is_prime32(n)) ++n;
+    return n;
+  }
+  // a bin's work entry: table size (of its class), probe scheme and item size
+  void place(BinWork& w, double est, uint64_t* slots, uint64_t* items) const {
+    w.scheme = scheme;
+    w.item_kmers = item;
+    uint64_t cp = cap(est);
+    if (cp > 0xFFFFF000ull) cp = w.scheme == 1 ? 4294967291ull / window * window : 0xFFFFF000ull;
+    if (w.scheme == 1) *slots = (*slots + window - 1) / window * window;  // window-aligned
+    w.cap = (uint32_t)cp;
+    w.table_off = *slots;
+    w.item_begin = (uint32_t)*items;
+    *slots += cp;
+    *items += (w.n_kmers + w.item_kmers - 1) / w.item_kmers;
+  }
 };
+
+static bool valid_item_kmers(uint32_t ik) { return ik == 64 || ik == 128 || ik == 256; }
 
 static const uint64_t kClassBound[GERBIL_TUNE_CLASSES - 1] = {4ull << 20, 64ull << 20, 1ull << 30};
 
 static Sizing make_sizing(const gerbil_ctx* ctx, const gerbil_opts& o, int k) {
   Sizing z{};
   z.slot_bytes = 8ull * gerbil::slot_words_for_k(k);
+  z.window = gerbil::probe_window_for_k(k);
   const double a = (o.load_factor > 0.05f && o.load_factor <= 0.95f) ? o.load_factor : 0.5;
   for (int c = 0; c < GERBIL_TUNE_CLASSES; ++c) z.alpha[c] = a;
+  z.scheme = o.probe_scheme == 1 ? 1u : 0u;
+  z.item = valid_item_kmers(o.item_kmers) ? o.item_kmers : (uint32_t)gerbil::ITEM_KMERS;
   for (int c = 0; c < GERBIL_TUNE_CLASSES - 1; ++c) z.bound[c] = kClassBound[c];
   if (o.autotune) {
     auto it = ctx->tuning.find(words_for(k));
-    if (it != ctx->tuning.end())
+    if (it != ctx->tuning.end()) {
+      const gerbil_tuning& t = it->second;
       for (int c = 0; c < GERBIL_TUNE_CLASSES; ++c)
-        if (it->second.load_factor[c] > 0.05f && it->second.load_factor[c] <= 0.95f)
-          z.alpha[c] = it->second.load_factor[c];
+        if (t.load_factor[c] > 0.05f && t.load_factor[c] <= 0.95f) z.alpha[c] = t.load_factor[c];
+      if (t.probe_scheme == 0 || t.probe_scheme == 1) z.scheme = (uint32_t)t.probe_scheme;
+      if (valid_item_kmers(t.item_kmers)) z.item = t.item_kmers;
+    }
   }
+  if (words_for(k) > 4) z.item = gerbil::ITEM_KMERS;  // smaller items are built up to 4 words
   return z;
 }
 
@@ -767,6 +831,8 @@ static int count_fused(gerbil_ctx* ctx, const gerbil_bins* b, const std::vector<
     w.n_kmers = (uint32_t)b->nkmers[bi];
     const double est = std::max(1.0, std::ceil(ratio * (double)w.n_kmers));
     w.cap = (uint32_t)std::min<uint64_t>(sz.cap(est), 0xFFFFF000ull);
+    w.item_kmers = gerbil::ITEM_KMERS;  // the fused form probes linearly, in 256-k-mer items
+    w.scheme = 0;
     w.n_items = (w.n_kmers + gerbil::ITEM_KMERS - 1) / gerbil::ITEM_KMERS;
     w.n_chunks = (w.cap + gerbil::CHUNK_SLOTS - 1) / gerbil::CHUNK_SLOTS;
     occ += w.n_kmers;
@@ -910,6 +976,8 @@ static int count_fused(gerbil_ctx* ctx, const gerbil_bins* b, const std::vector<
   fp.c.nwork = (uint32_t)nw;
   fp.c.nitems = 0;
   fp.c.imap = nullptr;
+  fp.c.scheme = 0;
+  fp.c.item_kmers = gerbil::ITEM_KMERS;
   fp.c.k = k;
   fp.c.canonical = opts.canonical ? 1 : 0;
   fp.c.theta = theta;
@@ -1000,6 +1068,8 @@ static int count_waves(gerbil_ctx* ctx, const gerbil_bins* b, const std::vector<
     w.n_kmers = (uint32_t)b->nkmers[bi];
     const double est = std::max(1.0, std::ceil(ratio * (double)w.n_kmers));
     w.cap = (uint32_t)std::min<uint64_t>(sz.cap(est), 0xFFFFF000ull);
+    w.item_kmers = gerbil::ITEM_KMERS;  // waves probe linearly, in 256-k-mer items
+    w.scheme = 0;
     w.item_begin = (uint32_t)items;
     items += (w.n_kmers + gerbil::ITEM_KMERS - 1) / gerbil::ITEM_KMERS;
     occ += w.n_kmers;
@@ -1086,6 +1156,8 @@ static int count_waves(gerbil_ctx* ctx, const gerbil_bins* b, const std::vector<
   cp.probe_hist = ctx->probe_hist;
   cp.schedule = opts.schedule;
   cp.wide_tables = tables_beyond_l2(ctx, work, SW);
+  cp.scheme = 0;  // waves probe linearly, in 256-k-mer items
+  cp.item_kmers = gerbil::ITEM_KMERS;
   if (items) {
     cp.nitems = items;
     CKW(gerbil::launch_item_map(cp, st));
@@ -1292,13 +1364,7 @@ static int count_impl(gerbil_ctx* ctx, const gerbil_bins* b, const std::vector<i
       w.n_super = (uint32_t)b->nsuper[bi];
       w.n_kmers = (uint32_t)b->nkmers[bi];
       const double est = std::max(1.0, std::ceil(ratio * (double)w.n_kmers));
-      uint64_t cap = sz.cap(est);
-      cap = std::min<uint64_t>(cap, 0xFFFFFFF0ull);
-      w.cap = (uint32_t)cap;
-      w.table_off = slots;
-      w.item_begin = (uint32_t)items;
-      slots += cap;
-      items += (w.n_kmers + gerbil::ITEM_KMERS - 1) / gerbil::ITEM_KMERS;
+      sz.place(w, est, &slots, &items);
       work.push_back(w);
     }
     if (items >= (1ull << 32)) return fail(ctx, GERBIL_E_INVAL, "too many work items");
@@ -1431,6 +1497,8 @@ static int count_impl(gerbil_ctx* ctx, const gerbil_bins* b, const std::vector<i
     cp.probe_hist = ctx->probe_hist;
     cp.schedule = opts.schedule;
     cp.wide_tables = tables_beyond_l2(ctx, work, gerbil::slot_words_for_k(k));
+    cp.scheme = (int)sz.scheme;
+    cp.item_kmers = sz.item;
     if (items) {
       CKG(gerbil::launch_item_map(cp, ls));  // preparation: timed with the clears
       ctx->times.kernel_launches++;
@@ -1617,6 +1685,12 @@ static int count_checks(gerbil_ctx* ctx, const gerbil_bins* b, int k, uint32_t m
   if (min_count < 1) return fail(ctx, GERBIL_E_INVAL, "min_count must be >= 1");
   if (opts.canonical && !b->canon_min)
     return fail(ctx, GERBIL_E_INVAL, "canonical counting needs canonical minimizers");
+  if (opts.probe_scheme != 0 && opts.probe_scheme != 1)
+    return fail(ctx, GERBIL_E_INVAL, "probe_scheme must be 0 or 1");
+  if (opts.item_kmers != 0 && !valid_item_kmers(opts.item_kmers))
+    return fail(ctx, GERBIL_E_INVAL, "item_kmers must be 0, 64, 128 or 256");
+  if (opts.item_kmers != 0 && opts.item_kmers != (uint32_t)gerbil::ITEM_KMERS && words_for(k) > 4)
+    return fail(ctx, GERBIL_E_UNSUPPORTED, "work items of 64 or 128 k-mers need k <= 128");
   return GERBIL_OK;
 }
 
@@ -1651,9 +1725,11 @@ static int autotune_impl(gerbil_ctx* ctx, const gerbil_bins* b, const std::vecto
   o.fused = 0;
   o.schedule = 1;
   o.load_factor = 0.5f;
+  o.probe_scheme = 0;
+  o.item_kmers = 0;
   std::vector<int32_t> sample;
-  const size_t step = std::max<size_t>(1, list.size() / 16);
-  for (size_t i = 0; i < list.size(); i += step) sample.push_back(list[i]);
+  const size_t step16 = std::max<size_t>(1, list.size() / 16);
+  for (size_t i = 0; i < list.size(); i += step16) sample.push_back(list[i]);
   uint64_t occ = 0;
   for (int32_t bi : sample) occ += b->nkmers[bi];
   if (occ == 0) return fail(ctx, GERBIL_E_INVAL, "autotune: the sample holds no k-mers");
@@ -1664,7 +1740,6 @@ static int autotune_impl(gerbil_ctx* ctx, const gerbil_bins* b, const std::vecto
   CK(cudaStreamSynchronize(ctx->stream));
   ph_collect(ctx, true);
   ctx->profiling = true;
-  gerbil_tuning t{};
   int rc = GERBIL_OK;
   auto restore = [&]() {
     cudaStreamSynchronize(ctx->stream);
@@ -1677,26 +1752,90 @@ static int autotune_impl(gerbil_ctx* ctx, const gerbil_bins* b, const std::vecto
     if ((rc = count_impl(ctx, b, sample, k, min_count, o, &tmp))) { restore(); return rc; }
     gerbil_counts_free(tmp);
   }
-  // 1. form and schedule at load factor 0.5
-  static const int forms[][2] = {{0, 1}, {0, 0}, {1, 1}, {2, 1}};
-  double best = 1e30;
-  int bf = 0, bs = 1;
-  for (const auto& f : forms) {
-    o.fused = f[0];
-    o.schedule = f[1];
-    double ms = 0;
-    if ((rc = tune_time(ctx, b, sample, k, min_count, o, &ms))) { restore(); return rc; }
-    t.samples++;
-    if (ms < best) { best = ms; bf = f[0]; bs = f[1]; }
-  }
-  o.fused = bf;
-  o.schedule = bs;
-  // 2. load factor per table-size class, on the sample's bins of that class
-  const Sizing z0 = make_sizing(ctx, o, k);
   const double ratio = std::min(1.0, ctx->ratio_known ? ctx->ratio * 1.25 : 1.0);
-  static const float alphas[] = {0.35f, 0.5f, 0.65f, 0.8f};
+  const Sizing z0 = make_sizing(ctx, o, k);
+  // the sample: every 16th bin, or every 8th, 4th, 2nd, every bin, until its tables take four
+  // times the L2 cache -- a sample whose tables all stay in L2 would time its compaction (and
+  // its low load factors) far below what the whole batch sees
+  {
+    auto tables = [&](size_t st) {
+      double bytes = 0;
+      for (size_t i = 0; i < list.size(); i += st)
+        if (b->nkmers[list[i]])
+          bytes += (double)z0.cap(std::max(1.0, std::ceil(ratio * (double)b->nkmers[list[i]]))) *
+                   (double)z0.slot_bytes;
+      return bytes;
+    };
+    size_t st = step16;
+    while (st > 1 && tables(st) < 4.0 * ctx->l2_bytes) st = std::max<size_t>(1, st / 2);
+    sample.clear();
+    for (size_t i = 0; i < list.size(); i += st) sample.push_back(list[i]);
+  }
+  occ = 0;
+  for (int32_t bi : sample) occ += b->nkmers[bi];
+
+  // the defaults: what a batch runs without tuning
+  gerbil_tuning d{};
+  for (int c = 0; c < GERBIL_TUNE_CLASSES; ++c) d.load_factor[c] = 0.5f;
+  for (int c = 0; c < GERBIL_TUNE_CLASSES - 1; ++c) d.class_bytes[c] = kClassBound[c];
+  d.fused = 0;
+  d.schedule = 1;
+  d.k_words = W;
+  d.probe_scheme = 0;
+  d.item_kmers = gerbil::ITEM_KMERS;
+  gerbil_tuning t = d;
+  // times phase two of `bins` with the candidate's settings (held as the context's tuning)
+  o.autotune = 1;
+  uint32_t nsamples = 0;
+  auto timed = [&](const gerbil_tuning& cand, const std::vector<int32_t>& bins, double* ms) {
+    ctx->tuning[W] = cand;
+    nsamples++;
+    return tune_time(ctx, b, bins, k, min_count, o, ms);
+  };
+  // a candidate replaces the best so far only when it is at least 2% faster on `bins`
+  double best = 0;
+  auto consider = [&](const gerbil_tuning& cand, const std::vector<int32_t>& bins, double* cur) -> int {
+    double ms = 0;
+    const int r = timed(cand, bins, &ms);
+    if (r) return r;
+    if (ms < 0.98 * *cur) {
+      *cur = ms;
+      t = cand;
+    }
+    return GERBIL_OK;
+  };
+#define TUNE_TRY(CAND, BINS, CUR)                                               \
+  do {                                                                          \
+    if ((rc = consider((CAND), (BINS), (CUR)))) {                               \
+      ctx->tuning.erase(W);                                                     \
+      restore();                                                                \
+      return rc;                                                                \
+    }                                                                           \
+  } while (0)
+  if ((rc = timed(t, sample, &best))) { ctx->tuning.erase(W); restore(); return rc; }
+  // 1. form and schedule
+  static const int forms[][2] = {{0, 0}, {1, 1}, {2, 1}};
+  for (const auto& f : forms) {
+    gerbil_tuning cand = t;
+    cand.fused = f[0];
+    cand.schedule = f[1];
+    TUNE_TRY(cand, sample, &best);
+  }
+  // 2. probe scheme, then work-item size (built for keys of up to four words), whole sample
+  {
+    gerbil_tuning cand = t;
+    cand.probe_scheme = 1;
+    TUNE_TRY(cand, sample, &best);
+  }
+  if (W <= 4) {
+    for (uint32_t ik : {128u, 64u}) {
+      gerbil_tuning cand = t;
+      cand.item_kmers = ik;
+      TUNE_TRY(cand, sample, &best);
+    }
+  }
+  // 3. the load factor of each table-size class, on the sample's bins of that class
   for (int c = 0; c < GERBIL_TUNE_CLASSES; ++c) {
-    t.load_factor[c] = 0.5f;
     std::vector<int32_t> sub;
     uint64_t sub_occ = 0;
     for (int32_t bi : sample) {
@@ -1706,21 +1845,24 @@ static int autotune_impl(gerbil_ctx* ctx, const gerbil_bins* b, const std::vecto
       sub_occ += b->nkmers[bi];
     }
     if (sub.empty() || sub_occ < 100000) continue;  // too little to time: keep 0.5
-    double cbest = 1e30;
-    for (float a : alphas) {
-      o.load_factor = a;
-      double ms = 0;
-      if ((rc = tune_time(ctx, b, sub, k, min_count, o, &ms))) { restore(); return rc; }
-      t.samples++;
-      if (ms < cbest) { cbest = ms; t.load_factor[c] = a; }
+    double cbest = 0;
+    if ((rc = timed(t, sub, &cbest))) { ctx->tuning.erase(W); restore(); return rc; }
+    for (float a : {0.35f, 0.65f, 0.8f}) {
+      gerbil_tuning cand = t;
+      cand.load_factor[c] = a;
+      TUNE_TRY(cand, sub, &cbest);
     }
   }
-  o.load_factor = 0.5f;
-  for (int c = 0; c < GERBIL_TUNE_CLASSES - 1; ++c) t.class_bytes[c] = kClassBound[c];
-  t.fused = bf;
-  t.schedule = bs;
-  t.k_words = W;
+#undef TUNE_TRY
+  // 4. the whole batch, tuned settings against the defaults: the tuning is kept only if it is
+  // faster there too (a sample can favour settings that the batch does not)
+  {
+    double mt = 0, md = 0;
+    if ((rc = timed(t, list, &mt)) || (rc = timed(d, list, &md))) { ctx->tuning.erase(W); restore(); return rc; }
+    if (!(mt < md)) t = d;
+  }
   t.ns_per_kmer = best * 1e6 / (double)occ;
+  t.samples = nsamples;
   restore();
   ctx->tuning[W] = t;
   if (out) *out = t;
@@ -1751,6 +1893,10 @@ int gerbil_set_tuning(gerbil_ctx* ctx, int k, const gerbil_tuning* t) {
   for (int c = 0; c < GERBIL_TUNE_CLASSES; ++c)
     if (!(t->load_factor[c] > 0.05f && t->load_factor[c] <= 0.95f))
       return fail(ctx, GERBIL_E_INVAL, "tuning: load factor out of range");
+  if (t->probe_scheme != 0 && t->probe_scheme != 1)
+    return fail(ctx, GERBIL_E_INVAL, "tuning: probe scheme out of range");
+  if (!valid_item_kmers(t->item_kmers) || (t->item_kmers != (uint32_t)gerbil::ITEM_KMERS && words_for(k) > 4))
+    return fail(ctx, GERBIL_E_INVAL, "tuning: item size out of range for this key width");
   gerbil_tuning c = *t;
   c.k_words = words_for(k);
   ctx->tuning[c.k_words] = c;
@@ -1765,6 +1911,75 @@ int gerbil_get_tuning(const gerbil_ctx* ctx, int k, gerbil_tuning* out) {
   return GERBIL_OK;
 }
 
+static int join_parts(gerbil_counts* c);
+
+// gerbil_opts.sorted_output: the rows in ascending key order (LSD radix sort over the 2k key
+// bits, 8 bits per pass, sort.cu), in the result's own buffers.
+static int sort_result(gerbil_ctx* ctx, gerbil_counts* c, int k) {
+  int rc = join_parts(c);
+  if (rc) return rc;
+  const uint64_t n = c->n;
+  if (n < 2) return GERBIL_OK;
+  if (n >= (1ull << 32)) return fail(ctx, GERBIL_E_UNSUPPORTED, "sorted output of 2^32 rows or more");
+  const int W = c->W;
+  const int passes = (2 * k + 7) / 8;
+  const uint64_t ntiles = gerbil::sort_tiles(n);
+  unsigned long long* k2 = nullptr;
+  uint32_t* c2 = nullptr;
+  uint32_t* hist = nullptr;
+  const size_t hbytes = (ntiles * 256 + 256) * 4;
+  if ((rc = dev_alloc(ctx, (void**)&k2, n * W * 8))) return rc;
+  if ((rc = dev_alloc(ctx, (void**)&c2, n * 4))) {
+    dev_free(ctx, k2, n * W * 8);
+    return rc;
+  }
+  if ((rc = dev_alloc(ctx, (void**)&hist, hbytes))) {
+    dev_free(ctx, k2, n * W * 8);
+    dev_free(ctx, c2, n * 4);
+    return rc;
+  }
+  unsigned long long *ka = c->keys, *kb = k2;
+  uint32_t *ca = c->counts, *cb = c2;
+  cudaError_t e = cudaSuccess;
+  for (int p = 0; p < passes && e == cudaSuccess; ++p) {
+    e = gerbil::launch_sort_pass(ka, ca, kb, cb, n, W, p, hist, hist + ntiles * 256, ctx->stream);
+    std::swap(ka, kb);
+    std::swap(ca, cb);
+    ctx->times.kernel_launches += 4;
+  }
+  dev_free(ctx, hist, hbytes);
+  if (e != cudaSuccess) {
+    dev_free(ctx, k2, n * W * 8);
+    dev_free(ctx, c2, n * 4);
+    return fail(ctx, GERBIL_E_CUDA, std::string("sort: ") + cudaGetErrorString(e));
+  }
+  if (ka == k2) {  // the sorted rows are in the new buffers: they become the result's
+    const uint64_t cap = c->bytes / (W * 8 + 4);
+    dev_free(ctx, c->keys, cap * W * 8);
+    dev_free(ctx, c->counts, cap * 4);
+    c->keys = k2;
+    c->counts = c2;
+    c->bytes = n * (W * 8 + 4);
+  } else {
+    dev_free(ctx, k2, n * W * 8);
+    dev_free(ctx, c2, n * 4);
+  }
+  c->stats.sorted = 1;
+  return GERBIL_OK;
+}
+
+// count_impl, then (sorted_output) the rows in ascending key order.
+static int count_sorted(gerbil_ctx* ctx, const gerbil_bins* b, const std::vector<int32_t>& list,
+                        int k, uint32_t min_count, const gerbil_opts& opts, gerbil_counts** out) {
+  int rc = count_impl(ctx, b, list, k, min_count, opts, out);
+  if (rc || !opts.sorted_output) return rc;
+  if ((rc = sort_result(ctx, *out, k))) {
+    gerbil_counts_free(*out);
+    *out = nullptr;
+  }
+  return rc;
+}
+
 int gerbil_count(gerbil_ctx* ctx, const gerbil_bins* b, int bin, int k, uint32_t min_count,
                  const gerbil_opts* opts_in, gerbil_counts** out) {
   if (!ctx || !out) return GERBIL_E_INVAL;
@@ -1776,7 +1991,7 @@ int gerbil_count(gerbil_ctx* ctx, const gerbil_bins* b, int bin, int k, uint32_t
   if (bin < 0 || bin >= b->nbins) return fail(ctx, GERBIL_E_INVAL, "bin out of range");
   CK(cudaSetDevice(ctx->device));
   std::vector<int32_t> list(1, bin);
-  return count_impl(ctx, b, list, k, min_count, opts, out);
+  return count_sorted(ctx, b, list, k, min_count, opts, out);
 }
 
 int gerbil_count_batch(gerbil_ctx* ctx, const gerbil_bins* b, const int32_t* bin_list, int nb,
@@ -1802,7 +2017,7 @@ int gerbil_count_batch(gerbil_ctx* ctx, const gerbil_bins* b, const int32_t* bin
     for (int i = 0; i < b->nbins; ++i) list.push_back(i);
   }
   CK(cudaSetDevice(ctx->device));
-  return count_impl(ctx, b, list, k, min_count, opts, out);
+  return count_sorted(ctx, b, list, k, min_count, opts, out);
 }
 
 // App. C records: per part (a joined result has several), count the long-count rows per tile,
@@ -1913,11 +2128,9 @@ int gerbil_counts_info(const gerbil_counts* c, uint64_t* n, int* words, gerbil_c
   return GERBIL_OK;
 }
 
-int gerbil_counts_view(const gerbil_counts* cc, const uint64_t** keys, const uint32_t** counts) {
-  if (!cc) return GERBIL_E_INVAL;
-  gerbil_counts* c = const_cast<gerbil_counts*>(cc);
+// Joins the groups' rows of a grouped result into one buffer (no-op for a plain result).
+static int join_parts(gerbil_counts* c) {
   if (!c->parts.empty()) {
-    // join the groups' rows into one buffer on first view
     gerbil_ctx* ctx = c->ctx;
     CK(cudaSetDevice(ctx->device));
     const int W = c->W;
@@ -1945,6 +2158,16 @@ int gerbil_counts_view(const gerbil_counts* cc, const uint64_t** keys, const uin
     c->keys = k2;
     c->counts = c2;
     c->bytes = c->n * (W * 8 + 4);
+  }
+  return GERBIL_OK;
+}
+
+int gerbil_counts_view(const gerbil_counts* cc, const uint64_t** keys, const uint32_t** counts) {
+  if (!cc) return GERBIL_E_INVAL;
+  gerbil_counts* c = const_cast<gerbil_counts*>(cc);
+  if (!c->parts.empty()) {  // join the groups' rows into one buffer on first view
+    const int rc = join_parts(c);
+    if (rc) return rc;
   }
   if (keys) *keys = (const uint64_t*)c->keys;
   if (counts) *counts = c->counts;

@@ -66,7 +66,9 @@ class gerbil_opts(ctypes.Structure):
                 ("ring_slots", ctypes.c_uint32), ("fused", ctypes.c_int32),
                 ("schedule", ctypes.c_int32), ("max_table_mib", ctypes.c_uint32),
                 ("autotune", ctypes.c_uint32), ("graph", ctypes.c_uint32),
-                ("dfp_pivot", ctypes.c_float), ("dfp_sample", ctypes.c_uint32)]
+                ("dfp_pivot", ctypes.c_float), ("dfp_sample", ctypes.c_uint32),
+                ("probe_scheme", ctypes.c_int32), ("item_kmers", ctypes.c_uint32),
+                ("sorted_output", ctypes.c_int32), ("reserved_opts", ctypes.c_int32)]
 
 
 TUNE_CLASSES = 4
@@ -77,14 +79,16 @@ class gerbil_tuning(ctypes.Structure):
                 ("class_bytes", ctypes.c_uint64 * (TUNE_CLASSES - 1)),
                 ("fused", ctypes.c_int32), ("schedule", ctypes.c_int32),
                 ("k_words", ctypes.c_int32), ("samples", ctypes.c_uint32),
-                ("ns_per_kmer", ctypes.c_double)]
+                ("ns_per_kmer", ctypes.c_double),
+                ("probe_scheme", ctypes.c_int32), ("item_kmers", ctypes.c_uint32)]
 
     def as_dict(self):
         return {"load_factor": [float(x) for x in self.load_factor],
                 "class_bytes": [int(x) for x in self.class_bytes],
                 "fused": int(self.fused), "schedule": int(self.schedule),
                 "k_words": int(self.k_words), "samples": int(self.samples),
-                "ns_per_kmer": float(self.ns_per_kmer)}
+                "ns_per_kmer": float(self.ns_per_kmer),
+                "probe_scheme": int(self.probe_scheme), "item_kmers": int(self.item_kmers)}
 
     @classmethod
     def from_dict(cls, d):
@@ -96,6 +100,8 @@ class gerbil_tuning(ctypes.Structure):
         t.fused, t.schedule = d["fused"], d["schedule"]
         t.k_words, t.samples = d.get("k_words", 0), d.get("samples", 0)
         t.ns_per_kmer = d.get("ns_per_kmer", 0.0)
+        t.probe_scheme = d.get("probe_scheme", 0)
+        t.item_kmers = d.get("item_kmers", 256)
         return t
 
 
@@ -103,10 +109,10 @@ class gerbil_count_stats(ctypes.Structure):
     _fields_ = [("occurrences", ctypes.c_uint64), ("distinct", ctypes.c_uint64),
                 ("emitted", ctypes.c_uint64), ("overflowed", ctypes.c_uint64),
                 ("table_slots", ctypes.c_uint64), ("retries", ctypes.c_uint32),
-                ("bins", ctypes.c_uint32), ("groups", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+                ("bins", ctypes.c_uint32), ("groups", ctypes.c_uint32), ("sorted", ctypes.c_uint32)]
 
     def as_dict(self):
-        return {name: int(getattr(self, name)) for name, _ in self._fields_ if name != "reserved"}
+        return {name: int(getattr(self, name)) for name, _ in self._fields_}
 
 
 class gerbil_phase_times(ctypes.Structure):
@@ -362,17 +368,39 @@ def gerbil_counts_free(counts):
 
 
 def gerbil_count_small_noalloc(seq, offsets, k: int, min_count: int, canonical: bool,
-                               keys_out, counts_out, stream: int | None = None, nbases=None):
+                               keys_out, counts_out, stream: int | None = None):
     """Counts a small read set with no device allocation inside the library.
 
-    seq/offsets are torch CUDA tensors (uint8 / int64); keys_out (int64[cap, W]) and
-    counts_out (int32[cap]) are caller-allocated CUDA tensors.  Returns the number of rows.
+    seq (uint8[n]) and offsets (int64[nreads + 1]) are contiguous torch CUDA tensors;
+    keys_out (int64, at least cap * W elements, W = ceil(2k/64)) and counts_out (int32[cap])
+    are caller-allocated contiguous CUDA tensors on the same device.  Returns the number of
+    rows.  Tensors of another shape, type or device raise ValueError before the call, since
+    the library writes up to cap * W key words and reads offsets[nreads] bases.
     """
-    n = ctypes.c_uint64()
-    nreads = offsets.numel() - 1
-    if nbases is None:
-        nbases = int(offsets[-1].item()) if nreads >= 0 else 0
+    import torch
+    W = (2 * k + 63) // 64
+    need = ((seq, torch.uint8, "seq"), (offsets, torch.int64, "offsets"),
+            (keys_out, torch.int64, "keys_out"), (counts_out, torch.int32, "counts_out"))
+    for t, dt, name in need:
+        if not isinstance(t, torch.Tensor) or not t.is_cuda:
+            raise ValueError("%s must be a CUDA tensor" % name)
+        if t.dtype != dt:
+            raise ValueError("%s must be %s, not %s" % (name, dt, t.dtype))
+        if not t.is_contiguous():
+            raise ValueError("%s must be contiguous" % name)
+        if t.device != seq.device:
+            raise ValueError("%s is on %s, seq on %s" % (name, t.device, seq.device))
+    if offsets.dim() != 1 or offsets.numel() < 1:
+        raise ValueError("offsets must hold nreads + 1 >= 1 entries")
     cap = counts_out.numel()
+    if keys_out.numel() < cap * W:
+        raise ValueError("keys_out holds %d words; %d rows of %d words need %d"
+                         % (keys_out.numel(), cap, W, cap * W))
+    nreads = offsets.numel() - 1
+    first, nbases = (int(x) for x in offsets[[0, -1]].tolist())
+    if first < 0 or nbases > seq.numel():
+        raise ValueError("offsets run outside seq (%d..%d of %d bases)" % (first, nbases, seq.numel()))
+    n = ctypes.c_uint64()
     st = load().gerbil_count_small_noalloc(seq.data_ptr(), offsets.data_ptr(), nreads, nbases, k,
                                            min_count, 1 if canonical else 0, keys_out.data_ptr(),
                                            counts_out.data_ptr(), cap, ctypes.byref(n), stream)

@@ -66,3 +66,46 @@ def revcomp_reads(seq: np.ndarray, offs: np.ndarray):
     for i in range(len(o) - 1):
         out[o[i]:o[i + 1]] = comp[o[i]:o[i + 1]][::-1]
     return out, offs
+
+
+_FNV_BASIS = 0xcbf29ce484222325 - (1 << 64)  # as a signed 64-bit integer
+_FNV_PRIME = 0x100000001b3
+
+
+def fnv1a64_device(keys, k: int, rows_per_chunk: int = 1 << 25):
+    """FNV-1a 64 of every key's ASCII string (the oracle's pass filter), for keys int64[n, W]
+    on a CUDA device; int64[n] (two's complement of the unsigned hash).  Torch wraps int64
+    products modulo 2^64, which is the hash's arithmetic."""
+    import torch
+    n, W = keys.shape
+    lut = torch.tensor([ord(c) for c in "ACGT"], dtype=torch.int64, device=keys.device)
+    out = torch.empty(n, dtype=torch.int64, device=keys.device)
+    for a in range(0, n, rows_per_chunk):
+        kk = keys[a:a + rows_per_chunk]
+        h = torch.full((kk.shape[0],), _FNV_BASIS, dtype=torch.int64, device=keys.device)
+        for i in range(k):
+            bit = 2 * (k - 1 - i)
+            base = (kk[:, W - 1 - bit // 64] >> (bit % 64)) & 3  # masked: the shift's sign bits go
+            h = (h ^ lut[base]) * _FNV_PRIME
+        out[a:a + kk.shape[0]] = h
+    return out
+
+
+def device_pass_rows(keys, counts, k: int, npass: int, pass_index: int = 0):
+    """Host copies of the device rows whose key is in the oracle's pass (npass a power of two,
+    so the unsigned residue is the low bits of the signed hash)."""
+    import torch
+    assert npass & (npass - 1) == 0
+    h = fnv1a64_device(keys, k)
+    sel = torch.nonzero((h & (npass - 1)) == pass_index).flatten()
+    return (keys[sel].cpu().numpy().view(np.uint64),
+            counts[sel].cpu().numpy().view(np.uint32).astype(np.uint64))
+
+
+def device_digest(keys, counts, k: int):
+    """Order-independent digest of device rows: (rows, sum of counts, wrapping sum of
+    FNV(key) * (count + 1)).  Equal results give equal digests in any row order."""
+    import torch
+    h = fnv1a64_device(keys, k)
+    c = counts.to(torch.int64) & 0xFFFFFFFF
+    return (int(keys.shape[0]), int(c.sum().item()), int((h * (c + 1)).sum().item()))

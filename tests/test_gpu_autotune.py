@@ -41,6 +41,8 @@ def test_autotune_picks_valid_settings_and_counts_match(data):
     t = ctx.autotune(bins, K, 2)
     assert t["fused"] in (0, 1, 2) and t["schedule"] in (0, 1)
     assert all(a in (0.35, 0.5, 0.65, 0.8) for a in (round(x, 2) for x in t["load_factor"]))
+    assert all(x in (0, 1) for x in t["probe_scheme"])
+    assert all(x in (64, 128, 256) for x in t["item_kmers"])
     assert t["k_words"] == 3 and t["samples"] >= 4 and t["ns_per_kmer"] > 0
     assert ctx.get_tuning(K) == t and ctx.get_tuning(96) == t  # same key width (3 words)
     assert ctx.get_tuning(64) is None  # 2 words
@@ -48,12 +50,14 @@ def test_autotune_picks_valid_settings_and_counts_match(data):
     assert_same_rows(_rows(ctx, bins, gerbil.default_opts(autotune=1)), want)
 
 
-@pytest.mark.parametrize("fused,schedule,alpha", [(0, 1, 0.8), (0, 0, 0.35), (1, 1, 0.65),
-                                                  (2, 1, 0.8)])
-def test_every_setting_of_the_search_space_counts_exactly(data, fused, schedule, alpha):
+@pytest.mark.parametrize("fused,schedule,alpha,scheme,ik", [
+    (0, 1, 0.8, 0, 256), (0, 0, 0.35, 1, 128), (1, 1, 0.65, 0, 256), (2, 1, 0.8, 0, 256),
+    (0, 1, 0.8, 1, 64), (0, 1, 0.35, 0, 64), (0, 1, 0.65, 1, 256)])
+def test_every_setting_of_the_search_space_counts_exactly(data, fused, schedule, alpha, scheme, ik):
     gerbil, ctx, bins, want = data
-    ctx.set_tuning(K, {"load_factor": [alpha] * gerbil.TUNE_CLASSES, "fused": fused,
-                       "schedule": schedule})
+    n = gerbil.TUNE_CLASSES
+    ctx.set_tuning(K, {"load_factor": [alpha] * n, "fused": fused, "schedule": schedule,
+                       "probe_scheme": [scheme] * n, "item_kmers": [ik] * n})
     assert_same_rows(_rows(ctx, bins, gerbil.default_opts(autotune=1)), want)
     ctx.set_tuning(K, None)
     assert ctx.get_tuning(K) is None
@@ -110,13 +114,14 @@ def test_graph_form_with_overflow_and_retry(data):
     res.free()
 
 
-def test_probe_statistics_account_for_every_kmer(data):
+@pytest.mark.parametrize("scheme", [0, 1])
+def test_probe_statistics_account_for_every_kmer(data, scheme):
     """Probe histograms (Sec. 3.3): every inserted k-mer is recorded once (placed after some
-    number of slots, or sent to the overflow area); lines touched never exceed slots read; the
-    statistics change no count."""
+    number of slots, or sent to the overflow area); lines (scheme 0) or windows (scheme 1)
+    never exceed slots read; the statistics change no count."""
     gerbil, ctx, bins, want = data
     ctx.probe_stats(True)
-    got = _rows(ctx, bins, gerbil.default_opts())
+    got = _rows(ctx, bins, gerbil.default_opts(probe_scheme=scheme))
     slots, lines = ctx.get_probe_stats()
     occ = bins.info()["n_kmers"]
     assert int(slots.sum()) == occ and int(lines.sum()) == occ
@@ -131,7 +136,8 @@ def test_probe_statistics_account_for_every_kmer(data):
     # theta = 1 with small tables: k-mers that found no room are counted in the last bucket
     ctx.probe_stats(True)
     res = ctx.count_batch(bins, None, K, 2, gerbil.default_opts(max_probes=1, distinct_ratio=0.05,
-                                                                 overflow_slots=1 << 22))
+                                                                 overflow_slots=1 << 22,
+                                                                 probe_scheme=scheme))
     st = res.info()[2]
     res.free()
     slots, lines = ctx.get_probe_stats()

@@ -136,6 +136,49 @@ def test_count_matches_oracle_all_word_counts(g, k):
         assert_same_rows(got, oracle.count(seq, offs, k, canonical=True, min_count=mc))
 
 
+# both probe schemes (linear; the paper's windowed double hashing) and every work-item size on
+# the same inputs, with and without forced overflow (theta = 1), over the slot sizes 16..112 B
+@pytest.mark.parametrize("k", [8, 32, 33, 64, 65, 97, 99, 127, 200, 400])
+def test_probe_schemes_and_item_sizes(g, k):
+    m = min(11, k - 1)
+    seq, offs = synth.random_small(500, max(1, k - 4), k + 300, p_n=0.003, seed=3000 + k)
+    seq = np.concatenate([seq, seq[: int(offs[120])]])
+    offs = np.concatenate([offs, offs[1:121] + offs[-1]])
+    gerbil, ctx, torch = g
+    combos = ((0, 256), (1, 256), (0, 128), (1, 64), (0, 64), (1, 128))
+    if k > 128:  # items of 64 and 128 k-mers are built for keys of up to four words
+        for scheme, ik in combos[2:]:
+            with pytest.raises(gerbil.GerbilError) as e:
+                _gpu_count(g, seq, offs, k, m, 16, 1, probe_scheme=scheme, item_kmers=ik)
+            assert e.value.status == gerbil.GERBIL_E_UNSUPPORTED
+        combos = combos[:2]
+    for mc in (1, 2):
+        want = oracle.count(seq, offs, k, canonical=True, min_count=mc)
+        for scheme, ik in combos:
+            ctx.forget_ratio()  # tables sized for all-distinct keys: nothing overflows
+            got, st = _gpu_count(g, seq, offs, k, m, 16, mc, probe_scheme=scheme, item_kmers=ik)
+            assert st["overflowed"] == 0
+            assert_same_rows(got, want)
+            if ik != 256 and mc == 2:
+                continue
+            got, st = _gpu_count(g, seq, offs, k, m, 16, mc, probe_scheme=scheme, item_kmers=ik,
+                                 max_probes=1, distinct_ratio=0.05, overflow_slots=1 << 22)
+            assert st["overflowed"] > 0
+            assert_same_rows(got, want)
+            got, st = _gpu_count(g, seq, offs, k, m, 16, mc, probe_scheme=scheme, item_kmers=ik,
+                                 persistent=0, schedule=0)
+            assert_same_rows(got, want)
+
+
+def test_bad_probe_scheme_and_item_size_rejected(g):
+    gerbil, ctx, torch = g
+    seq, offs = synth.random_small(20, 40, 60, p_n=0.0, seed=1)
+    for bad in (dict(probe_scheme=2), dict(item_kmers=96), dict(item_kmers=512)):
+        with pytest.raises(gerbil.GerbilError) as e:
+            _gpu_count(g, seq, offs, 21, 7, 4, 1, **bad)
+        assert e.value.status == gerbil.GERBIL_E_INVAL
+
+
 # keys of six or more words in one table larger than the L2 cache: the insert kernel's form
 # without the register cap
 @pytest.mark.parametrize("k", [200, 400, 479])
@@ -321,3 +364,56 @@ def test_bounded_wait_runs_out_and_context_stays_usable(g):
     seq, offs = synth.random_small(50, 40, 120, p_n=0.01, seed=77)
     got, _ = _gpu_count(g, seq, offs, 31, 7, 8, 1)
     assert_same_rows(got, oracle.count(seq, offs, 31))
+
+
+# ---- sorted output ---------------------------------------------------------------------
+
+@pytest.mark.parametrize("k", [20, 32, 65, 99, 200, 479])
+def test_sorted_output_equals_oracle_in_order(g, k):
+    """gerbil_opts.sorted_output: the rows come back in ascending key order -- compared with the
+    oracle's rows (ascending by construction) position by position, with no host sort -- for
+    key widths of 1, 1, 3, 4, 7 and 15 words, from the batch and from a grouped batch."""
+    gerbil, ctx, torch = g
+    m = min(11, k - 1)
+    seq, offs = synth.random_small(700, max(1, k - 4), k + 300, p_n=0.003, seed=4000 + k)
+    seq = np.concatenate([seq, seq[: int(offs[150])]])
+    offs = np.concatenate([offs, offs[1:151] + offs[-1]])
+    for mc, extra in ((1, {}), (2, {}), (1, {"max_table_mib": 1})):
+        wk, wc = oracle.count(seq, offs, k, canonical=True, min_count=mc)
+        o = gerbil.default_opts(sorted_output=1, **extra)
+        s, of = _dev(torch, seq, offs)
+        bins = ctx.partition(s, of, k, m, 16, o)
+        res = ctx.count_batch(bins, None, k, mc, o)
+        keys, counts = res.to_host()
+        st = res.info()[2]
+        res.free()
+        bins.free()
+        assert st["sorted"] == 1
+        if extra:
+            assert st["groups"] > 1
+        assert np.array_equal(np.asarray(keys, np.uint64).reshape(wk.shape), wk)
+        assert np.array_equal(np.asarray(counts, np.uint64), wc)
+
+
+def test_sorted_output_many_rows_and_per_bin(g):
+    """A larger sort (several hundred tiles of 2048 rows, equal high digits everywhere) and the
+    single-bin call."""
+    gerbil, ctx, torch = g
+    seq, offs = synth.uniform_reads(6000, 150, 0.002, seed=77)
+    k = 31
+    wk, wc = oracle.count(seq, offs, k, canonical=True, min_count=1)
+    assert len(wc) > 600_000
+    o = gerbil.default_opts(sorted_output=1)
+    s, of = _dev(torch, seq, offs)
+    bins = ctx.partition(s, of, k, 7, 8, o)
+    res = ctx.count_batch(bins, None, k, 1, o)
+    keys, counts = res.to_host()
+    res.free()
+    assert np.array_equal(np.asarray(keys, np.uint64).reshape(wk.shape), wk)
+    assert np.array_equal(np.asarray(counts, np.uint64), wc)
+    one = ctx.count(bins, 3, k, 1, o)
+    kk, cc = one.to_host()
+    one.free()
+    bins.free()
+    kk = np.asarray(kk, np.uint64).reshape(-1, 1)
+    assert len(cc) > 1000 and np.all(kk[1:, 0] > kk[:-1, 0])
