@@ -86,6 +86,10 @@ def _args():
     ap.add_argument("--config-sample-windows", type=int, default=300_000,
                     help="k-mer windows of each config's oracle-checked read sample")
     ap.add_argument("--no-serving", action="store_true", help="configs block without serving")
+    ap.add_argument("--steps-only", action="store_true",
+                    help="only the timed steps of the headline workload (for launch lists): no "
+                         "membench, batched-vs-per-bin, probe statistics, App. C, e2e, oracle "
+                         "or configs block")
     return ap.parse_args()
 
 
@@ -123,8 +127,10 @@ def _peaks():
 
 
 def _src_sha():
+    """sha-256 (16 hex digits) of the phase-two kernel sources."""
     h = hashlib.sha256()
-    for f in ("count.cu", "common.cuh", "kernels.h"):
+    for f in ("count.cu", "insert.cuh", "insert_w1_2.cu", "insert_w3.cu", "insert_w4.cu",
+              "insert_w5_7.cu", "insert_w8_11.cu", "insert_w12_15.cu", "common.cuh", "kernels.h"):
         with open(os.path.join(ROOT, "paper_1607_06618_b300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -521,7 +527,7 @@ def main_ours(a, world, rank, local):
     # ceilings of the operations the insert kernel is made of (random 32-byte slot load, then
     # an atomic add on it), L2-resident and HBM-sized, measured on this GPU
     membench = None
-    if rank == 0:
+    if rank == 0 and not a.steps_only:
         membench = {}
         for label, nbytes in (("l2_32MB", 32 << 20), ("hbm_4GB", 4 << 30)):
             for op, name in ((0, "red"), (1, "load32"), (2, "load32_then_red"), (3, "cas")):
@@ -536,7 +542,7 @@ def main_ours(a, world, rank, local):
 
     # batched (one persistent launch) vs one count call per bin, phase two only
     bvp = None
-    if a.per_bin_steps > 0 and rank == 0:
+    if a.per_bin_steps > 0 and rank == 0 and not a.steps_only:
         variants = [("batched_ms", opts), ("batched_fused_ms", gerbil.default_opts(fused=1)),
                     ("batched_static_schedule_ms", gerbil.default_opts(schedule=0)),
                     ("batched_waves_ms", gerbil.default_opts(fused=2)),
@@ -554,7 +560,7 @@ def main_ours(a, world, rank, local):
     # read / within the first line or window, the most slots / lines any k-mer needed, and the
     # phase-two time of each scheme; recorded outside the timed region
     probes = None
-    if rank == 0:
+    if rank == 0 and not a.steps_only:
         bins = ctx.partition(s_dev, o_dev, k, m, nbins, opts, bb)
 
         def _maxb(h):
@@ -589,7 +595,7 @@ def main_ours(a, world, rank, local):
 
     # App. C output records of one step's result, written on the device (event-timed)
     appc = None
-    if rank == 0:
+    if rank == 0 and not a.steps_only:
         bins = ctx.partition(s_dev, o_dev, k, m, nbins, opts, bb)
         res = ctx.count_batch(bins, None, k, mc, opts)
         res.encode_records(k, device=True)  # warm-up
@@ -611,7 +617,7 @@ def main_ours(a, world, rank, local):
     # --e2e-workers W > 1, W host threads each drive a context of their own (own CUDA stream
     # and pinned buffers), so one step's copies overlap another step's kernels.
     e2e = None
-    if a.e2e_steps > 0:
+    if a.e2e_steps > 0 and not a.steps_only:
         import threading
         nrow = info["emitted"]
         nw = max(1, a.e2e_workers)
@@ -683,7 +689,7 @@ def main_ours(a, world, rank, local):
     # the oracle on one core over a bounded sample (cpu_baseline), and the same reads counted
     # on the GPU: row-for-row equality
     cpu = None
-    if rank == 0 and not a.no_cpu_baseline:
+    if rank == 0 and not a.no_cpu_baseline and not a.steps_only:
         chk = _sample_check(gerbil, ctx, s_dev, o_dev, p, opts, a.cpu_sample_windows)
         cpu = {"value": chk["oracle_kmers_per_s"], "unit": UNIT, "cores": 1,
                "nproc": os.cpu_count(), "kind": "oracle",
@@ -697,7 +703,7 @@ def main_ours(a, world, rank, local):
 
     # the other workloads (configs 1, 3, 4) and the serving stream, each measured on its own
     configs = None
-    if rank == 0 and not a.no_configs:
+    if rank == 0 and not a.no_configs and not a.steps_only:
         configs = {}
         for name in CONFIG_WORKLOADS:
             configs[name] = run_config(a, name, local, hbm, peak_kind)

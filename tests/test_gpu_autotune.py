@@ -41,8 +41,7 @@ def test_autotune_picks_valid_settings_and_counts_match(data):
     t = ctx.autotune(bins, K, 2)
     assert t["fused"] in (0, 1, 2) and t["schedule"] in (0, 1)
     assert all(a in (0.35, 0.5, 0.65, 0.8) for a in (round(x, 2) for x in t["load_factor"]))
-    assert all(x in (0, 1) for x in t["probe_scheme"])
-    assert all(x in (64, 128, 256) for x in t["item_kmers"])
+    assert t["probe_scheme"] in (0, 1) and t["item_kmers"] in (64, 128, 256)
     assert t["k_words"] == 3 and t["samples"] >= 4 and t["ns_per_kmer"] > 0
     assert ctx.get_tuning(K) == t and ctx.get_tuning(96) == t  # same key width (3 words)
     assert ctx.get_tuning(64) is None  # 2 words
@@ -57,7 +56,7 @@ def test_every_setting_of_the_search_space_counts_exactly(data, fused, schedule,
     gerbil, ctx, bins, want = data
     n = gerbil.TUNE_CLASSES
     ctx.set_tuning(K, {"load_factor": [alpha] * n, "fused": fused, "schedule": schedule,
-                       "probe_scheme": [scheme] * n, "item_kmers": [ik] * n})
+                       "probe_scheme": scheme, "item_kmers": ik})
     assert_same_rows(_rows(ctx, bins, gerbil.default_opts(autotune=1)), want)
     ctx.set_tuning(K, None)
     assert ctx.get_tuning(K) is None
