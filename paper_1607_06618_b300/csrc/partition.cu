@@ -69,9 +69,11 @@ __global__ void boundary_kernel(const uint64_t* __restrict__ offsets, uint64_t n
 // One CTA owns the window starts [P0, P0+T) of the global base stream.  It stages the 2-bit
 // bases and masks it needs in shared memory and gives every m-mer a key: 0 if the m-mer holds
 // an undetermined base or straddles a read start, else 1 + its rank.  The sliding minimum of
-// the keys over w = k-m+1 m-mers (by doubling) is then 0 exactly for the windows that are not
-// counted (for m >= 2 every interior read start is straddled by one of the window's m-mers),
-// and 1 + the minimizer's rank otherwise.  Super-mer starts and ends come from two ballot
+// the keys over w = k-m+1 m-mers (van Herk / Gil-Werman: the m-mers are cut into blocks of w,
+// each with its running minima from the left and from the right, and a window, which spans
+// the end of one block and the start of the next, takes the minimum of one of each) is then 0
+// exactly for the windows that are not counted (for m >= 2 every interior read start is
+// straddled by one of the window's m-mers), and 1 + the minimizer's rank otherwise.  Super-mer starts and ends come from two ballot
 // masks; a super-mer never runs past the next multiple of L_max, so the CTA looks at most
 // L_max windows past its range.  Each super-mer becomes one record (start, k-mers, bin),
 // appended with one atomic per warp, and counted into its bin.
@@ -140,7 +142,9 @@ __device__ __forceinline__ uint32_t order_rank(uint32_t c, int m, int ordering,
   }
 }
 
-template <int MLEN>  // the minimizer length, so that every shift below is a constant
+// MLEN: the minimizer length, so that every shift below is a constant; KMC2: the ordering is
+// GERBIL_ORDER_KMC2 (the default), ranked inline instead of through order_rank's switch.
+template <int MLEN, bool KMC2>
 __global__ void __launch_bounds__(256) supermer_kernel(SupermerParams P) {
   extern __shared__ __align__(16) unsigned char smem[];
   const long long T = P.tile;
@@ -158,22 +162,19 @@ __global__ void __launch_bounds__(256) supermer_kernel(SupermerParams P) {
   const long long wlo = (O >= 0) ? (O >> 5) : -1;  // first staged word
   const int nsw = (int)(((O + NB - 1) >> 5) - wlo) + 2;
 
-  // shared memory: staged words and masks | PRE | SUF | [KEY if w <= 8] | sparse table over
-  // segment minima | SB | BB.  PRE and SUF are indexed through pidx(q) = q + q/32, so that the
-  // eight stores of a thread's segment (stride 8 across the warp) hit distinct banks.
+  // shared memory: staged words and masks | PRE (the keys, then the running minima from the
+  // left within blocks of w) | SUF (from the right) | SB | BB.  PRE and SUF are indexed through
+  // pidx(q) = q + q/32, so that the eight stores of a thread's segment (stride 8 across the
+  // warp) hit distinct banks.
   const int NSEG = (NQ + SEG - 1) / SEG;
   const int NQP = NQ + (NQ >> 5) + 1;
-  const int midmax = ((w - 1) / SEG) + 1;
-  const int LEV = 32 - __clz(midmax);
   unsigned long long* sw = reinterpret_cast<unsigned long long*>(smem);
   uint32_t* snm = reinterpret_cast<uint32_t*>(sw + nsw);
   uint32_t* sbm = snm + nsw;
   uint32_t* PRE = sbm + nsw;
   uint32_t* SUF = PRE + NQP;
-  uint32_t* KEY = SUF + NQP;
-  uint32_t* ST = KEY + (w <= SEG ? NQ : 0);
   const int nbw = (NW + 31) >> 5;
-  uint32_t* SB = ST + LEV * NSEG;
+  uint32_t* SB = SUF + NQP;
   uint32_t* BB = SB + nbw;
 
   const long long nwords = (long long)P.nwords;
@@ -187,8 +188,7 @@ __global__ void __launch_bounds__(256) supermer_kernel(SupermerParams P) {
   __syncthreads();
 
   // keys of the m-mers, SEG consecutive ones per thread, all cut from one 32-base window and
-  // its reverse complement; per segment the running minima from the left (PRE) and from the
-  // right (SUF) and the segment minimum (level 0 of the sparse table)
+  // its reverse complement, stored in PRE
   const int lbO = (int)(O - 32 * wlo);  // local base index of global base O
   const long long n = (long long)P.n;
   const uint32_t vmask = (1u << (2 * m)) - 1u;
@@ -204,71 +204,51 @@ __global__ void __launch_bounds__(256) supermer_kernel(SupermerParams P) {
     const unsigned long long win = bases64(sw, lb);
     const unsigned long long rcwin = rev2(~win);
     const uint32_t nm32 = bits32(snm, lb), bm32 = bits32(sbm, lb);
-    uint32_t key[SEG];
-    uint32_t pre = 0xFFFFFFFFu;
     const int pq0 = q0 + (q0 >> 5);  // pidx(q0); a segment never crosses a 32-boundary
 #pragma unroll
     for (int d = 0; d < SEG; ++d) {
       const int iq = q0 + d;
-      uint32_t kk = 0xFFFFFFFFu;  // past the tile: neutral
-      if (iq < NQ) {
-        kk = 0u;
-        bool ok = iq >= q_lo && iq < q_hi && ((nm32 << d) >> (32 - m)) == 0u;
-        if constexpr (m >= 2) ok = ok && ((bm32 << (d + 1)) >> (33 - m)) == 0u;  // no read start inside
-        if (ok) {
-          const uint32_t v = (uint32_t)(win >> (64 - 2 * m - 2 * d)) & vmask;
-          uint32_t c = v;
-          if (P.canon_min) {
-            const uint32_t rc = (uint32_t)(rcwin >> (2 * d)) & vmask;
-            c = rc < v ? rc : v;
-          }
-          kk = order_rank(c, m, P.ordering, P.rank_table) + 1u;
+      if (iq >= NQ) break;
+      uint32_t kk = 0u;
+      bool ok = iq >= q_lo && iq < q_hi && ((nm32 << d) >> (32 - m)) == 0u;
+      if constexpr (m >= 2) ok = ok && ((bm32 << (d + 1)) >> (33 - m)) == 0u;  // no read start inside
+      if (ok) {
+        const uint32_t v = (uint32_t)(win >> (64 - 2 * m - 2 * d)) & vmask;
+        uint32_t c = v;
+        if (P.canon_min) {
+          const uint32_t rc = (uint32_t)(rcwin >> (2 * d)) & vmask;
+          c = rc < v ? rc : v;
         }
+        if constexpr (KMC2) kk = (c | (kmc2_demoted(c, m) << 30)) + 1u;
+        else kk = order_rank(c, m, P.ordering, P.rank_table) + 1u;
       }
-      key[d] = kk;
-      pre = min(pre, kk);
-      if (iq < NQ) {
-        PRE[pq0 + d] = pre;
-        if (w <= SEG) KEY[iq] = kk;
-      }
+      PRE[pq0 + d] = kk;
     }
-    uint32_t suf = 0xFFFFFFFFu;
-#pragma unroll
-    for (int d = SEG - 1; d >= 0; --d) {
-      suf = min(suf, key[d]);
-      if (q0 + d < NQ) SUF[pq0 + d] = suf;
-    }
-    ST[seg] = pre;
   }
-  for (int l = 1; l < LEV; ++l) {
-    __syncthreads();
-    const uint32_t* src = ST + (l - 1) * NSEG;
-    uint32_t* dst = ST + l * NSEG;
-    const int half = 1 << (l - 1);
-    for (int j = threadIdx.x; j < NSEG; j += blockDim.x)
-      dst[j] = (j + half < NSEG) ? min(src[j], src[j + half]) : src[j];
+  __syncthreads();
+  // running minima within blocks of w m-mers, one thread per block: from the right into SUF,
+  // then from the left over the keys in place (PRE)
+  for (int b0 = threadIdx.x * w; b0 < NQ; b0 += blockDim.x * w) {
+    const int b1 = min(b0 + w, NQ);
+    uint32_t run = 0xFFFFFFFFu;
+    for (int q = b1 - 1; q >= b0; --q) {
+      run = min(run, PRE[q + (q >> 5)]);
+      SUF[q + (q >> 5)] = run;
+    }
+    run = 0xFFFFFFFFu;
+    for (int q = b0; q < b1; ++q) {
+      run = min(run, PRE[q + (q >> 5)]);
+      PRE[q + (q >> 5)] = run;
+    }
   }
   __syncthreads();
 
   // window minimum: 0 = a window with an undetermined base or a read start inside, else
-  // 1 + the minimizer's rank
+  // 1 + the minimizer's rank.  Window i covers m-mers i .. i+w-1: the end of i's block from i
+  // (SUF) and the start of the next block up to i+w-1 (PRE), or all of i's block when i starts it
   auto wmin = [&](int i) -> uint32_t {
-    const int a = i, bq = i + w - 1;
-    uint32_t mk;
-    if (w <= SEG) {
-      mk = 0xFFFFFFFFu;
-      for (int q = a; q <= bq; ++q) mk = min(mk, KEY[q]);
-    } else {
-      const int sa = a / SEG, sb = bq / SEG;
-      mk = min(SUF[a + (a >> 5)], PRE[bq + (bq >> 5)]);
-      const int mid = sb - sa - 1;
-      if (mid > 0) {
-        const int l = 31 - __clz(mid);
-        const uint32_t* row = ST + l * NSEG;
-        mk = min(mk, min(row[sa + 1], row[sb - (1 << l)]));
-      }
-    }
-    return mk;
+    const int bq = i + w - 1;
+    return min(SUF[i + (i >> 5)], PRE[bq + (bq >> 5)]);
   };
   auto counted = [&](int i, uint32_t mk) -> bool {
     bool ok = i >= q_lo && i < p_hi && mk != 0u;
@@ -460,16 +440,14 @@ __global__ void __launch_bounds__(256) scatter_kernel(SupermerParams P, unsigned
 }
 
 size_t supermer_smem_bytes(int tile, int lmax, int k, int m) {
+  (void)m;
   const long long NW = (long long)tile + 1 + lmax;
   const long long NQ = NW + k;  // upper bound (m >= 1)
   const long long NB = NW + k;
   const long long nsw = NB / 32 + 3;
   const long long NQP = NQ + NQ / 32 + 1;
-  const long long nseg = (NQ + SEG - 1) / SEG;
-  const long long lev = 32 - __builtin_clz((unsigned)((k - 1) / SEG + 1));
   const long long nbw = (NW + 31) / 32;
-  const long long key = (k - m + 1 <= SEG) ? NQ : 0;  // KEY only when w <= SEG
-  return nsw * 16 + 2 * NQP * 4 + key * 4 + lev * nseg * 4 + 2 * nbw * 4 + 64;
+  return nsw * 16 + 2 * NQP * 4 + 2 * nbw * 4 + 64;
 }
 
 cudaError_t launch_encode(const uint8_t* seq, uint64_t n, unsigned long long* packed,
@@ -496,10 +474,17 @@ constexpr int SUPER_SMEM_CEILING = 200 * 1024;
 template <int M>
 static cudaError_t launch_supermer_m(const SupermerParams& p, uint64_t blocks, size_t smem, cudaStream_t st) {
   if (smem > (size_t)SUPER_SMEM_CEILING) return cudaErrorInvalidValue;
-  cudaError_t e = cudaFuncSetAttribute(supermer_kernel<M>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       SUPER_SMEM_CEILING);
-  if (e != cudaSuccess) return e;
-  supermer_kernel<M><<<(unsigned)blocks, 256, smem, st>>>(p);
+  if (p.ordering == 0) {
+    cudaError_t e = cudaFuncSetAttribute(supermer_kernel<M, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         SUPER_SMEM_CEILING);
+    if (e != cudaSuccess) return e;
+    supermer_kernel<M, true><<<(unsigned)blocks, 256, smem, st>>>(p);
+  } else {
+    cudaError_t e = cudaFuncSetAttribute(supermer_kernel<M, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         SUPER_SMEM_CEILING);
+    if (e != cudaSuccess) return e;
+    supermer_kernel<M, false><<<(unsigned)blocks, 256, smem, st>>>(p);
+  }
   return cudaGetLastError();
 }
 
