@@ -49,6 +49,7 @@ cudaError_t launch_mmer_freq(const unsigned long long* packed, const uint32_t* n
                              int canon_min, uint32_t* freq, int nsm, cudaStream_t st);
 cudaError_t launch_scatter(const SupermerParams& p, unsigned long long nrec, int nsm, cudaStream_t st);
 size_t supermer_smem_bytes(int tile, int lmax, int k, int m);
+int supermer_tile();  // window starts per CTA of the super-mer kernel
 
 // ---- phase two ------------------------------------------------------------------------------
 // One entry per bin being counted.

@@ -79,7 +79,10 @@ __global__ void boundary_kernel(const uint64_t* __restrict__ offsets, uint64_t n
 // appended with one atomic per warp, and counted into its bin.
 
 constexpr int SEG = 8;  // consecutive m-mers per thread in the key pass
-constexpr int SUPER_TILE = 3072;  // window starts per CTA (measured: 3072 over 2048 and 4096)
+#ifndef GERBIL_SUPER_TILE
+#define GERBIL_SUPER_TILE 3072
+#endif
+constexpr int SUPER_TILE = GERBIL_SUPER_TILE;  // window starts per CTA
 constexpr int SUPER_WORDS = SUPER_TILE / 32 + 1;  // mask words holding a CTA's windows 0..tile
 
 __device__ __forceinline__ unsigned long long bases64(const unsigned long long* sw, int lb) {
@@ -438,6 +441,8 @@ __global__ void __launch_bounds__(256) scatter_kernel(SupermerParams P, unsigned
     if (local) __syncthreads();  // hist is reused by the next chunk
   }
 }
+
+int supermer_tile() { return SUPER_TILE; }
 
 size_t supermer_smem_bytes(int tile, int lmax, int k, int m) {
   (void)m;

@@ -576,7 +576,7 @@ int gerbil_partition(gerbil_ctx* ctx, const gerbil_reads* reads, int k, int m, i
   sp.lmax = opts.supermer_cap;
   sp.nbins = (uint32_t)nbins;
   sp.bounds = dbounds;
-  sp.tile = 3072;  // window starts per CTA (the super-mer kernel's SUPER_TILE)
+  sp.tile = gerbil::supermer_tile();  // window starts per CTA
   sp.bin_nsuper = binbuf;
   sp.bin_nkmers = binbuf + nbins;
   sp.bin_cursor = binbuf + 2 * nbins;
