@@ -89,13 +89,7 @@ __global__ void __launch_bounds__(256, 3) compact_kernel(CompactParams P) {
     for (int u = 0; u < COMPACT_UNROLL; ++u) {
       const unsigned long long slot = cb + u * blockDim.x + threadIdx.x;
       if (slot < P.slot_hi) {
-        const unsigned long long* sp = P.arena + slot * SW;
-#pragma unroll
-        for (int i = 0; i < SW; i += 2) {
-          const ulonglong2 x = *reinterpret_cast<const ulonglong2*>(sp + i);
-          v[u][i] = x.x;
-          v[u][i + 1] = x.y;
-        }
+        load_slot<SW>(P.arena + slot * SW, v[u]);  // 32-byte loads where the slot allows
       } else {
 #pragma unroll
         for (int i = 0; i < SW; ++i) v[u][i] = 0ull;
