@@ -73,8 +73,12 @@ __device__ __forceinline__ unsigned long long cta_append(uint32_t e, Counters* c
   return first;
 }
 
+// Resident CTAs per SM the registers are held to: 4 while the slots held in flight fit without
+// spills (slots of up to 64 bytes), else 3 (measured on k = 65: 3 -> 4 CTAs, 0.637 -> 0.605 ms;
+// 6 or 8 slots in flight per thread were slower)
+constexpr int compact_min_blocks(int SW) { return SW <= 8 ? 4 : 3; }
 template <int W, int WS>
-__global__ void __launch_bounds__(256, 3) compact_kernel(CompactParams P) {
+__global__ void __launch_bounds__(256, compact_min_blocks(slot_words(WS))) compact_kernel(CompactParams P) {
   constexpr int SW = slot_words(WS);
   constexpr int COMPACT_UNROLL = SW <= 4 ? 4 : 2;
   __shared__ uint32_t wsum[8];
