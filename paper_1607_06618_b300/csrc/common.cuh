@@ -57,6 +57,18 @@ __device__ __forceinline__ void to_stored(const unsigned long long key[W], unsig
   }
 }
 
+// Chunk c of to_stored of the key that is b when use_b, else a (the chunks computed one at a
+// time, for kernels that do not keep the stored form in registers).
+template <int W, int C>
+__device__ __forceinline__ unsigned long long stored_chunk(const unsigned long long a[W],
+                                                           const unsigned long long b[W], bool use_b) {
+  constexpr int L = 63 * C, r = L >> 6, sh = L & 63;
+  unsigned long long v = 0;
+  if constexpr (r < W) v = (use_b ? b[W - 1 - r] : a[W - 1 - r]) >> sh;
+  if constexpr (sh >= 2 && r + 1 < W) v |= (use_b ? b[W - 2 - r] : a[W - 2 - r]) << (64 - sh);
+  return MARK | (v & MASK63);
+}
+
 template <int W, int WS>
 __device__ __forceinline__ void from_stored(const unsigned long long st[WS], unsigned long long key[W]) {
 #pragma unroll

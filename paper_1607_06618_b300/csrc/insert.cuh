@@ -5,11 +5,21 @@
 #pragma once
 
 #include <algorithm>
+#include <type_traits>
 
 #include "common.cuh"
 #include "kernels.h"
 
 namespace gerbil {
+
+// Calls f(std::integral_constant<int, i>) for i = B, B+S, ... below E (compile-time indices).
+template <int B, int E, int S, class F>
+__device__ __forceinline__ void static_for(F&& f) {
+  if constexpr (B < E) {
+    f(std::integral_constant<int, B>{});
+    static_for<B + S, E, S>(f);
+  }
+}
 
 // Dispatch on the key width W = ceil(2k/64) and the stored words WS = ceil(2k/63) (W or W+1).
 #define GERBIL_KEY_SWITCH(W, WS, CALL)                 \
@@ -266,10 +276,22 @@ __device__ __forceinline__ void insert_item(const CountParams& P, uint32_t wi, c
   // is placed takes its next one at the start of the following step, while the other lanes go
   // on probing theirs.  A warp thus waits for the longest sum of probe chains over a lane's
   // k-mers, not for the longest chain of every k-mer in turn.
-  unsigned long long st[WS];
+  // Keys of fourteen words do not keep their stored form in registers while they are probed:
+  // each chunk is cut from fwd or rc when it is compared or written, which frees WS registers
+  // (measured on the 10 Mbp long-read sweep: k = 448 insert 9.46 -> 8.38 ms, its 128-160 bytes
+  // of spills gone; for 10-13 words, which do not spill at 2 CTAs per SM, it cost 1-4%)
+  constexpr bool LAZY = ROLL_RC && W == 14;
+  unsigned long long st[LAZY ? 1 : WS];
+  bool urc = false;  // LAZY: the key is rc (else fwd)
   uint32_t tagw = 0, s = 0, t = 0, spins = 0;
   uint32_t j = ja;
   bool busy = false;
+  // chunk u of the stored key in flight
+  auto stored_u = [&](auto U) -> unsigned long long {
+    constexpr int u = decltype(U)::value;
+    if constexpr (LAZY) return stored_chunk<W, u>(fwd, rc, urc);
+    else return st[u];
+  };
 #pragma unroll 1
   for (;;) {
     if (!busy) {
@@ -311,7 +333,8 @@ __device__ __forceinline__ void insert_item(const CountParams& P, uint32_t wi, c
 #pragma unroll
       for (int u = 0; u < W; ++u) key[u] = use_rc ? rc[u] : fwd[u];
       const unsigned long long h = key_hash<W>(key);
-      to_stored<W, WS>(key, st);
+      if constexpr (LAZY) urc = use_rc;
+      else to_stored<W, WS>(key, st);
       tagw = META_CLAIMED | (uint32_t)((h >> 34) & META_TAG_MASK);
       if constexpr (windowed) s = slot_of(h, nwin) * WIN;
       else s = slot_of(h, wk.cap);
@@ -327,12 +350,14 @@ __device__ __forceinline__ void insert_item(const CountParams& P, uint32_t wi, c
     int why = 0;
     if (v[0] == 0ull) {
       if (cas_relaxed(slot, 0ull, ((unsigned long long)tagw << 32) | 1ull) == 0ull) {
-        st_relaxed(slot + 1, st[0]);  // word 1 alone, then 16-byte aligned pairs
-#pragma unroll
-        for (int u = 1; u < WS; u += 2) {
-          if (u + 1 < WS) st_relaxed_v2(slot + 1 + u, st[u], st[u + 1]);
-          else st_relaxed(slot + 1 + u, st[u]);
-        }
+        st_relaxed(slot + 1, stored_u(std::integral_constant<int, 0>{}));  // word 1 alone,
+        static_for<1, WS, 2>([&](auto U) {                                // then aligned pairs
+          constexpr int u = decltype(U)::value;
+          if constexpr (u + 1 < WS)
+            st_relaxed_v2(slot + 1 + u, stored_u(U), stored_u(std::integral_constant<int, u + 1>{}));
+          else
+            st_relaxed(slot + 1 + u, stored_u(U));
+        });
         busy = false;
         if constexpr (STATS) record_probe<SW>(P, wk, s, t, 0);
       }
@@ -340,11 +365,11 @@ __device__ __forceinline__ void insert_item(const CountParams& P, uint32_t wi, c
     }
     if (((uint32_t)(v[0] >> 32) & ~META_MERGED) == tagw) {
       bool all = true, eq = true;
-#pragma unroll
-      for (int u = 0; u < WS; ++u) {
+      static_for<0, WS, 1>([&](auto U) {
+        constexpr int u = decltype(U)::value;
         all &= (v[1 + u] & MARK) != 0ull;
-        eq &= v[1 + u] == st[u];
-      }
+        eq &= v[1 + u] == stored_u(U);
+      });
       if (!all) {  // the claimer has not written every key word yet: read the slot again
         if (++spins > P.spin_limit) {
           why = 2;
@@ -380,7 +405,12 @@ __device__ __forceinline__ void insert_item(const CountParams& P, uint32_t wi, c
       why = 1;
     }
     unsigned long long key[W];
-    from_stored<W, WS>(st, key);
+    if constexpr (LAZY) {
+#pragma unroll
+      for (int u = 0; u < W; ++u) key[u] = urc ? rc[u] : fwd[u];
+    } else {
+      from_stored<W, WS>(st, key);
+    }
     to_overflow<W>(P, wi, key, why);
     if constexpr (STATS) record_probe<SW>(P, wk, s, t, why);
     busy = false;
