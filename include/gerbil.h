@@ -338,12 +338,13 @@ int gerbil_count_batch(gerbil_ctx* ctx, const gerbil_bins* bins, const int32_t* 
 int gerbil_counts_info(const gerbil_counts* counts, uint64_t* n, int* words,
                        gerbil_count_stats* stats);
 
-/* Device pointers of a result: keys[n][W] (row-major, layout above) and counts[n] (u32), the
- * rows App. C writes out.  Owned by the result and valid until gerbil_counts_free; a result
- * counted in bin groups is joined into one buffer on the first view.
- * Errors: E_INVAL (NULL), E_NOMEM, E_CUDA. */
-int gerbil_counts_view(const gerbil_counts* counts, const uint64_t** keys_dev,
-                       const uint32_t** counts_dev);
+/* Device view of a result: *n rows (may be NULL), *words = W key words per row (may be NULL),
+ * and the device pointers keys[n][W] (row-major, layout above) and counts[n] (u32), the rows
+ * App. C writes out (either pointer may be NULL).  Owned by the result and valid until
+ * gerbil_counts_free; a result counted in bin groups is joined into one buffer on the first
+ * view.  Errors: E_INVAL (NULL result), E_NOMEM, E_CUDA. */
+int gerbil_counts_view(const gerbil_counts* counts, uint64_t* n, int* words,
+                       const uint64_t** keys_dev, const uint32_t** counts_dev);
 
 /* Copies a result to host arrays owned by the caller: keys (cap*W words, layout above) and
  * counts (cap entries); plain or pinned host memory.  Synchronizes the context's stream.

@@ -364,12 +364,19 @@ __device__ __forceinline__ void insert_item(const CountParams& P, uint32_t wi, c
       continue;  // claimed by another lane meanwhile: look at the same slot again
     }
     if (((uint32_t)(v[0] >> 32) & ~META_MERGED) == tagw) {
-      bool all = true, eq = true;
-      static_for<0, WS, 1>([&](auto U) {
-        constexpr int u = decltype(U)::value;
-        all &= (v[1 + u] & MARK) != 0ull;
-        eq &= v[1 + u] == stored_u(U);
-      });
+      // equal stored words carry their markers, so equality alone means the key is found;
+      // the markers are looked at only when the words differ
+      bool eq = true;
+      static_for<0, WS, 1>([&](auto U) { eq &= v[1 + decltype(U)::value] == stored_u(U); });
+      if (eq) {
+        red_add(slot, 1ull);
+        busy = false;
+        if constexpr (STATS) record_probe<SW>(P, wk, s, t, 0);
+        continue;
+      }
+      bool all = true;
+#pragma unroll
+      for (int u = 0; u < WS; ++u) all &= (v[1 + u] & MARK) != 0ull;
       if (!all) {  // the claimer has not written every key word yet: read the slot again
         if (++spins > P.spin_limit) {
           why = 2;
@@ -377,11 +384,6 @@ __device__ __forceinline__ void insert_item(const CountParams& P, uint32_t wi, c
           if (spins > 8) __nanosleep(32);
           continue;
         }
-      } else if (eq) {
-        red_add(slot, 1ull);
-        busy = false;
-        if constexpr (STATS) record_probe<SW>(P, wk, s, t, 0);
-        continue;
       }
     }
     if (!why) {  // the next slot of the probe sequence

@@ -2162,8 +2162,11 @@ static int join_parts(gerbil_counts* c) {
   return GERBIL_OK;
 }
 
-int gerbil_counts_view(const gerbil_counts* cc, const uint64_t** keys, const uint32_t** counts) {
+int gerbil_counts_view(const gerbil_counts* cc, uint64_t* n, int* words, const uint64_t** keys,
+                       const uint32_t** counts) {
   if (!cc) return GERBIL_E_INVAL;
+  if (n) *n = cc->n;
+  if (words) *words = cc->W;
   gerbil_counts* c = const_cast<gerbil_counts*>(cc);
   if (!c->parts.empty()) {  // join the groups' rows into one buffer on first view
     const int rc = join_parts(c);

@@ -179,7 +179,7 @@ def load() -> ctypes.CDLL:
         "gerbil_count_batch": (I32, [P, P, P, I32, I32, U32, ctypes.POINTER(gerbil_opts), PP]),
         "gerbil_counts_info": (I32, [P, ctypes.POINTER(U64), ctypes.POINTER(I32),
                                      ctypes.POINTER(gerbil_count_stats)]),
-        "gerbil_counts_view": (I32, [P, PP, PP]),
+        "gerbil_counts_view": (I32, [P, ctypes.POINTER(U64), ctypes.POINTER(I32), PP, PP]),
         "gerbil_counts_to_host": (I32, [P, P, P, U64]),
         "gerbil_counts_free": (None, [P]),
         "gerbil_profile": (I32, [P, I32]),
@@ -350,9 +350,12 @@ def gerbil_counts_info(counts):
 
 
 def gerbil_counts_view(counts):
+    """(rows, key words, keys device pointer, counts device pointer) of a result."""
+    n, w = ctypes.c_uint64(), ctypes.c_int()
     kp, cp = ctypes.c_void_p(), ctypes.c_void_p()
-    _check(load().gerbil_counts_view(counts, ctypes.byref(kp), ctypes.byref(cp)))
-    return kp.value or 0, cp.value or 0
+    _check(load().gerbil_counts_view(counts, ctypes.byref(n), ctypes.byref(w), ctypes.byref(kp),
+                                     ctypes.byref(cp)))
+    return n.value, w.value, kp.value or 0, cp.value or 0
 
 
 def gerbil_counts_to_host(counts, keys_out=None, counts_out=None):
@@ -531,7 +534,7 @@ class Counts:
         """(keys int64[n, W], counts int32[n]) torch views of the device result (no copy)."""
         import torch
         n, W, _ = self.info()
-        kp, cp = gerbil_counts_view(self.handle)
+        _, _, kp, cp = gerbil_counts_view(self.handle)
         if n == 0:
             dev = torch.device("cuda", self.ctx.device)
             return (torch.zeros((0, W), dtype=torch.int64, device=dev),
