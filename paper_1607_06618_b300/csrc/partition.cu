@@ -1,6 +1,7 @@
 // partition.cu -- phase one on the GPU: 2-bit encoding, rolling minimizers, super-mer split
 // and bin scatter (Sec. 2.1, Fig. 1; Sec. 2.3 Phase One; Sec. 3.1-3.2).
 #include <algorithm>
+#include <type_traits>
 
 #include "common.cuh"
 #include "kernels.h"
@@ -73,14 +74,18 @@ __global__ void boundary_kernel(const uint64_t* __restrict__ offsets, uint64_t n
 // each with its running minima from the left and from the right, and a window, which spans
 // the end of one block and the start of the next, takes the minimum of one of each) is then 0
 // exactly for the windows that are not counted (for m >= 2 every interior read start is
-// straddled by one of the window's m-mers), and 1 + the minimizer's rank otherwise.  Super-mer starts and ends come from two ballot
-// masks; a super-mer never runs past the next multiple of L_max, so the CTA looks at most
+// straddled by one of the window's m-mers), and 1 + the minimizer's rank otherwise.  Super-mer
+// starts and ends are two bit masks over the windows, one word of 32 windows per thread; a
+// super-mer never runs past the next multiple of L_max, so the CTA looks at most
 // L_max windows past its range.  Each super-mer becomes one record (start, k-mers, bin),
 // appended with one atomic per warp, and counted into its bin.
 
 constexpr int SEG = 8;  // consecutive m-mers per thread in the key pass
 #ifndef GERBIL_SUPER_TILE
 #define GERBIL_SUPER_TILE 3072
+#endif
+#ifndef GERBIL_SUPER_MINB
+#define GERBIL_SUPER_MINB 7  // resident CTAs per SM the registers are held to (shared memory allows 7)
 #endif
 constexpr int SUPER_TILE = GERBIL_SUPER_TILE;  // window starts per CTA
 constexpr int SUPER_WORDS = SUPER_TILE / 32 + 1;  // mask words holding a CTA's windows 0..tile
@@ -92,6 +97,21 @@ __device__ __forceinline__ unsigned long long bases64(const unsigned long long* 
 __device__ __forceinline__ uint32_t bits32(const uint32_t* sm, int lb) {
   const int w = lb >> 5, o = lb & 31;
   return o ? ((sm[w] << o) | (sm[w + 1] >> (32 - o))) : sm[w];
+}
+
+// Bit 31-d of the result is set if any of bits 31-d .. 32-d-L of x is (L consecutive bases
+// from base d, first base at bit 31): x OR-ed with itself shifted by 1 .. L-1, in doubling steps.
+template <int L>
+__device__ __forceinline__ uint32_t spread(uint32_t x) {
+  if constexpr (L <= 1) {
+    return x;
+  } else {
+    constexpr int H = L / 2;
+    const uint32_t y = spread<H>(x);
+    const uint32_t z = y | (y << H);          // covers 2H
+    if constexpr (L % 2) return z | (x << (L - 1));
+    else return z;
+  }
 }
 
 // KMC2 reading (Sec. 3.1): demote m-mers that start with AAA or ACA or hold AA past
@@ -148,7 +168,7 @@ __device__ __forceinline__ uint32_t order_rank(uint32_t c, int m, int ordering,
 // MLEN: the minimizer length, so that every shift below is a constant; KMC2: the ordering is
 // GERBIL_ORDER_KMC2 (the default), ranked inline instead of through order_rank's switch.
 template <int MLEN, bool KMC2>
-__global__ void __launch_bounds__(256) supermer_kernel(SupermerParams P) {
+__global__ void __launch_bounds__(256, GERBIL_SUPER_MINB) supermer_kernel(SupermerParams P) {
   extern __shared__ __align__(16) unsigned char smem[];
   const long long T = P.tile;
   const long long P0 = (long long)blockIdx.x * T;
@@ -206,26 +226,30 @@ __global__ void __launch_bounds__(256) supermer_kernel(SupermerParams P) {
     const int lb = lbO + q0;
     const unsigned long long win = bases64(sw, lb);
     const unsigned long long rcwin = rev2(~win);
-    const uint32_t nm32 = bits32(snm, lb), bm32 = bits32(sbm, lb);
+    // bit 31-d of bad: m-mer q0+d holds an undetermined base, straddles a read start (one at
+    // bases d+1 .. d+m-1), or lies outside [q_lo, q_hi)
+    uint32_t bad = spread<m>(bits32(snm, lb));
+    if constexpr (m >= 2) bad |= spread<m - 1>(bits32(sbm, lb) << 1);
+    const int lo = q_lo - q0, hi = q_hi - q0;
+    if (lo > 0) bad |= ~(0xFFFFFFFFu >> lo);
+    if (hi < 32) bad |= hi <= 0 ? 0xFFFFFFFFu : (0xFFFFFFFFu >> hi);
     const int pq0 = q0 + (q0 >> 5);  // pidx(q0); a segment never crosses a 32-boundary
-#pragma unroll
-    for (int d = 0; d < SEG; ++d) {
-      const int iq = q0 + d;
-      if (iq >= NQ) break;
-      uint32_t kk = 0u;
-      bool ok = iq >= q_lo && iq < q_hi && ((nm32 << d) >> (32 - m)) == 0u;
-      if constexpr (m >= 2) ok = ok && ((bm32 << (d + 1)) >> (33 - m)) == 0u;  // no read start inside
-      if (ok) {
-        const uint32_t v = (uint32_t)(win >> (64 - 2 * m - 2 * d)) & vmask;
-        uint32_t c = v;
-        if (P.canon_min) {
-          const uint32_t rc = (uint32_t)(rcwin >> (2 * d)) & vmask;
-          c = rc < v ? rc : v;
-        }
-        if constexpr (KMC2) kk = (c | (kmc2_demoted(c, m) << 30)) + 1u;
-        else kk = order_rank(c, m, P.ordering, P.rank_table) + 1u;
+    auto key = [&](int d) -> uint32_t {
+      if ((bad << d) & 0x80000000u) return 0u;
+      const uint32_t v = (uint32_t)(win >> (64 - 2 * m - 2 * d)) & vmask;
+      uint32_t c = v;
+      if (P.canon_min) {
+        const uint32_t rc = (uint32_t)(rcwin >> (2 * d)) & vmask;
+        c = rc < v ? rc : v;
       }
-      PRE[pq0 + d] = kk;
+      if constexpr (KMC2) return (c | (kmc2_demoted(c, m) << 30)) + 1u;
+      else return order_rank(c, m, P.ordering, P.rank_table) + 1u;
+    };
+    if (q0 + SEG <= NQ) {
+#pragma unroll
+      for (int d = 0; d < SEG; ++d) PRE[pq0 + d] = key(d);
+    } else {
+      for (int d = 0; q0 + d < NQ; ++d) PRE[pq0 + d] = key(d);
     }
   }
   __syncthreads();
@@ -265,50 +289,67 @@ __global__ void __launch_bounds__(256) supermer_kernel(SupermerParams P) {
     return ok;
   };
 
-  // window minima and super-mer starts / boundaries as bit masks, one ballot per 32 windows,
-  // each warp over a contiguous run of mask words (the predecessor of a lane's window is the
-  // previous lane's, or the last window of the warp's previous word): window i starts a
+  // window minima and super-mer starts / boundaries as bit masks, one thread per mask word of
+  // 32 consecutive windows, which it scans in order (no shuffles or votes): window i starts a
   // super-mer if it is counted and its predecessor is not, or has another minimizer, or i sits
-  // on a multiple of L_max; a boundary is a start or an uncounted window.
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  // on a multiple of L_max; a boundary is a start or an uncounted window (window 0, the
+  // previous CTA's last, and the windows past NW are boundaries and never starts).
   {
     const uint32_t lm = (uint32_t)lmax;
     const bool pow2 = (lm & (lm - 1)) == 0;
-    const int per = (nbw + nwarp - 1) / nwarp;
-    const int wd0 = warp * per, wd1 = min(nbw, wd0 + per);
-    uint32_t cm = 0;  // minimum and counted-flag of the window before the current word
-    bool cv = false;
-    if (wd0 < wd1 && wd0 > 0) {
-      const int ip = wd0 * 32 - 1;
-      cm = wmin(ip);
-      cv = counted(ip, cm);
-    }
-    for (int wd = wd0; wd < wd1; ++wd) {
-      const int i = wd * 32 + lane;
-      const bool in = i < NW;
-      const uint32_t mk = in ? wmin(i) : 0u;
-      const bool v = in && counted(i, mk);
-      uint32_t pm = __shfl_up_sync(0xFFFFFFFFu, mk, 1);
-      bool pv = __shfl_up_sync(0xFFFFFFFFu, (int)v, 1) != 0;
-      if (lane == 0) {
-        pm = cm;
-        pv = cv;
+    for (int wd = threadIdx.x; wd < nbw; wd += blockDim.x) {
+      const int i0 = wd * 32;
+      uint32_t pm = 0u, pv = 0u;  // minimum of window i0 - 1, and 1 if it is counted
+      if (wd > 0) {
+        pm = wmin(i0 - 1);
+        pv = counted(i0 - 1, pm) ? 1u : 0u;
       }
-      bool st = false, bd = true;
-      if (i >= 1 && in) {
-        const uint32_t r = Omod + (uint32_t)i;
-        const bool cut = pow2 ? ((r & (lm - 1)) == 0u) : (r % lm == 0u);
-        st = v && (!pv || pm != mk || cut);
-        bd = !v || st;
+      // PRE index of m-mer i0 + j + w - 1: base + j, plus one from the 32-boundary on
+      const int c0 = i0 + w - 1;
+      const int pbase = c0 + (c0 >> 5), jc = 32 - (c0 & 31);
+      const int sbase = 33 * wd;  // SUF index of m-mer i0 + j: sbase + j
+      uint32_t nz = 0u, df = 0u, ob = 0xFFFFFFFFu;
+      auto scan = [&](auto FULL) {
+        constexpr bool full = decltype(FULL)::value;
+        uint32_t prev = pm;
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          uint32_t mk = 0u;
+          if (full || i0 + j < NW) mk = min(SUF[sbase + j], PRE[pbase + j + (j >= jc ? 1 : 0)]);
+          nz |= (mk != 0u ? 1u : 0u) << j;
+          df |= (mk != prev ? 1u : 0u) << j;
+          prev = mk;
+          if constexpr (m == 1) {  // no m-mer straddles a read start: test the window itself
+            const int lb = lbO + i0 + j;
+            bool ok = true;
+            for (int c = 1; ok && c < k; c += 32) {
+              const int l = min(32, k - c);
+              ok = (bits32(sbm, lb + c) >> (32 - l)) == 0u;
+            }
+            if (!ok) ob &= ~(1u << j);
+          }
+        }
+      };
+      if (i0 + 32 <= NW) scan(std::true_type{});
+      else scan(std::false_type{});
+      // counted windows: q_lo <= i < p_hi, a minimum above 0 (and, for m = 1, no read start)
+      uint32_t rb = 0xFFFFFFFFu;
+      if (i0 < q_lo) rb &= 0xFFFFFFFFu << (q_lo - i0);
+      const int hi = p_hi - i0;
+      if (hi < 32) rb &= hi <= 0 ? 0u : ((1u << hi) - 1u);
+      const uint32_t vb = nz & rb & ob;
+      // windows on a multiple of L_max
+      uint32_t cb = 0u;
+      const uint32_t r0 = pow2 ? ((Omod + (uint32_t)i0) & (lm - 1u)) : ((Omod + (uint32_t)i0) % lm);
+      for (unsigned long long c = r0 ? lm - r0 : 0u; c < 32ull; c += lm) cb |= 1u << c;
+      uint32_t st = vb & (~((vb << 1) | pv) | df | cb);
+      uint32_t bd = ~vb | st;
+      if (wd == 0) {
+        st &= ~1u;
+        bd |= 1u;
       }
-      const uint32_t sb = __ballot_sync(0xFFFFFFFFu, st);
-      const uint32_t bb = __ballot_sync(0xFFFFFFFFu, bd);
-      if (lane == 0) {
-        SB[wd] = sb;
-        BB[wd] = bb;
-      }
-      cm = __shfl_sync(0xFFFFFFFFu, mk, 31);
-      cv = __shfl_sync(0xFFFFFFFFu, (int)v, 31) != 0;
+      SB[wd] = st;
+      BB[wd] = bd;
     }
   }
   __syncthreads();
@@ -318,6 +359,7 @@ __global__ void __launch_bounds__(256) supermer_kernel(SupermerParams P) {
   // atomic; then every thread takes starts r, r + 256, ... (records in window order): the word
   // holding start r, its bit, its end (the first boundary after it; a cut every L_max windows
   // bounds the search), its minimizer and bin
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int own = (int)(P1 - P0);
   const int ownw = (own >> 5) + 1;  // mask words holding windows 0..own (<= SUPER_WORDS)
   auto own_bits = [&](int wd) -> uint32_t {
@@ -348,16 +390,9 @@ __global__ void __launch_bounds__(256) supermer_kernel(SupermerParams P) {
     }
   }
   __syncthreads();
-  const uint32_t total = s_wpre[ownw];
-  for (uint32_t r = threadIdx.x; r < total; r += blockDim.x) {
-    int lo = 0, hi = ownw;  // s_wpre[lo] <= r < s_wpre[hi]
-    while (hi - lo > 1) {
-      const int mid = (lo + hi) >> 1;
-      if (s_wpre[mid] <= r) lo = mid; else hi = mid;
-    }
-    uint32_t bits = own_bits(lo);
-    for (uint32_t n = r - s_wpre[lo]; n > 0; --n) bits &= bits - 1u;  // drop the earlier starts
-    const int i = lo * 32 + __ffs(bits) - 1;
+  // one record per start i, the CTA's r-th: its end (the first boundary after it; a cut every
+  // L_max windows bounds the search), its minimizer and bin
+  auto emit = [&](int i, uint32_t r) {
     const int j = i + 1;
     int end = NW;
     for (int wj = j >> 5; wj < nbw; ++wj) {
@@ -385,6 +420,17 @@ __global__ void __launch_bounds__(256) supermer_kernel(SupermerParams P) {
     const unsigned long long idx = s_rbase + r;
     if (idx < P.rec_cap)
       P.rec[idx] = make_ulonglong2((unsigned long long)(O + i), ((unsigned long long)bin << 32) | nk);
+  };
+  const uint32_t total = s_wpre[ownw];
+  for (uint32_t r = threadIdx.x; r < total; r += blockDim.x) {
+    int lo = 0, hi = ownw;  // s_wpre[lo] <= r < s_wpre[hi]
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (s_wpre[mid] <= r) lo = mid; else hi = mid;
+    }
+    uint32_t bits = own_bits(lo);
+    for (uint32_t n = r - s_wpre[lo]; n > 0; --n) bits &= bits - 1u;  // drop the earlier starts
+    emit(lo * 32 + __ffs(bits) - 1, r);
   }
 }
 
