@@ -163,7 +163,15 @@ typedef struct gerbil_opts {
                                   lexicographic order of the k-mers, A < C < G < T), sorted on
                                   the device; a grouped result is joined first.  0 (default):
                                   unordered */
-  int32_t reserved_opts;       /* zero */
+  int32_t claim_first;         /* probe order of the insert kernel: 0 (default): chosen per
+                                  batch from the distinct ratio the context learned (claim
+                                  first above 0.6, i.e. when most k-mers are new keys); 1: each
+                                  probe first tries to claim the slot with a CAS on its meta
+                                  word and reads the key words only if the slot holds a key
+                                  with the same tag (a new key costs one round trip to memory);
+                                  2: each probe reads the slot first and claims only an empty
+                                  one (a repeated key costs one round trip).  Counts do not
+                                  depend on it */
 } gerbil_opts;
 
 /* Per-call statistics of a count. */

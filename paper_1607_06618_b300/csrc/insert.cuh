@@ -232,7 +232,8 @@ __host__ __device__ constexpr uint32_t probe_window(int SW) {
 // run 2 instead of 1, k = 479 13.26 -> 10.72 ms; for 10-14 words it bought none and cost 3%).
 __host__ __device__ constexpr bool rc_fresh(int W) { return W == 8 || W == 9 || W == 15; }
 
-template <int W, int WS, bool STATS = false, int SCHEME = 0, int KPL = ITEM_KMERS / 32>
+// CF: claim first (CountParams::cas_first), built for the default scheme and item size.
+template <int W, int WS, bool STATS = false, int SCHEME = 0, int KPL = ITEM_KMERS / 32, bool CF = false>
 __device__ __forceinline__ void insert_item(const CountParams& P, uint32_t wi, const BinWork& wk,
                                             uint32_t it, uint32_t s_lo, WarpSmem& S, int lane) {
   constexpr uint32_t ik = 32u * KPL;  // k-mers of the item, <= ITEM_KMERS
@@ -346,23 +347,39 @@ __device__ __forceinline__ void insert_item(const CountParams& P, uint32_t wi, c
     // one probe of slot s (Alg. 1)
     unsigned long long* slot = tab + (unsigned long long)s * SW;
     unsigned long long v[SW];
-    load_slot<SW>(slot, v);
-    int why = 0;
-    if (v[0] == 0ull) {
-      if (cas_relaxed(slot, 0ull, ((unsigned long long)tagw << 32) | 1ull) == 0ull) {
-        st_relaxed(slot + 1, stored_u(std::integral_constant<int, 0>{}));  // word 1 alone,
-        static_for<1, WS, 2>([&](auto U) {                                // then aligned pairs
-          constexpr int u = decltype(U)::value;
-          if constexpr (u + 1 < WS)
-            st_relaxed_v2(slot + 1 + u, stored_u(U), stored_u(std::integral_constant<int, u + 1>{}));
-          else
-            st_relaxed(slot + 1 + u, stored_u(U));
-        });
-        busy = false;
-        if constexpr (STATS) record_probe<SW>(P, wk, s, t, 0);
+    const unsigned long long claim = ((unsigned long long)tagw << 32) | 1ull;
+    bool claimed = false;
+    if constexpr (CF) {
+      // mostly new keys: claim first (one round trip when the slot is empty) and read the
+      // key words only when the meta word's tag matches
+      const unsigned long long old = cas_relaxed(slot, 0ull, claim);
+      claimed = old == 0ull;
+      if (!claimed) {
+        if (((uint32_t)(old >> 32) & ~META_MERGED) == tagw) load_slot<SW>(slot, v);
+        else v[0] = old;  // another key: its words are not looked at
       }
-      continue;  // claimed by another lane meanwhile: look at the same slot again
+    } else {
+      // mostly repeated keys: read the slot first (a found key costs one round trip)
+      load_slot<SW>(slot, v);
+      if (v[0] == 0ull) {
+        claimed = cas_relaxed(slot, 0ull, claim) == 0ull;
+        if (!claimed) continue;  // claimed by another lane meanwhile: look at the slot again
+      }
     }
+    if (claimed) {  // the slot is ours: its marked key words
+      st_relaxed(slot + 1, stored_u(std::integral_constant<int, 0>{}));  // word 1 alone,
+      static_for<1, WS, 2>([&](auto U) {                                // then aligned pairs
+        constexpr int u = decltype(U)::value;
+        if constexpr (u + 1 < WS)
+          st_relaxed_v2(slot + 1 + u, stored_u(U), stored_u(std::integral_constant<int, u + 1>{}));
+        else
+          st_relaxed(slot + 1 + u, stored_u(U));
+      });
+      busy = false;
+      if constexpr (STATS) record_probe<SW>(P, wk, s, t, 0);
+      continue;
+    }
+    int why = 0;
     if (((uint32_t)(v[0] >> 32) & ~META_MERGED) == tagw) {
       // equal stored words carry their markers, so equality alone means the key is found;
       // the markers are looked at only when the words differ
@@ -420,12 +437,12 @@ __device__ __forceinline__ void insert_item(const CountParams& P, uint32_t wi, c
   __syncwarp();  // S is reused by the next item
 }
 
-template <int W, int WS, bool STATS, int SCHEME, int KPL>
+template <int W, int WS, bool STATS, int SCHEME, int KPL, bool CF>
 __device__ __forceinline__ void count_item(const CountParams& P, unsigned long long item,
                                            unsigned long long entry, WarpSmem& S, int lane) {
   const uint32_t wi = (uint32_t)(entry >> 32), s_lo = (uint32_t)entry;
   const BinWork wk = P.work[wi];
-  insert_item<W, WS, STATS, SCHEME, KPL>(P, wi, wk, (uint32_t)(item - wk.item_begin), s_lo, S, lane);
+  insert_item<W, WS, STATS, SCHEME, KPL, CF>(P, wi, wk, (uint32_t)(item - wk.item_begin), s_lo, S, lane);
 }
 
 // Warps take items in bin order from a device counter (the next one is requested while the
@@ -456,14 +473,14 @@ constexpr int insert_min_blocks(int W) {
 }
 
 // STATS: the instantiation that records probe statistics (only launched while they are on).
-template <int W, int WS, bool STATS, int SCHEME, int KPL>
+template <int W, int WS, bool STATS, int SCHEME, int KPL, bool CF>
 __device__ __forceinline__ void insert_items(const CountParams& P, WarpSmem* S) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (!P.schedule) {  // fixed: warp w takes items base + w, base + w + nw, ...
     const unsigned long long nw = (unsigned long long)gridDim.x * (blockDim.x >> 5);
     for (unsigned long long item = P.item_base + blockIdx.x * (unsigned long long)(blockDim.x >> 5) + warp;
          item < P.nitems; item += nw)
-      count_item<W, WS, STATS, SCHEME, KPL>(P, item, __ldg(P.imap + item), S[warp], lane);
+      count_item<W, WS, STATS, SCHEME, KPL, CF>(P, item, __ldg(P.imap + item), S[warp], lane);
     return;
   }
   unsigned long long* queue = P.queue;
@@ -474,7 +491,7 @@ __device__ __forceinline__ void insert_items(const CountParams& P, WarpSmem* S) 
     unsigned long long next = 0;
     if (lane == 0) next = P.item_base + atomicAdd(queue, 1ull);
     const unsigned long long entry = __ldg(P.imap + item);
-    count_item<W, WS, STATS, SCHEME, KPL>(P, item, entry, S[warp], lane);
+    count_item<W, WS, STATS, SCHEME, KPL, CF>(P, item, entry, S[warp], lane);
     item = __shfl_sync(0xFFFFFFFFu, next, 0);
   }
 }
@@ -483,7 +500,7 @@ __device__ __forceinline__ void insert_items(const CountParams& P, WarpSmem* S) 
 // bins' tables average more than the L2 cache (CountParams::wide_tables).  Their probes go to
 // HBM whatever the warps in flight, so the cap's spills cost time without hiding any more
 // latency (measured: k = 200 with 126 GB of tables, 71.1 ms uncapped against 74.1 ms capped).
-template <int W, int WS, bool STATS, bool CAP, int SCHEME, int KPL>
+template <int W, int WS, bool STATS, bool CAP, int SCHEME, int KPL, bool CF>
 __global__ void __launch_bounds__(256, CAP ? insert_min_blocks(W) : 1) insert_kernel(CountParams P) {
   __shared__ WarpSmem S[8];
   if constexpr (STATS) {
@@ -494,12 +511,12 @@ __global__ void __launch_bounds__(256, CAP ? insert_min_blocks(W) : 1) insert_ke
     unsigned long long* global_hist = P.probe_hist;
     CountParams Q = P;
     Q.probe_hist = hist;
-    insert_items<W, WS, STATS, SCHEME, KPL>(Q, S);
+    insert_items<W, WS, STATS, SCHEME, KPL, CF>(Q, S);
     __syncthreads();
     for (int i = threadIdx.x; i < 2 * PROBE_BUCKETS; i += blockDim.x)
       if (hist[i]) atomicAdd(global_hist + i, hist[i]);
   } else {
-    insert_items<W, WS, STATS, SCHEME, KPL>(P, S);
+    insert_items<W, WS, STATS, SCHEME, KPL, CF>(P, S);
   }
 }
 
@@ -507,41 +524,48 @@ __global__ void __launch_bounds__(256, CAP ? insert_min_blocks(W) : 1) insert_ke
 // Launch of one (key width, stored words, probe scheme, k-mers per lane) instantiation:
 // persistent -- as many CTAs as are resident at once (occupancy query), each warp taking items
 // -- or one warp per item.
-template <int w, int ws, bool CAP, int SCHEME, int KPL>
+template <int w, int ws, bool CAP, int SCHEME, int KPL, bool CF>
 static cudaError_t launch_insert_as(const CountParams& p, unsigned long long need, int persistent,
                                     int nsm, cudaStream_t st) {
   unsigned long long grid = need;
   if (persistent) {
     int per_sm = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        &per_sm, insert_kernel<w, ws, false, CAP, SCHEME, KPL>, COUNT_THREADS, 0);
+        &per_sm, insert_kernel<w, ws, false, CAP, SCHEME, KPL, CF>, COUNT_THREADS, 0);
     if (e != cudaSuccess) return e;
     grid = std::min<unsigned long long>(need, (unsigned long long)nsm * std::max(1, per_sm));
   }
-  // probe statistics always use the capped form (they time nothing)
-  if (p.probe_hist) insert_kernel<w, ws, true, true, SCHEME, KPL><<<(unsigned)grid, COUNT_THREADS, 0, st>>>(p);
-  else insert_kernel<w, ws, false, CAP, SCHEME, KPL><<<(unsigned)grid, COUNT_THREADS, 0, st>>>(p);
+  // probe statistics always use the capped, read-first form (they time nothing; both probe
+  // orders visit the same slots)
+  if (p.probe_hist)
+    insert_kernel<w, ws, true, true, SCHEME, KPL, false><<<(unsigned)grid, COUNT_THREADS, 0, st>>>(p);
+  else
+    insert_kernel<w, ws, false, CAP, SCHEME, KPL, CF><<<(unsigned)grid, COUNT_THREADS, 0, st>>>(p);
   return cudaGetLastError();
 }
 
-template <int w, int ws, int SCHEME, int KPL>
+template <int w, int ws, int SCHEME, int KPL, bool CF = false>
 static cudaError_t launch_insert_sk(const CountParams& p, unsigned long long need, int persistent,
                                     int nsm, cudaStream_t st) {
   if constexpr (w >= 6 && insert_min_blocks(w) > 1) {
     if (p.wide_tables && !p.probe_hist)
-      return launch_insert_as<w, ws, false, SCHEME, KPL>(p, need, persistent, nsm, st);
+      return launch_insert_as<w, ws, false, SCHEME, KPL, CF>(p, need, persistent, nsm, st);
   }
-  return launch_insert_as<w, ws, true, SCHEME, KPL>(p, need, persistent, nsm, st);
+  return launch_insert_as<w, ws, true, SCHEME, KPL, CF>(p, need, persistent, nsm, st);
 }
 
-// Work-item sizes other than 256 k-mers are compiled for keys of up to four words only.
+// Work-item sizes other than 256 k-mers are compiled for keys of up to four words only; the
+// claim-first probe order for the default scheme and item size only.
 __host__ __device__ constexpr bool small_items_for(int w) { return w <= 4; }
 
 template <int w, int ws>
 static cudaError_t launch_insert_w(const CountParams& p, unsigned long long need, int persistent,
                                    int nsm, cudaStream_t st) {
   const int kpl = (int)(p.item_kmers / 32);
-  if (p.scheme == 0 && kpl == 8) return launch_insert_sk<w, ws, 0, 8>(p, need, persistent, nsm, st);
+  if (p.scheme == 0 && kpl == 8) {
+    if (p.cas_first && !p.probe_hist) return launch_insert_sk<w, ws, 0, 8, true>(p, need, persistent, nsm, st);
+    return launch_insert_sk<w, ws, 0, 8>(p, need, persistent, nsm, st);
+  }
   if (p.scheme == 1 && kpl == 8) return launch_insert_sk<w, ws, 1, 8>(p, need, persistent, nsm, st);
   if constexpr (small_items_for(w)) {
     if (p.scheme == 0 && kpl == 4) return launch_insert_sk<w, ws, 0, 4>(p, need, persistent, nsm, st);

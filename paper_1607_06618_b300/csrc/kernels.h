@@ -102,6 +102,8 @@ struct CountParams {
   // insert kernel without its register cap)
   int wide_tables;
   int scheme;                    // probe scheme of every bin of the launch (BinWork::scheme)
+  int cas_first;                 // 1: every probe claims with a CAS before reading the key
+                                 // words (mostly new keys); 0: reads the slot first
   uint32_t item_kmers;           // k-mers per work item of every bin of the launch: 64, 128
                                  // or 256 (64 and 128 for keys of up to four words only)
 };

@@ -68,7 +68,7 @@ class gerbil_opts(ctypes.Structure):
                 ("autotune", ctypes.c_uint32), ("graph", ctypes.c_uint32),
                 ("dfp_pivot", ctypes.c_float), ("dfp_sample", ctypes.c_uint32),
                 ("probe_scheme", ctypes.c_int32), ("item_kmers", ctypes.c_uint32),
-                ("sorted_output", ctypes.c_int32), ("reserved_opts", ctypes.c_int32)]
+                ("sorted_output", ctypes.c_int32), ("claim_first", ctypes.c_int32)]
 
 
 TUNE_CLASSES = 4

@@ -170,10 +170,41 @@ def test_probe_schemes_and_item_sizes(g, k):
             assert_same_rows(got, want)
 
 
+# both probe orders (claim first / read first, gerbil_opts.claim_first) on the same inputs, with
+# and without forced overflow (theta = 1), in the capped and the uncapped (tables beyond L2)
+# forms of the kernel
+@pytest.mark.parametrize("k", [21, 32, 65, 99, 200, 479])
+def test_claim_first_and_read_first_probe_orders(g, k):
+    gerbil, ctx, torch = g
+    m = min(11, k - 1)
+    seq, offs = synth.random_small(500, max(1, k - 4), k + 300, p_n=0.003, seed=3500 + k)
+    seq = np.concatenate([seq, seq[: int(offs[120])]])
+    offs = np.concatenate([offs, offs[1:121] + offs[-1]])
+    for mc in (1, 2):
+        want = oracle.count(seq, offs, k, canonical=True, min_count=mc)
+        for cf in (1, 2):
+            ctx.forget_ratio()
+            got, st = _gpu_count(g, seq, offs, k, m, 16, mc, claim_first=cf)
+            assert st["overflowed"] == 0
+            assert_same_rows(got, want)
+            got, st = _gpu_count(g, seq, offs, k, m, 16, mc, claim_first=cf, max_probes=1,
+                                 distinct_ratio=0.05, overflow_slots=1 << 22)
+            assert st["overflowed"] > 0
+            assert_same_rows(got, want)
+    if k in (200, 479):  # one table larger than L2: the uncapped form of the kernel
+        seq, offs = synth.uniform_reads(2500, 1000, 0.0, seed=7500 + k)
+        want = oracle.count(seq, offs, k, canonical=True, min_count=1)
+        for cf in (1, 2):
+            ctx.forget_ratio()
+            got, st = _gpu_count(g, seq, offs, k, 11, 1, 1, claim_first=cf)
+            assert_same_rows(got, want)
+
+
 def test_bad_probe_scheme_and_item_size_rejected(g):
     gerbil, ctx, torch = g
     seq, offs = synth.random_small(20, 40, 60, p_n=0.0, seed=1)
-    for bad in (dict(probe_scheme=2), dict(item_kmers=96), dict(item_kmers=512)):
+    for bad in (dict(probe_scheme=2), dict(item_kmers=96), dict(item_kmers=512),
+                dict(claim_first=3), dict(claim_first=-1)):
         with pytest.raises(gerbil.GerbilError) as e:
             _gpu_count(g, seq, offs, 21, 7, 4, 1, **bad)
         assert e.value.status == gerbil.GERBIL_E_INVAL
