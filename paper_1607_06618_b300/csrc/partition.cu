@@ -185,8 +185,8 @@ __global__ void __launch_bounds__(256, GERBIL_SUPER_MINB) supermer_kernel(Superm
   const long long wlo = (O >= 0) ? (O >> 5) : -1;  // first staged word
   const int nsw = (int)(((O + NB - 1) >> 5) - wlo) + 2;
 
-  // shared memory: staged words and masks | PRE (the keys, then the running minima from the
-  // left within blocks of w) | SUF (from the right) | SB | BB.  PRE and SUF are indexed through
+  // shared memory: staged words and masks | PRE (the keys, then their running minima from the
+  // left within blocks of w) | SUF (the keys, then from the right) | SB | BB.  PRE and SUF are indexed through
   // pidx(q) = q + q/32, so that the eight stores of a thread's segment (stride 8 across the
   // warp) hit distinct banks.
   const int NSEG = (NQ + SEG - 1) / SEG;
@@ -247,25 +247,35 @@ __global__ void __launch_bounds__(256, GERBIL_SUPER_MINB) supermer_kernel(Superm
     };
     if (q0 + SEG <= NQ) {
 #pragma unroll
-      for (int d = 0; d < SEG; ++d) PRE[pq0 + d] = key(d);
+      for (int d = 0; d < SEG; ++d) PRE[pq0 + d] = SUF[pq0 + d] = key(d);
     } else {
-      for (int d = 0; q0 + d < NQ; ++d) PRE[pq0 + d] = key(d);
+      for (int d = 0; q0 + d < NQ; ++d) PRE[pq0 + d] = SUF[pq0 + d] = key(d);
     }
   }
   __syncthreads();
-  // running minima within blocks of w m-mers, one thread per block: from the right into SUF,
-  // then from the left over the keys in place (PRE)
-  for (int b0 = threadIdx.x * w; b0 < NQ; b0 += blockDim.x * w) {
-    const int b1 = min(b0 + w, NQ);
-    uint32_t run = 0xFFFFFFFFu;
-    for (int q = b1 - 1; q >= b0; --q) {
-      run = min(run, PRE[q + (q >> 5)]);
-      SUF[q + (q >> 5)] = run;
-    }
-    run = 0xFFFFFFFFu;
-    for (int q = b0; q < b1; ++q) {
-      run = min(run, PRE[q + (q >> 5)]);
-      PRE[q + (q >> 5)] = run;
+  // running minima within blocks of w m-mers, in place: one thread per block from the right
+  // (SUF), and in the warps after those, one thread per block from the left (PRE); both arrays
+  // start out holding the keys
+  {
+    const int nblk = (NQ + w - 1) / w;
+    const int nblk32 = (nblk + 31) & ~31;  // the left-to-right threads start on a warp boundary
+    for (int t = threadIdx.x; t < nblk32 + nblk; t += blockDim.x) {
+      if (t < nblk32 && t >= nblk) continue;
+      const bool right = t < nblk32;
+      const int b0 = (right ? t : t - nblk32) * w;
+      const int b1 = min(b0 + w, NQ);
+      uint32_t run = 0xFFFFFFFFu;
+      if (right) {
+        for (int q = b1 - 1; q >= b0; --q) {
+          run = min(run, SUF[q + (q >> 5)]);
+          SUF[q + (q >> 5)] = run;
+        }
+      } else {
+        for (int q = b0; q < b1; ++q) {
+          run = min(run, PRE[q + (q >> 5)]);
+          PRE[q + (q >> 5)] = run;
+        }
+      }
     }
   }
   __syncthreads();
