@@ -640,51 +640,82 @@ def main_ours(a, world, rank, local):
             cnt_pin = torch.empty(max(1, nrow), dtype=torch.int32).pin_memory()
             workers.append((wctx, keys_pin, cnt_pin))
 
-        def e2e_step(wctx, kp, cp):
+        # the result a step hands back: App. C records (the counter's output format: 1 or 5
+        # bytes of count, then 4 bases per byte), or the rows (key words + 32-bit count)
+        rec_bytes = []
+        for wctx, _, _ in workers:
             bins = wctx.partition(hs, ho, k, m, nbins, opts, bb)
             res = wctx.count_batch(bins, None, k, mc, opts)
-            gerbil.gerbil_counts_to_host(res.handle, kp.numpy().view(np.uint64),
-                                         cp.numpy().view(np.uint32))
+            rec_bytes.append(int(gerbil.gerbil_encode_records(res.handle, k)))
+            res.free()
+            bins.free()
+        # room for every count in its 5-byte form: the encoder then skips its size pass
+        rec_room = max(1, nrow * ((k + 3) // 4 + 5), rec_bytes[0])
+        rec_pin = [torch.empty(rec_room, dtype=torch.uint8).pin_memory() for _ in workers]
+
+        def e2e_step(i, result):
+            wctx, kp, cp = workers[i]
+            bins = wctx.partition(hs, ho, k, m, nbins, opts, bb)
+            res = wctx.count_batch(bins, None, k, mc, opts)
+            if result == "records":
+                gerbil.gerbil_encode_records(res.handle, k, rec_pin[i].data_ptr(), rec_pin[i].numel(), 0)
+            else:
+                gerbil.gerbil_counts_to_host(res.handle, kp.numpy().view(np.uint64),
+                                             cp.numpy().view(np.uint32))
             res.free()
             bins.free()
 
-        for w in workers:  # warm-up (ratio learning, scratch growth) of every worker
-            e2e_step(*w)
-        if dist:
-            dist.barrier()
-        torch.cuda.synchronize()
-        share = [a.e2e_steps // nw + (1 if i < a.e2e_steps % nw else 0) for i in range(nw)]
-        errors = []
+        def threaded(share, result):
+            errors = []
 
-        def run(i):
-            try:
-                for _ in range(share[i]):
-                    e2e_step(*workers[i])
-            except Exception as exc:  # reported after the join
-                errors.append(exc)
+            def run(i):
+                try:
+                    for _ in range(share[i]):
+                        e2e_step(i, result)
+                except Exception as exc:  # reported after the join
+                    errors.append(exc)
 
-        threads = [threading.Thread(target=run, args=(i,)) for i in range(nw)]
-        t0 = time.perf_counter()
-        for t in threads:
-            t.start()
-        for t in threads:
-            t.join()
-        torch.cuda.synchronize()
-        te = (time.perf_counter() - t0) / a.e2e_steps
-        if errors:
-            raise errors[0]
+            threads = [threading.Thread(target=run, args=(i,)) for i in range(nw)]
+            for t in threads:
+                t.start()
+            for t in threads:
+                t.join()
+            if errors:
+                raise errors[0]
+
+        def run_e2e(result):
+            # warm-up: every worker once alone (ratio learning, scratch growth), then two steps
+            # each with all workers at once, so that the memory pool has grown to what the
+            # concurrent steps hold before the clock starts
+            for i in range(nw):
+                e2e_step(i, result)
+            threaded([2] * nw, result)
+            if dist:
+                dist.barrier()
+            torch.cuda.synchronize()
+            share = [a.e2e_steps // nw + (1 if i < a.e2e_steps % nw else 0) for i in range(nw)]
+            t0 = time.perf_counter()
+            threaded(share, result)
+            torch.cuda.synchronize()
+            te = (time.perf_counter() - t0) / a.e2e_steps
+            val, te_ms = _replica_value(occ, 1000 * te, dist, world, "cuda")
+            d2h = rec_bytes[0] if result == "records" else int(nrow * (8 * W + 4))
+            return {"value": val, "unit": UNIT, "h2d_bytes_per_step": int(seq.nbytes + offs.nbytes),
+                    "d2h_bytes_per_step": int(d2h), "ms_per_step": te_ms,
+                    "workers": nw, "steps": a.e2e_steps, "result": result,
+                    "what": "host wall clock over all steps; each step: reads copied from pinned host "
+                            "memory, gerbil_partition + gerbil_count_batch, then %s copied to pinned "
+                            "host memory; %d host threads with a context (stream) each"
+                            % ("the App. C output records (gerbil_encode_records)" if result == "records"
+                               else "the rows (gerbil_counts_to_host)", nw)}
+
+        e2e = run_e2e("rows")
+        e2e_rec = run_e2e("records")
         for wctx, _, _ in workers:
             if wctx is not ctx:
                 wctx.close()
-        e2e_value, te_ms = _replica_value(occ, 1000 * te, dist, world, "cuda")
-        te = te_ms / 1000
-        e2e = {"value": e2e_value, "unit": UNIT,
-               "h2d_bytes_per_step": int(seq.nbytes + offs.nbytes),
-               "d2h_bytes_per_step": int(nrow * (8 * W + 4)), "ms_per_step": 1000 * te,
-               "workers": nw, "steps": a.e2e_steps,
-               "what": "host wall clock over all steps; each step: reads copied from pinned host "
-                       "memory, gerbil_partition + gerbil_count_batch, rows copied to pinned host "
-                       "memory; %d host threads with a context (stream) each" % nw}
+        e2e["records_instead"] = {key: e2e_rec[key] for key in
+                                  ("value", "d2h_bytes_per_step", "ms_per_step")}
 
     # the oracle on one core over a bounded sample (cpu_baseline), and the same reads counted
     # on the GPU: row-for-row equality
@@ -709,6 +740,11 @@ def main_ours(a, world, rank, local):
             configs[name] = run_config(a, name, local, hbm, peak_kind)
         if not a.no_serving:
             configs[SERVING_WORKLOAD] = run_serving(a, local, None, 3)
+        rows, ck_k, _, _, G = _ksweep(a, local, KSWEEP_CONFIG_KS, a.config_steps, 3)
+        configs["ksweep-genome%gM-1000bp-20x" % (G / 1e6)] = {
+            "workload": "genome%gM-1000bp-20x, 0.2%% substitutions, m=11, 512 bins, min count 2"
+                        % (G / 1e6), "what": "keys of 10 to 15 words (k = 320, 400, 479)",
+            "clocks": ck_k, "results": rows}
 
     if rank == 0:
         cfg = _config(a.workload, p, seq, offs)
@@ -895,14 +931,16 @@ def main_orderings(a, rank, local):
 KSWEEP = (32, 48, 65, 99, 127, 150, 200, 256, 320, 400, 479)
 
 
-def main_ksweep(a, rank, local):
-    """Throughput against k (Sec. 4 finds the GPU speed-up of the paper's hybrid counter gone
-    beyond k = 150, because fewer wider table entries fit in the parallel window scan).
-    One long-read workload holds every k of the sweep: a 10 Mbp uniform genome (seed 6001;
+KSWEEP_CONFIG_KS = (320, 400, 479)  # the wide-key points carried by the default bench line
+
+
+def _ksweep(a, local, ks, steps, warmup):
+    """Throughput against k on one long-read workload: a 10 Mbp uniform genome (seed 6001;
     --ksweep-genome changes its length), 20x of 1000 bp reads from both strands with 0.2%
-    substitutions (seed 6002), m = 11, 512 bins, min count 2.  Per k: the whole step on the GPU (event-timed, phase split), the
-    insert kernel's byte model and HBM fraction, and the oracle on one core over a bounded
-    sample, whose reads the GPU also counts for a bit-exact check."""
+    substitutions (seed 6002), m = 11, 512 bins, min count 2.  Per k: the whole step on the GPU
+    (event-timed, phase split), the insert kernel's byte model and HBM fraction, and the oracle
+    on one core over a bounded sample, whose reads the GPU also counts for a bit-exact check.
+    Returns (rows, clocks, HBM peak, peak kind, genome length)."""
     import torch
     import oracle
     from paper_1607_06618_b300 import gerbil, synth
@@ -919,7 +957,7 @@ def main_ksweep(a, rank, local):
     hbm, peak_kind = _peaks()
     rows = []
     clocks = Clocks(local)
-    for k in (tuple(int(x) for x in a.ks.split(",")) if a.ks else KSWEEP):
+    for k in ks:
         W = (2 * k + 63) // 64
         WS = (2 * k + 62) // 63
         info = {}
@@ -933,7 +971,7 @@ def main_ksweep(a, rank, local):
             res.free()
             bins.free()
 
-        for i in range(max(3, a.warmup)):
+        for i in range(max(3, warmup)):
             step(record=(i == 0))
         occ = info["occurrences"]
         n_bases = occ + info["n_supermers"] * (k - 1)
@@ -941,11 +979,11 @@ def main_ksweep(a, rank, local):
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        for _ in range(a.steps):
+        for _ in range(steps):
             step()
         e1.record(stream)
         torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1) / a.steps
+        ms = e0.elapsed_time(e1) / steps
         ph = ctx.phase_times()
         ctx.profile(False)
         ins_ms = ph["insert_ms"] / max(1, ph["insert_launches"])
@@ -978,7 +1016,7 @@ def main_ksweep(a, rank, local):
             "k": k, "W": W, "slot_bytes": slot, "slots_per_128B_line": round(128 / slot, 3),
             "occurrences": occ, "distinct": info["distinct"], "emitted": info["emitted"],
             "gpu_kmers_per_s": occ / (ms / 1000.0), "ms_per_step": ms,
-            "phase_ms": {key[:-3]: ph[key] / a.steps for key in
+            "phase_ms": {key[:-3]: ph[key] / steps for key in
                          ("encode_ms", "supermer_ms", "clear_ms", "insert_ms", "compact_ms",
                           "overflow_ms") if key in ph},
             "insert_bytes_per_occ": insert_bytes / occ,
@@ -989,6 +1027,17 @@ def main_ksweep(a, rank, local):
         torch.cuda.empty_cache()
     ck = clocks.stop()
     ctx.close()
+    del s_dev, o_dev
+    torch.cuda.empty_cache()
+    return rows, ck, hbm, peak_kind, G
+
+
+def main_ksweep(a, rank, local):
+    """Throughput against k (Sec. 4 finds the GPU speed-up of the paper's hybrid counter gone
+    beyond k = 150, because fewer wider table entries fit in the parallel window scan), over
+    every k of the sweep (or --ks)."""
+    ks = tuple(int(x) for x in a.ks.split(",")) if a.ks else KSWEEP
+    rows, ck, hbm, peak_kind, G = _ksweep(a, local, ks, a.steps, a.warmup)
     if rank == 0:
         print(json.dumps({"experiment": "throughput against k (Sec. 4, GPU speed-up beyond k = 150)",
                           "workload": "genome%gM-1000bp-20x, 0.2%% substitutions, m=11, 512 "

@@ -371,8 +371,10 @@ void gerbil_counts_free(gerbil_counts* counts);
  * *nbytes receives the size of all records.  out == NULL only computes the size; otherwise out
  * (cap bytes, device memory when out_on_device != 0, else host memory) receives the records.
  * The work runs on the stream of the context that owns the result and synchronizes it; scratch
- * comes from that context.  Errors: E_INVAL (k of another key width, cap too small -- *nbytes
- * is still set), E_NOMEM, E_CUDA. */
+ * comes from that context.  A host buffer with room for rows * (ceil(k/4) + 5) bytes (every
+ * count in its 5-byte form) lets a one-part result skip the size pass before the records are
+ * written: one stream synchronisation instead of two.  Errors: E_INVAL (k of another key width,
+ * cap too small -- *nbytes is still set), E_NOMEM, E_CUDA. */
 int gerbil_encode_records(const gerbil_counts* counts, int k, void* out, uint64_t cap,
                           int out_on_device, uint64_t* nbytes);
 

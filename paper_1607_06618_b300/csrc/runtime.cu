@@ -2082,6 +2082,41 @@ int gerbil_encode_records(const gerbil_counts* c, int k, void* out, uint64_t cap
     CKE(gerbil::launch_encode_scan(t, nt, t + maxt, st));
     ctx->times.kernel_launches += 2;
   }
+  // One part written to host memory that has room for the longest records (every count 5
+  // bytes): the records are written without waiting for their size; the n * (KB + 1) bytes
+  // they take at least are copied back at once, and only the 4-byte extensions of counts of
+  // 255 and more wait for the size (one synchronisation instead of two).
+  if (out && !out_on_device && parts.size() == 1 && parts[0].n && cap >= parts[0].n * (KB + 5)) {
+    const uint64_t lo = parts[0].n * (KB + 1), hi = parts[0].n * (KB + 5);
+    uint8_t* stage = nullptr;
+    if ((rc = dev_alloc(ctx, (void**)&stage, hi))) {
+      cleanup();
+      return rc;
+    }
+    gerbil::EncodeParams ep{};
+    ep.keys = parts[0].keys;
+    ep.counts = parts[0].counts;
+    ep.n = parts[0].n;
+    ep.k = k;
+    ep.tile_long = tl;
+    ep.out = stage;
+    ep.base = 0;
+    cudaError_t e = gerbil::launch_encode_write(ep, st);
+    ctx->times.kernel_launches++;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, stage, lo, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&totals[0], tl + maxt, 8, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    const uint64_t nall = lo + 4 * (uint64_t)totals[0];
+    if (e == cudaSuccess && nall > lo) {
+      e = cudaMemcpyAsync((uint8_t*)out + lo, stage + lo, nall - lo, cudaMemcpyDeviceToHost, st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    }
+    dev_free(ctx, stage, hi);
+    CKE(e);
+    *nbytes = nall;
+    cleanup();
+    return GERBIL_OK;
+  }
   for (size_t i = 0; i < parts.size(); ++i)
     if (parts[i].n) CKE(cudaMemcpyAsync(&totals[i], tl + i * (maxt + 1) + maxt, 8, cudaMemcpyDeviceToHost, st));
   CKE(cudaStreamSynchronize(st));

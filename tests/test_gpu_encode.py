@@ -1,6 +1,6 @@
 """App. C output records written on the GPU equal the oracle's encoder row by row (bytes, no
-tolerance), for one-byte and five-byte counts, every key width, host and device output, and a
-result joined from bin groups."""
+tolerance), for one-byte and five-byte counts, every key width, host and device output (host
+output with and without room for the longest records), and a result joined from bin groups."""
 import numpy as np
 import pytest
 
@@ -52,6 +52,10 @@ def test_records_equal_oracle_encoding(g, k):
     assert host.tobytes() == want
     dev = res.encode_records(k, device=True)
     assert dev.cpu().numpy().tobytes() == want
+    # a host buffer with room for every count in its 5-byte form: written without a size pass
+    room = np.full(len(counts) * ((k + 3) // 4 + 5), 0xAB, dtype=np.uint8)
+    nb = gerbil.gerbil_encode_records(res.handle, k, room.ctypes.data, room.size, 0)
+    assert nb == len(want) and room[:nb].tobytes() == want
     with pytest.raises(gerbil.GerbilError):
         gerbil.gerbil_encode_records(res.handle, k + 64 if k + 64 <= 256 else k - 64)
     res.free()
