@@ -60,6 +60,8 @@ def _args():
     ap.add_argument("--graph", action="store_true", help="phase two as one captured CUDA graph")
     ap.add_argument("--probe-scheme", type=int, default=None,
                     help="0 linear probing (default), 1 windowed double hashing (Sec. 3.3)")
+    ap.add_argument("--claim-first", type=int, default=None,
+                    help="probe order: 0 by the learned distinct ratio, 1 claim first, 2 read first")
     ap.add_argument("--item-kmers", type=int, default=None,
                     help="k-mers per insert work item: 64, 128 or 256 (default)")
     ap.add_argument("--load-factor", type=float, default=None, help="table load factor (0.5)")
@@ -251,7 +253,8 @@ def _device_workload(name):
 
 
 def _insert_kernel_name(k, opts, fused):
-    W, WS = (2 * k + 63) // 64, (2 * k + 62) // 63
+    W = (2 * k + 63) // 64
+    WS = 1 if 2 * k <= 93 else (2 * k - 30 + 62) // 63  # stored chunks beyond the 30-bit tag
     return ("fused_kernel<%d,%d>" if fused else "insert_kernel<%d,%d>") % (W, WS)
 
 
@@ -505,6 +508,8 @@ def main_ours(a, world, rank, local):
         kw["probe_scheme"] = a.probe_scheme
     if a.item_kmers is not None:
         kw["item_kmers"] = a.item_kmers
+    if a.claim_first is not None:
+        kw["claim_first"] = a.claim_first
     if a.load_factor is not None:
         kw["load_factor"] = a.load_factor
     opts = gerbil.default_opts(**kw)
@@ -623,7 +628,7 @@ def main_ours(a, world, rank, local):
         nw = max(1, a.e2e_workers)
         # every worker holds tables of its own: no more workers than sets of tables fit in half
         # the device (one for the 126 GB tables of the long-read workload)
-        slot_bytes = 8 * (((2 * k + 62) // 63 + 2) & ~1)
+        slot_bytes = gerbil.slot_bytes(k)
         half = torch.cuda.get_device_properties(local).total_memory // 2
         nw = max(1, min(nw, half // max(1, info["table_slots"] * slot_bytes)))
         seq_pin = torch.from_numpy(seq).pin_memory()
@@ -958,13 +963,12 @@ def _ksweep(a, local, ks, steps, warmup):
     m, nbins, mc = 11, 512, 2
     stream = torch.cuda.current_stream()
     ctx = gerbil.Context(local, stream=stream.cuda_stream)
-    opts = gerbil.default_opts()
+    opts = gerbil.default_opts(**({} if a.claim_first is None else {"claim_first": a.claim_first}))
     hbm, peak_kind = _peaks()
     rows = []
     clocks = Clocks(local)
     for k in ks:
         W = (2 * k + 63) // 64
-        WS = (2 * k + 62) // 63
         info = {}
 
         def step(record=False):
@@ -1016,7 +1020,7 @@ def _ksweep(a, local, ks, steps, warmup):
                 and np.array_equal(np.asarray(gc, np.uint64)[order], np.asarray(wc, np.uint64)))
         if not same:
             raise SystemExit("k=%d: GPU result differs from the oracle on the sample" % k)
-        slot = 8 * ((WS + 2) & ~1)
+        slot = gerbil.slot_bytes(k)
         rows.append({
             "k": k, "W": W, "slot_bytes": slot, "slots_per_128B_line": round(128 / slot, 3),
             "occurrences": occ, "distinct": info["distinct"], "emitted": info["emitted"],

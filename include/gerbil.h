@@ -164,8 +164,9 @@ typedef struct gerbil_opts {
                                   the device; a grouped result is joined first.  0 (default):
                                   unordered */
   int32_t claim_first;         /* probe order of the insert kernel: 0 (default): chosen per
-                                  batch from the distinct ratio the context learned (claim
-                                  first above 0.6, i.e. when most k-mers are new keys); 1: each
+                                  batch: claim first for keys of ten or more words
+                                  (k > 288) when the distinct ratio the context learned is
+                                  above 0.6, i.e. most k-mers are new keys; 1: each
                                   probe first tries to claim the slot with a CAS on its meta
                                   word and reads the key words only if the slot holds a key
                                   with the same tag (a new key costs one round trip to memory);
@@ -502,8 +503,9 @@ int gerbil_membench(gerbil_ctx* ctx, uint64_t bytes, int op, uint64_t per_thread
  * offsets[nreads] (host value); *n_out (host) receives the number of rows.
  * Scratch: a fixed 32 MiB table in a file-scope device array, held by every GPU that loads
  * the library until the process exits.  Inputs with more than
- * floor((4194304 - 16) / S / 2) k-mer windows, where S = 2 * ceil((ceil(2k/63) + 1) / 2)
- * words per slot (about 1.05 million windows for k <= 31, 524 thousand for k = 65), are
+ * floor((4194304 - 16) / S / 2) k-mer windows, where S = 2 * ceil((C + 1) / 2) words per slot
+ * and C = max(1, ceil((2k - 30) / 63)) (about 1.05 million windows for k <= 46, 524 thousand
+ * for k = 65), are
  * rejected with GERBIL_E_INVAL before any GPU work.  The first call on a device resolves the
  * array's address (cudaGetSymbolAddress) for that device; make that first call before any
  * stream capture.  The address is kept for the life of the process: after a cudaDeviceReset

@@ -29,27 +29,40 @@ struct Counters {
 };
 
 // ---- table slot layout -------------------------------------------------------------------
-// A slot is SW = even(WS+1) 64-bit words: word 0 = meta, words 1..WS = the stored key.  meta's
-// low 32 bits hold the count; the high 32 bits hold CLAIMED | MERGED | 30-bit tag taken from
-// the key's hash; meta == 0 is an empty slot.  The stored key is the 2k-bit key cut into
-// WS = ceil(2k/63) chunks of 63 bits, each with bit 63 set as a "written" marker.  A cleared
-// word (0) can therefore never be mistaken for a written one: a reader that sees every
-// marker set has read the final key, word by word, with relaxed loads and no ordering.
+// A slot is SW = even(WS+1) 64-bit words: word 0 = meta, words 1..WS = the rest of the key.
+// meta's low 32 bits hold the count; the high 32 bits hold CLAIMED | MERGED | the key's low 30
+// bits (its "tag": a reader whose tag differs has another key, without looking further); meta
+// == 0 is an empty slot.  The key's bits from bit 30 up are cut into WS = max(1, ceil((2k -
+// 30) / 63)) chunks of 63 bits, each with bit 63 set as a "written" marker.  A cleared word (0)
+// can therefore never be mistaken for a written one: a reader that sees every marker set has
+// read the final key, word by word, with relaxed loads and no ordering.
 constexpr uint32_t META_CLAIMED = 1u << 31;
 constexpr uint32_t META_MERGED = 1u << 30;
-constexpr uint32_t META_TAG_MASK = (1u << 30) - 1;
+constexpr int KEY_TAG_BITS = 30;
+constexpr uint32_t META_TAG_MASK = (1u << KEY_TAG_BITS) - 1;
 constexpr unsigned long long MERGED64 = (unsigned long long)META_MERGED << 32;
 constexpr unsigned long long MARK = 1ull << 63;
 constexpr unsigned long long MASK63 = MARK - 1;
 
 __host__ __device__ constexpr int slot_words(int WS) { return (WS + 2) & ~1; }
+// chunks of the key beyond the tag: max(1, ceil((2k - 30) / 63))
+__host__ __device__ constexpr int stored_words_of(int k) {
+  return 2 * k <= KEY_TAG_BITS + 63 ? 1 : (2 * k - KEY_TAG_BITS + 62) / 63;
+}
 
-// key (W words, word 0 most significant) -> WS marked 63-bit chunks, chunk 0 least significant
+// the key's low 30 bits: its tag in the meta word
+template <int W>
+__device__ __forceinline__ uint32_t key_tag(const unsigned long long key[W]) {
+  return (uint32_t)key[W - 1] & META_TAG_MASK;
+}
+
+// key (W words, word 0 most significant) -> WS marked 63-bit chunks of its bits from bit 30 up,
+// chunk 0 least significant
 template <int W, int WS>
 __device__ __forceinline__ void to_stored(const unsigned long long key[W], unsigned long long st[WS]) {
 #pragma unroll
   for (int c = 0; c < WS; ++c) {
-    const int L = 63 * c, r = L >> 6, sh = L & 63;  // r counts words from the least significant
+    const int L = KEY_TAG_BITS + 63 * c, r = L >> 6, sh = L & 63;  // r counts words from the least significant
     unsigned long long v = 0;
     if (r < W) v = key[W - 1 - r] >> sh;
     if (sh >= 2 && r + 1 < W) v |= key[W - 2 - r] << (64 - sh);
@@ -62,21 +75,25 @@ __device__ __forceinline__ void to_stored(const unsigned long long key[W], unsig
 template <int W, int C>
 __device__ __forceinline__ unsigned long long stored_chunk(const unsigned long long a[W],
                                                            const unsigned long long b[W], bool use_b) {
-  constexpr int L = 63 * C, r = L >> 6, sh = L & 63;
+  constexpr int L = KEY_TAG_BITS + 63 * C, r = L >> 6, sh = L & 63;
   unsigned long long v = 0;
   if constexpr (r < W) v = (use_b ? b[W - 1 - r] : a[W - 1 - r]) >> sh;
   if constexpr (sh >= 2 && r + 1 < W) v |= (use_b ? b[W - 2 - r] : a[W - 2 - r]) << (64 - sh);
   return MARK | (v & MASK63);
 }
 
+// the key from its tag (the low 30 bits of a meta word's high half, or the tag itself) and its
+// stored chunks
 template <int W, int WS>
-__device__ __forceinline__ void from_stored(const unsigned long long st[WS], unsigned long long key[W]) {
+__device__ __forceinline__ void from_stored(const unsigned long long st[WS], uint32_t tag,
+                                            unsigned long long key[W]) {
 #pragma unroll
   for (int j = 0; j < W; ++j) key[j] = 0;
+  key[W - 1] = tag & META_TAG_MASK;
 #pragma unroll
   for (int c = 0; c < WS; ++c) {
     const unsigned long long v = st[c] & MASK63;
-    const int L = 63 * c, r = L >> 6, sh = L & 63;
+    const int L = KEY_TAG_BITS + 63 * c, r = L >> 6, sh = L & 63;
     if (r < W) key[W - 1 - r] |= v << sh;
     if (sh >= 2 && r + 1 < W) key[W - 2 - r] |= v >> (64 - sh);
   }

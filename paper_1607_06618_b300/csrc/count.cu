@@ -133,8 +133,9 @@ __global__ void __launch_bounds__(256, compact_min_blocks(slot_words(WS))) compa
         }
         if (P.mode == 1) {
           unsigned long long key[W];
-          from_stored<W, WS>(&v[u][1], key);
-          const uint32_t extra = table_take<WS>(P.otab, P.ocap, &v[u][1], key_hash<W>(key));
+          from_stored<W, WS>(&v[u][1], (uint32_t)(mt >> 32), key);
+          const uint32_t extra = table_take<WS>(P.otab, P.ocap, &v[u][1], (uint32_t)(mt >> 32),
+                                                key_hash<W>(key));
           if (extra) atomicAdd(&P.ctr->merged, 1ull);
           c += extra;
         }
@@ -150,7 +151,7 @@ __global__ void __launch_bounds__(256, compact_min_blocks(slot_words(WS))) compa
       if (!cnt[u]) continue;
       if (row < P.out_cap) {
         unsigned long long key[W];
-        from_stored<W, WS>(&v[u][1], key);
+        from_stored<W, WS>(&v[u][1], (uint32_t)(v[u][0] >> 32), key);
 #pragma unroll
         for (int j = 0; j < W; ++j) P.out_keys[row * W + j] = key[j];
         P.out_counts[row] = cnt[u];
@@ -316,7 +317,7 @@ __device__ __forceinline__ void compact_chunk(const FusedParams& F, const BinWor
       if ((uint32_t)v[u][0] >= F.min_count) {
         if (row < F.out_cap) {
           unsigned long long key[W];
-          from_stored<W, WS>(&v[u][1], key);
+          from_stored<W, WS>(&v[u][1], (uint32_t)(v[u][0] >> 32), key);
 #pragma unroll
           for (int j = 0; j < W; ++j) F.out_keys[row * W + j] = key[j];
           F.out_counts[row] = (uint32_t)v[u][0];
@@ -398,7 +399,8 @@ __global__ void __launch_bounds__(256) overflow_insert_kernel(OverflowParams P) 
     for (int j = 0; j < W; ++j) key[j] = P.ovf[i * W + j];
     unsigned long long st[WS];
     to_stored<W, WS>(key, st);
-    const int res = table_insert<WS>(P.otab, P.ocap, st, key_hash<W>(key), P.ocap, P.spin_limit);
+    const int res = table_insert<WS>(P.otab, P.ocap, st, key_tag<W>(key), key_hash<W>(key), P.ocap,
+                                     P.spin_limit);
     if (res) set_err(P.ctr, ERR_SPIN);
   }
 }
@@ -424,7 +426,7 @@ __global__ void __launch_bounds__(256) overflow_emit_kernel(OverflowParams P) {
         unsigned long long st[WS];
 #pragma unroll
         for (int j = 0; j < WS; ++j) st[j] = sp[1 + j];
-        from_stored<W, WS>(st, key);
+        from_stored<W, WS>(st, (uint32_t)(mt >> 32), key);
         c = (uint32_t)mt;
         emit = c >= P.min_count;
       }
@@ -436,7 +438,7 @@ __global__ void __launch_bounds__(256) overflow_emit_kernel(OverflowParams P) {
 }
 
 // ---- launchers: dispatch on (W, WS) (GERBIL_KEY_SWITCH, insert.cuh) ---------------------------
-int stored_words(int k) { return (2 * k + 62) / 63; }
+int stored_words(int k) { return stored_words_of(k); }
 int slot_words_for_k(int k) { return slot_words(stored_words(k)); }
 uint32_t probe_window_for_k(int k) { return probe_window(slot_words_for_k(k)); }
 
@@ -569,7 +571,7 @@ __global__ void __launch_bounds__(256) noalloc_insert_kernel(const uint8_t* __re
       to_stored<W, WS>(key, st);
       // flag bit 0: no free slot within cap probes; bit 1: a bounded wait for a peer's key
       // words gave up (reported apart, as a timeout)
-      const int res = table_insert<WS>(tab, cap, st, key_hash<W>(key), cap, 1u << 20);
+      const int res = table_insert<WS>(tab, cap, st, key_tag<W>(key), key_hash<W>(key), cap, 1u << 20);
       if (res) atomicOr(reinterpret_cast<unsigned int*>(scratch + 1), res == 2 ? 2u : 1u);
     }
   }
@@ -595,7 +597,7 @@ __global__ void __launch_bounds__(256) noalloc_compact_kernel(unsigned long long
     unsigned long long st[WS], key[W];
 #pragma unroll
     for (int j = 0; j < WS; ++j) st[j] = sp[1 + j];
-    from_stored<W, WS>(st, key);
+    from_stored<W, WS>(st, (uint32_t)(mt >> 32), key);
 #pragma unroll
     for (int j = 0; j < W; ++j) keys_out[row * W + j] = key[j];
     counts_out[row] = (uint32_t)mt;

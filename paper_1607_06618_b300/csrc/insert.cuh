@@ -21,58 +21,58 @@ __device__ __forceinline__ void static_for(F&& f) {
   }
 }
 
-// Dispatch on the key width W = ceil(2k/64) and the stored words WS = ceil(2k/63) (W or W+1).
+// Dispatch on the key width W = ceil(2k/64) and the stored chunks WS = stored_words_of(k)
+// (W - 1 or W from two words on).
 #define GERBIL_KEY_SWITCH(W, WS, CALL)                 \
   switch (W * 32 + WS) {                               \
     case 1 * 32 + 1: CALL(1, 1); break;                \
-    case 1 * 32 + 2: CALL(1, 2); break;                \
+    case 2 * 32 + 1: CALL(2, 1); break;                \
     case 2 * 32 + 2: CALL(2, 2); break;                \
-    case 2 * 32 + 3: CALL(2, 3); break;                \
+    case 3 * 32 + 2: CALL(3, 2); break;                \
     case 3 * 32 + 3: CALL(3, 3); break;                \
-    case 3 * 32 + 4: CALL(3, 4); break;                \
+    case 4 * 32 + 3: CALL(4, 3); break;                \
     case 4 * 32 + 4: CALL(4, 4); break;                \
-    case 4 * 32 + 5: CALL(4, 5); break;                \
+    case 5 * 32 + 4: CALL(5, 4); break;                \
     case 5 * 32 + 5: CALL(5, 5); break;                \
-    case 5 * 32 + 6: CALL(5, 6); break;                \
+    case 6 * 32 + 5: CALL(6, 5); break;                \
     case 6 * 32 + 6: CALL(6, 6); break;                \
-    case 6 * 32 + 7: CALL(6, 7); break;                \
+    case 7 * 32 + 6: CALL(7, 6); break;                \
     case 7 * 32 + 7: CALL(7, 7); break;                \
-    case 7 * 32 + 8: CALL(7, 8); break;                \
+    case 8 * 32 + 7: CALL(8, 7); break;                \
     case 8 * 32 + 8: CALL(8, 8); break;                \
-    case 8 * 32 + 9: CALL(8, 9); break;                \
+    case 9 * 32 + 8: CALL(9, 8); break;                \
     case 9 * 32 + 9: CALL(9, 9); break;                \
-    case 9 * 32 + 10: CALL(9, 10); break;              \
+    case 10 * 32 + 9: CALL(10, 9); break;              \
     case 10 * 32 + 10: CALL(10, 10); break;            \
-    case 10 * 32 + 11: CALL(10, 11); break;            \
+    case 11 * 32 + 10: CALL(11, 10); break;            \
     case 11 * 32 + 11: CALL(11, 11); break;            \
-    case 11 * 32 + 12: CALL(11, 12); break;            \
+    case 12 * 32 + 11: CALL(12, 11); break;            \
     case 12 * 32 + 12: CALL(12, 12); break;            \
-    case 12 * 32 + 13: CALL(12, 13); break;            \
+    case 13 * 32 + 12: CALL(13, 12); break;            \
     case 13 * 32 + 13: CALL(13, 13); break;            \
-    case 13 * 32 + 14: CALL(13, 14); break;            \
+    case 14 * 32 + 13: CALL(14, 13); break;            \
     case 14 * 32 + 14: CALL(14, 14); break;            \
-    case 14 * 32 + 15: CALL(14, 15); break;            \
+    case 15 * 32 + 14: CALL(15, 14); break;            \
     case 15 * 32 + 15: CALL(15, 15); break;            \
-    case 15 * 32 + 16: CALL(15, 16); break;            \
     default: return cudaErrorInvalidValue;             \
   }
 
 // ---- table insert (Alg. 1) -------------------------------------------------------------------
 // Probe sequence: slot0 = fastrange(hash), then linear steps, at most theta probes (Alg. 1's
 // trial limit).  Each probe reads the whole slot with relaxed 16-byte loads.  An empty slot is
-// claimed by CAS on its meta word (0 -> CLAIMED|tag, count 1); the claimer then writes the
-// marked key words.  A prober whose tag matches compares the key once every word carries its
+// claimed by CAS on its meta word (0 -> CLAIMED|tag, count 1; the tag is the key's low 30 bits);
+// the claimer then writes the marked key words.  A prober whose tag matches compares the key once every word carries its
 // marker (bounded wait otherwise) and adds 1 to the count.  Returns 0 on success, 1 if theta
 // probes found no room, 2 if a bounded wait gave up -- both send the k-mer to the overflow
 // area, which is always correct because overflow counts are added to table counts before
 // the min_count filter.
 template <int WS>
 __device__ __forceinline__ int table_insert_from(unsigned long long* __restrict__ tab, uint32_t cap,
-                                                 const unsigned long long st[WS], unsigned long long h,
+                                                 const unsigned long long st[WS], uint32_t tag,
                                                  uint32_t theta, uint32_t spin_limit, uint32_t s,
                                                  unsigned long long v[slot_words(WS)]) {
   constexpr int SW = slot_words(WS);
-  const uint32_t tagw = META_CLAIMED | (uint32_t)((h >> 34) & META_TAG_MASK);
+  const uint32_t tagw = META_CLAIMED | (tag & META_TAG_MASK);
   const unsigned long long claim = ((unsigned long long)tagw << 32) | 1ull;
   for (uint32_t t = 0; t < theta; ++t) {
     unsigned long long* slot = tab + (unsigned long long)s * SW;
@@ -123,25 +123,27 @@ __device__ __forceinline__ uint32_t slot_of(unsigned long long h, uint32_t cap) 
   return (uint32_t)(((h & 0xFFFFFFFFull) * (unsigned long long)cap) >> 32);
 }
 
+// st, tag: the key's stored chunks and its low 30 bits; h: its hash (the first slot)
 template <int WS>
 __device__ __forceinline__ int table_insert(unsigned long long* __restrict__ tab, uint32_t cap,
-                                            const unsigned long long st[WS], unsigned long long h,
-                                            uint32_t theta, uint32_t spin_limit) {
+                                            const unsigned long long st[WS], uint32_t tag,
+                                            unsigned long long h, uint32_t theta, uint32_t spin_limit) {
   constexpr int SW = slot_words(WS);
   const uint32_t s = slot_of(h, cap);
   unsigned long long v[SW];
   load_slot<SW>(tab + (unsigned long long)s * SW, v);
-  return table_insert_from<WS>(tab, cap, st, h, theta, spin_limit, s, v);
+  return table_insert_from<WS>(tab, cap, st, tag, theta, spin_limit, s, v);
 }
 
 // Lookup in a complete table (no concurrent inserts); marks the slot MERGED and returns its
 // count, or 0 if the key is absent.
 template <int WS>
 __device__ __forceinline__ uint32_t table_take(unsigned long long* __restrict__ tab, uint32_t cap,
-                                               const unsigned long long st[WS], unsigned long long h) {
+                                               const unsigned long long st[WS], uint32_t tag,
+                                               unsigned long long h) {
   constexpr int SW = slot_words(WS);
   uint32_t s = (uint32_t)(((h & 0xFFFFFFFFull) * (unsigned long long)cap) >> 32);
-  const uint32_t tagw = META_CLAIMED | (uint32_t)((h >> 34) & META_TAG_MASK);
+  const uint32_t tagw = META_CLAIMED | (tag & META_TAG_MASK);
   for (uint32_t t = 0; t < cap; ++t) {
     unsigned long long* slot = tab + (unsigned long long)s * SW;
     const unsigned long long mt = slot[0];
@@ -285,6 +287,7 @@ __device__ __forceinline__ void insert_item(const CountParams& P, uint32_t wi, c
   unsigned long long st[LAZY ? 1 : WS];
   bool urc = false;  // LAZY: the key is rc (else fwd)
   uint32_t tagw = 0, s = 0, t = 0, spins = 0;
+  uint32_t wstep = 0;  // scheme 1: 30 hash bits that give the window step
   uint32_t j = ja;
   bool busy = false;
   // chunk u of the stored key in flight
@@ -336,9 +339,13 @@ __device__ __forceinline__ void insert_item(const CountParams& P, uint32_t wi, c
       const unsigned long long h = key_hash<W>(key);
       if constexpr (LAZY) urc = use_rc;
       else to_stored<W, WS>(key, st);
-      tagw = META_CLAIMED | (uint32_t)((h >> 34) & META_TAG_MASK);
-      if constexpr (windowed) s = slot_of(h, nwin) * WIN;
-      else s = slot_of(h, wk.cap);
+      tagw = META_CLAIMED | key_tag<W>(key);
+      if constexpr (windowed) {
+        s = slot_of(h, nwin) * WIN;
+        wstep = (uint32_t)(h >> 34) & META_TAG_MASK;
+      } else {
+        s = slot_of(h, wk.cap);
+      }
       t = 0;
       spins = 0;
       busy = true;
@@ -413,8 +420,8 @@ __device__ __forceinline__ void insert_item(const CountParams& P, uint32_t wi, c
           continue;
         }
         if (++t < P.theta) {  // the next window of the double-hashing sequence
-          const uint32_t h2 = nwin > 1 ? 1u + (uint32_t)(((unsigned long long)(tagw & META_TAG_MASK) *
-                                                          (nwin - 1)) >> 30) : 0u;
+          const uint32_t h2 = nwin > 1 ? 1u + (uint32_t)(((unsigned long long)wstep * (nwin - 1)) >> 30)
+                                       : 0u;
           uint32_t w = s / WIN + h2;
           if (w >= nwin) w -= nwin;
           s = w * WIN;
@@ -428,7 +435,7 @@ __device__ __forceinline__ void insert_item(const CountParams& P, uint32_t wi, c
 #pragma unroll
       for (int u = 0; u < W; ++u) key[u] = urc ? rc[u] : fwd[u];
     } else {
-      from_stored<W, WS>(st, key);
+      from_stored<W, WS>(st, tagw, key);
     }
     to_overflow<W>(P, wi, key, why);
     if constexpr (STATS) record_probe<SW>(P, wk, s, t, why);

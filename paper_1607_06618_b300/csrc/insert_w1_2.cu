@@ -7,9 +7,8 @@ cudaError_t launch_insert_w1_2(int W, int WS, const CountParams& p, unsigned lon
                             int persistent, int nsm, cudaStream_t st) {
   switch (W * 32 + WS) {
     case 1 * 32 + 1: return launch_insert_w<1, 1>(p, need, persistent, nsm, st);
-    case 1 * 32 + 2: return launch_insert_w<1, 2>(p, need, persistent, nsm, st);
+    case 2 * 32 + 1: return launch_insert_w<2, 1>(p, need, persistent, nsm, st);
     case 2 * 32 + 2: return launch_insert_w<2, 2>(p, need, persistent, nsm, st);
-    case 2 * 32 + 3: return launch_insert_w<2, 3>(p, need, persistent, nsm, st);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -6,8 +6,8 @@ namespace gerbil {
 cudaError_t launch_insert_w3(int W, int WS, const CountParams& p, unsigned long long need,
                             int persistent, int nsm, cudaStream_t st) {
   switch (W * 32 + WS) {
+    case 3 * 32 + 2: return launch_insert_w<3, 2>(p, need, persistent, nsm, st);
     case 3 * 32 + 3: return launch_insert_w<3, 3>(p, need, persistent, nsm, st);
-    case 3 * 32 + 4: return launch_insert_w<3, 4>(p, need, persistent, nsm, st);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -6,8 +6,8 @@ namespace gerbil {
 cudaError_t launch_insert_w4(int W, int WS, const CountParams& p, unsigned long long need,
                             int persistent, int nsm, cudaStream_t st) {
   switch (W * 32 + WS) {
+    case 4 * 32 + 3: return launch_insert_w<4, 3>(p, need, persistent, nsm, st);
     case 4 * 32 + 4: return launch_insert_w<4, 4>(p, need, persistent, nsm, st);
-    case 4 * 32 + 5: return launch_insert_w<4, 5>(p, need, persistent, nsm, st);
     default: return cudaErrorInvalidValue;
   }
 }

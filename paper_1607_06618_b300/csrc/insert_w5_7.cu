@@ -6,12 +6,12 @@ namespace gerbil {
 cudaError_t launch_insert_w5_7(int W, int WS, const CountParams& p, unsigned long long need,
                             int persistent, int nsm, cudaStream_t st) {
   switch (W * 32 + WS) {
+    case 5 * 32 + 4: return launch_insert_w<5, 4>(p, need, persistent, nsm, st);
     case 5 * 32 + 5: return launch_insert_w<5, 5>(p, need, persistent, nsm, st);
-    case 5 * 32 + 6: return launch_insert_w<5, 6>(p, need, persistent, nsm, st);
+    case 6 * 32 + 5: return launch_insert_w<6, 5>(p, need, persistent, nsm, st);
     case 6 * 32 + 6: return launch_insert_w<6, 6>(p, need, persistent, nsm, st);
-    case 6 * 32 + 7: return launch_insert_w<6, 7>(p, need, persistent, nsm, st);
+    case 7 * 32 + 6: return launch_insert_w<7, 6>(p, need, persistent, nsm, st);
     case 7 * 32 + 7: return launch_insert_w<7, 7>(p, need, persistent, nsm, st);
-    case 7 * 32 + 8: return launch_insert_w<7, 8>(p, need, persistent, nsm, st);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -160,7 +160,8 @@ struct OverflowParams {
   Counters* ctr;
 };
 
-// Table slots hold the key cut into ceil(2k/63) marked words (see common.cuh); a slot is
+// Table slots hold the key's low 30 bits in the meta word and the rest cut into
+// stored_words(k) = max(1, ceil((2k - 30) / 63)) marked words (see common.cuh); a slot is
 // slot_words_for_k(k) 64-bit words.  Launchers dispatch on k.
 int stored_words(int k);
 int slot_words_for_k(int k);

@@ -801,15 +801,16 @@ static Sizing make_sizing(const gerbil_ctx* ctx, const gerbil_opts& o, int k) {
 }
 
 // Probe order (gerbil_opts.claim_first): claim first when most k-mers of the batch are expected
-// to be new keys, where a load-then-CAS costs two accesses per new key against one for the CAS
-// first.  The threshold is measured: at distinct ratio 0.55 (k = 320 on 1000 bp reads) reading
-// first was still 9% faster, at 0.63 and 0.71 (k = 400, 479) claiming first 6% and 12%, at 1.0
-// (long reads with 10% errors, k = 200) 3%.
-static int claim_first_for(const gerbil_ctx* ctx, const gerbil_opts& o) {
+// to be new keys and the key is wide, where a load-then-CAS costs two accesses per new key
+// against one for the CAS first.  Measured on the 1000 bp read sweep: claiming first was 6%
+// faster at k = 400 and 479 (distinct ratios 0.63 and 0.71, keys of 13 and 15 words) and
+// slower at every k up to 320 (ratios up to 0.55), and on long reads with 10% errors at k = 200
+// (every key new, 7 words, tables in HBM) 8% slower.
+static int claim_first_for(const gerbil_ctx* ctx, const gerbil_opts& o, int k) {
   if (o.claim_first == 1) return 1;
   if (o.claim_first == 2) return 0;
   const double r = o.distinct_ratio > 0.0f ? (double)o.distinct_ratio : (ctx->ratio_known ? ctx->ratio : 1.0);
-  return r > 0.6 ? 1 : 0;
+  return r > 0.6 && words_for(k) >= 10 ? 1 : 0;
 }
 
 // ---- phase two, fused persistent form -----------------------------------------------------------
@@ -1170,7 +1171,7 @@ static int count_waves(gerbil_ctx* ctx, const gerbil_bins* b, const std::vector<
   cp.schedule = opts.schedule;
   cp.wide_tables = tables_beyond_l2(ctx, work, SW);
   cp.scheme = 0;  // waves probe linearly, in 256-k-mer items
-  cp.cas_first = claim_first_for(ctx, opts);
+  cp.cas_first = claim_first_for(ctx, opts, k);
   cp.item_kmers = gerbil::ITEM_KMERS;
   if (items) {
     cp.nitems = items;
@@ -1512,7 +1513,7 @@ static int count_impl(gerbil_ctx* ctx, const gerbil_bins* b, const std::vector<i
     cp.schedule = opts.schedule;
     cp.wide_tables = tables_beyond_l2(ctx, work, gerbil::slot_words_for_k(k));
     cp.scheme = (int)sz.scheme;
-    cp.cas_first = claim_first_for(ctx, opts);
+    cp.cas_first = claim_first_for(ctx, opts, k);
     cp.item_kmers = sz.item;
     if (items) {
       CKG(gerbil::launch_item_map(cp, ls));  // preparation: timed with the clears

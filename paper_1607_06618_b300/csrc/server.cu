@@ -23,6 +23,7 @@
 #include <cuda_runtime.h>
 
 #include "../../include/gerbil.h"
+#include "kernels.h"
 
 namespace {
 
@@ -83,8 +84,8 @@ namespace {
 // result rows), whichever is larger.
 uint64_t estimate_bytes(const gerbil_server* s, const Job& j) {
   const int k = j.k, m = j.m;
-  const double W = (2 * k + 63) / 64, WS = (2 * k + 62) / 63;
-  const double slot = 8.0 * (double)(((int)WS + 2) & ~1);
+  const double W = (2 * k + 63) / 64;
+  const double slot = 8.0 * (double)gerbil::slot_words_for_k(k);
   const gerbil_opts& o = j.opts;
   const double alpha = (o.load_factor > 0.05f && o.load_factor <= 0.95f) ? o.load_factor : 0.5;
   double ratio = 1.0;

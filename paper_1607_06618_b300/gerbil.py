@@ -148,6 +148,13 @@ class gerbil_job_times(ctypes.Structure):
 
 
 CUDA_STREAM_LEGACY = 1  # cudaStreamLegacy
+
+
+def slot_bytes(k: int) -> int:
+    """Bytes of one hash-table slot at k (include/gerbil.h table layout): the meta word with
+    the key's low 30 bits, then the rest of the key in 63-bit chunks, rounded to 16 bytes."""
+    ws = 1 if 2 * k <= 30 + 63 else (2 * k - 30 + 62) // 63
+    return 8 * ((ws + 2) & ~1)
 _lib = None
 
 

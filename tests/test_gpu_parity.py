@@ -122,8 +122,13 @@ def test_partition_edge_reads(g):
 
 # ---- phase two -------------------------------------------------------------------------
 
-# the first and last k of every (key words, stored chunks) pair from k = 8 to the paper's 479
-@pytest.mark.parametrize("k", [8, 31, 32, 33, 63, 64, 65, 94, 95, 96, 97, 99, 126, 127, 128, 129, 157, 158, 160, 161, 189, 190, 192, 193, 200, 220, 221, 224, 225, 252, 253, 256, 257, 283, 284, 288, 289, 300, 315, 316, 320, 321, 346, 347, 352, 353, 378, 379, 384, 385, 409, 410, 416, 417, 441, 442, 448, 449, 472, 473, 479])
+# the first and last k of every (key words, stored chunks) pair from k = 8 to the paper's 479:
+# the key's low 30 bits sit in the meta word, the rest in max(1, ceil((2k - 30) / 63)) chunks
+@pytest.mark.parametrize("k", [8, 15, 16, 31, 32, 33, 46, 47, 64, 65, 78, 79, 96, 97, 99, 109,
+                               110, 128, 129, 141, 142, 160, 161, 172, 173, 192, 193, 200, 204,
+                               205, 224, 225, 235, 236, 256, 257, 267, 268, 288, 289, 298, 299,
+                               320, 321, 330, 331, 352, 353, 361, 362, 384, 385, 393, 394, 416,
+                               417, 424, 425, 448, 449, 456, 457, 479])
 def test_count_matches_oracle_all_word_counts(g, k):
     m = min(11, k - 1)
     seq, offs = synth.random_small(400, max(1, k - 4), k + 300, p_n=0.003, seed=1000 + k,
@@ -220,7 +225,7 @@ def test_count_wide_keys_tables_beyond_l2(g, k):
     offs = np.concatenate([offs, offs[1:301] + offs[-1]])
     ctx.forget_ratio()
     got, st = _gpu_count(g, seq, offs, k, 11, 1, 1)
-    slot = 8 * (((2 * k + 62) // 63 + 2) & ~1)
+    slot = gerbil.slot_bytes(k)
     assert st["table_slots"] * slot > torch.cuda.get_device_properties(0).L2_cache_size
     assert_same_rows(got, oracle.count(seq, offs, k, canonical=True, min_count=1))
 
