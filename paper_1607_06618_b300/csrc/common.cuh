@@ -229,9 +229,9 @@ __device__ __forceinline__ bool key_less(const unsigned long long a[W],
   return false;
 }
 
-// 64-bit hash of a key (the slot index uses the low 32 bits, the tag bits 34..63): the words
-// are folded into one by xor with distinct rotations, then mixed by two multiply/xorshift
-// rounds -- two 64-bit multiplies whatever W.
+// 64-bit hash of a key (the slot index uses the low 32 bits, the windowed scheme's window step
+// bits 34..63): the words are folded into one by xor with distinct rotations, then mixed by two
+// multiply/xorshift rounds -- two 64-bit multiplies whatever W.
 template <int W>
 __device__ __forceinline__ unsigned long long key_hash(const unsigned long long key[W]) {
   unsigned long long h = key[W - 1];

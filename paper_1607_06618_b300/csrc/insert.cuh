@@ -60,9 +60,10 @@ __device__ __forceinline__ void static_for(F&& f) {
 // ---- table insert (Alg. 1) -------------------------------------------------------------------
 // Probe sequence: slot0 = fastrange(hash), then linear steps, at most theta probes (Alg. 1's
 // trial limit).  Each probe reads the whole slot with relaxed 16-byte loads.  An empty slot is
-// claimed by CAS on its meta word (0 -> CLAIMED|tag, count 1; the tag is the key's low 30 bits);
-// the claimer then writes the marked key words.  A prober whose tag matches compares the key once every word carries its
-// marker (bounded wait otherwise) and adds 1 to the count.  Returns 0 on success, 1 if theta
+// claimed by CAS on its meta word (0 -> CLAIMED|tag, count 1; the tag is the key's low 30
+// bits); the claimer then writes the marked key words.  A prober whose tag matches compares the
+// rest of the key once every word carries its marker (bounded wait otherwise) and adds 1 to the
+// count.  Returns 0 on success, 1 if theta
 // probes found no room, 2 if a bounded wait gave up -- both send the k-mer to the overflow
 // area, which is always correct because overflow counts are added to table counts before
 // the min_count filter.
@@ -222,9 +223,9 @@ struct WarpSmem {
 // Probe schemes (BinWork::scheme).  0: linear probing from a fastrange slot, one slot per step.
 // 1: the paper's windowed double hashing (Sec. 3.3-3.4): the table is a sequence of windows of
 // probe_window(SW) slots (one 128-byte line for slots of 16 or 32 bytes); the first window is
-// fastrange(hash) over the windows, the next ones step by h2 = 1 + fastrange(tag, windows - 1)
-// windows (mod the window count), and every window is scanned from its first slot, one slot
-// per step.  theta counts slots under scheme 0 and windows under scheme 1.
+// fastrange(hash) over the windows, the next ones step by h2 = 1 + fastrange(bits 34..63 of the
+// hash, windows - 1) windows (mod the window count), and every window is scanned from its first
+// slot, one slot per step.  theta counts slots under scheme 0 and windows under scheme 1.
 __host__ __device__ constexpr uint32_t probe_window(int SW) {
   return (128 / (8 * SW)) >= 1 ? (uint32_t)(128 / (8 * SW)) : 1u;
 }
