@@ -30,6 +30,10 @@ struct gerbil_ctx {
   size_t arena_dirty = 0;  // bytes at the start of the table arena that may be non-zero
   double ratio = 1.0;  // distinct / occurrences measured on earlier calls
   bool ratio_known = false;
+  // rows / occurrences of the last batch counted at emit_min_count (sizes the result buffer)
+  double emit_ratio = 1.0;
+  uint32_t emit_min_count = 0;
+  bool emit_known = false;
   Counters* ctr = nullptr;   // device
   Counters* hctr = nullptr;  // pinned host mirror
   std::string last_error;
@@ -340,6 +344,7 @@ int gerbil_get_probe_stats(const gerbil_ctx* cctx, uint64_t* slots, uint64_t* li
 int gerbil_forget_ratio(gerbil_ctx* ctx) {
   if (!ctx) return GERBIL_E_INVAL;
   ctx->ratio_known = false;
+  ctx->emit_known = false;
   return GERBIL_OK;
 }
 
@@ -1405,7 +1410,16 @@ static int count_impl(gerbil_ctx* ctx, const gerbil_bins* b, const std::vector<i
     // plus the overflow-only keys; if that is large, a count-only pass sizes it exactly
     uint64_t out_cap = std::max<uint64_t>(
         1, std::min<uint64_t>({occ, slots + ovf_cap, (uint64_t)std::ceil(ratio * (double)occ) + ovf_cap}));
-    const bool exact_out = exact_retry || out_cap * (uint64_t)(W * 8 + 4) > (2ull << 30);
+    // the rows of the last batch at this min_count, per occurrence, bound a repeated batch's
+    // rows far better than its distinct keys do (a low estimate is caught: the batch is then
+    // counted again with an exact count-only pass first)
+    if (ctx->emit_known && ctx->emit_min_count == min_count)
+      out_cap = std::max<uint64_t>(1, std::min<uint64_t>(
+          out_cap, (uint64_t)std::ceil(1.25 * ctx->emit_ratio * (double)occ) + 65536 + ovf_cap));
+    // a count-only pass first (one more scan of every table) only for a result too large to
+    // hold at its estimate: above 2 GB and a quarter of the table limit
+    const uint64_t exact_bytes = std::max<uint64_t>(2ull << 30, table_limit(ctx, opts) / 4);
+    const bool exact_out = exact_retry || out_cap * (uint64_t)(W * 8 + 4) > exact_bytes;
     gerbil_counts* res = nullptr;
     auto drop = [&]() {
       if (res) gerbil_counts_free(res);
@@ -1686,6 +1700,9 @@ static int count_impl(gerbil_ctx* ctx, const gerbil_bins* b, const std::vector<i
     if (occ > 0) {
       ctx->ratio = (double)h.distinct / (double)occ;
       ctx->ratio_known = true;
+      ctx->emit_ratio = (double)h.out_count / (double)occ;
+      ctx->emit_min_count = min_count;
+      ctx->emit_known = true;
     }
     *out = res;
     return GERBIL_OK;
