@@ -17,19 +17,28 @@ namespace gerbil {
 // item_kmers/32 consecutive k-mers of the item, reads its bases through L1 and inserts.  No
 // CTA-wide barrier is involved.
 
+// One thread per work item: its work entry (the last with item_begin <= item) and, within the
+// bin, the last super-mer whose first k-mer is at most the item's first k-mer (both binary
+// searches), so that every thread does the same work whatever the bins' sizes.
 __global__ void __launch_bounds__(256) item_map_kernel(const BinWork* __restrict__ work, uint32_t nwork,
                                                       const uint32_t* __restrict__ sm_koff,
-                                                      unsigned long long* __restrict__ imap) {
-  for (uint32_t wi = blockIdx.x; wi < nwork; wi += gridDim.x) {
-    const BinWork wk = work[wi];
-    const uint32_t item_kmers = wk.item_kmers;
-    const uint32_t* koff = sm_koff + wk.sm_begin;
-    for (uint32_t s = threadIdx.x; s < wk.n_super; s += blockDim.x) {
-      const unsigned long long a = koff[s];
-      const unsigned long long b = (s + 1 < wk.n_super) ? koff[s + 1] : wk.n_kmers;
-      for (unsigned long long t = (a + item_kmers - 1) / item_kmers; t * item_kmers < b; ++t)
-        imap[wk.item_begin + t] = ((unsigned long long)wi << 32) | s;
+                                                      unsigned long long* __restrict__ imap,
+                                                      unsigned long long nitems) {
+  for (unsigned long long it = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; it < nitems;
+       it += (unsigned long long)gridDim.x * blockDim.x) {
+    uint32_t lo = 0, hi = nwork;
+    while (hi - lo > 1) {
+      const uint32_t mid = (lo + hi) >> 1;
+      if (__ldg(&work[mid].item_begin) <= it) lo = mid; else hi = mid;
     }
+    const unsigned long long j0 = (it - __ldg(&work[lo].item_begin)) * (unsigned long long)__ldg(&work[lo].item_kmers);
+    const uint32_t* koff = sm_koff + __ldg(&work[lo].sm_begin);
+    uint32_t a = 0, b = __ldg(&work[lo].n_super);
+    while (b - a > 1) {
+      const uint32_t mid = (a + b) >> 1;
+      if (__ldg(koff + mid) <= j0) a = mid; else b = mid;
+    }
+    imap[it] = ((unsigned long long)lo << 32) | a;
   }
 }
 
@@ -442,10 +451,10 @@ int stored_words(int k) { return stored_words_of(k); }
 int slot_words_for_k(int k) { return slot_words(stored_words(k)); }
 uint32_t probe_window_for_k(int k) { return probe_window(slot_words_for_k(k)); }
 
-cudaError_t launch_item_map(const CountParams& p, cudaStream_t st) {
-  if (p.nwork == 0) return cudaSuccess;
-  item_map_kernel<<<std::min<unsigned>(p.nwork, 4096u), 256, 0, st>>>(p.work, p.nwork, p.sm_koff,
-                                                                      p.imap);
+cudaError_t launch_item_map(const CountParams& p, int nsm, cudaStream_t st) {
+  if (p.nwork == 0 || p.nitems == 0) return cudaSuccess;
+  const unsigned long long blocks = std::min<unsigned long long>((p.nitems + 255) / 256, (unsigned long long)nsm * 8);
+  item_map_kernel<<<(unsigned)blocks, 256, 0, st>>>(p.work, p.nwork, p.sm_koff, p.imap, p.nitems);
   return cudaGetLastError();
 }
 

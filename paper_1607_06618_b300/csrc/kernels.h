@@ -168,7 +168,8 @@ int slot_words_for_k(int k);
 // slots per probe window of scheme 1 for keys of length k (a table's cap and first slot are
 // multiples of it when it uses scheme 1)
 uint32_t probe_window_for_k(int k);
-cudaError_t launch_item_map(const CountParams& p, cudaStream_t st);
+// imap of items [0, p.nitems): one thread per item (p.work, p.nwork, p.sm_koff)
+cudaError_t launch_item_map(const CountParams& p, int nsm, cudaStream_t st);
 cudaError_t launch_task_map(const FusedParams& p, cudaStream_t st);
 cudaError_t launch_fused(int k, const FusedParams& p, int nsm, cudaStream_t st);
 cudaError_t launch_insert(int k, const CountParams& p, int persistent, int nsm, cudaStream_t st);

@@ -1180,7 +1180,7 @@ static int count_waves(gerbil_ctx* ctx, const gerbil_bins* b, const std::vector<
   cp.item_kmers = gerbil::ITEM_KMERS;
   if (items) {
     cp.nitems = items;
-    CKW(gerbil::launch_item_map(cp, st));
+    CKW(gerbil::launch_item_map(cp, ctx->nsm, st));
     ctx->times.kernel_launches++;
   }
   ph_end(ctx, PH_CLEAR);
@@ -1530,7 +1530,7 @@ static int count_impl(gerbil_ctx* ctx, const gerbil_bins* b, const std::vector<i
     cp.cas_first = claim_first_for(ctx, opts, k);
     cp.item_kmers = sz.item;
     if (items) {
-      CKG(gerbil::launch_item_map(cp, ls));  // preparation: timed with the clears
+      CKG(gerbil::launch_item_map(cp, ctx->nsm, ls));  // preparation: timed with the clears
       ctx->times.kernel_launches++;
     }
     ph_end(ctx, PH_CLEAR, ls, capturing);
