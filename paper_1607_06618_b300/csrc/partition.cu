@@ -21,6 +21,30 @@ __device__ __forceinline__ void encode_byte(uint32_t c, unsigned long long& word
   mask |= (ok ? 0u : 1u) << (31 - j);
 }
 
+// 0x80 in every byte of x that is not zero, 0 elsewhere (the low seven bits plus 0x7F carry
+// into bit 7 when any is set; no byte carries into the next).
+__device__ __forceinline__ uint32_t nonzero_bytes(uint32_t x) {
+  return (((x & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | x) & 0x80808080u;
+}
+
+// The same encoding for the four bases of one little-endian 32-bit word (first base in the low
+// byte), all four bytes at once: codes = the four 2-bit codes, first base in bits 7..6; bad = the
+// four undetermined flags, first base in bit 3.  Equal to encode_byte on each byte for every
+// 32-bit input.
+__device__ __forceinline__ void encode_word4(uint32_t v, uint32_t& codes, uint32_t& bad) {
+  const uint32_t u = v & 0xDFDFDFDFu;
+  const uint32_t none = nonzero_bytes(u ^ 0x41414141u) & nonzero_bytes(u ^ 0x43434343u) &
+                        nonzero_bytes(u ^ 0x47474747u) & nonzero_bytes(u ^ 0x54545454u);
+  uint32_t t = (u >> 1) & 0x03030303u;
+  t ^= (t >> 1) & 0x01010101u;
+  const uint32_t b = none >> 7;  // 1 in the low bit of every undetermined byte
+  t &= (b ^ 0x01010101u) * 3u;   // undetermined bases encode as 0
+  // Gather the byte fields with one multiply each: byte i's field lands at bit 30 - 2i (codes)
+  // or 27 - i (flags), and no two partial products overlap.
+  codes = (t * 0x40100401u) >> 24;
+  bad = (b * 0x08040201u) >> 24;
+}
+
 __global__ void __launch_bounds__(256) encode_kernel(const uint8_t* __restrict__ seq, uint64_t n,
                                                      unsigned long long* __restrict__ packed,
                                                      uint32_t* __restrict__ nmask,
@@ -35,9 +59,12 @@ __global__ void __launch_bounds__(256) encode_kernel(const uint8_t* __restrict__
       const uint4 a = __ldg(p), b = __ldg(p + 1);
       const uint32_t v[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
 #pragma unroll
-      for (int q = 0; q < 8; ++q)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) encode_byte((v[q] >> (8 * j)) & 0xFFu, word, mask, 4 * q + j);
+      for (int q = 0; q < 8; ++q) {
+        uint32_t codes, bad;
+        encode_word4(v[q], codes, bad);
+        word |= (unsigned long long)codes << (56 - 8 * q);
+        mask |= bad << (28 - 4 * q);
+      }
     } else {
       for (int j = 0; j < 32; ++j) {
         if (b0 + j < n)

@@ -120,6 +120,22 @@ def test_partition_edge_reads(g):
     assert _rows(ex) == _rows(want)
 
 
+@pytest.mark.parametrize("k,m", [(32, 7), (65, 9)])
+def test_every_byte_value_in_reads(g, k, m):
+    """Sec. 2.4.1: only ACGTacgt are bases.  Each of the 256 byte values replaces twenty bases
+    at random positions of ragged reads (so both the 32-byte vector path and the scalar tail of
+    the encoder see it); bins and counts match the oracle."""
+    rng = np.random.default_rng(k)
+    seq, offs = synth.random_small(2000, k - 2, k + 600, p_n=0.0, seed=k + 7, lowercase=True)
+    seq = seq.copy()
+    hit = rng.choice(seq.size, 256 * 20, replace=False)
+    seq[hit] = np.tile(np.arange(256, dtype=np.uint8), 20)
+    ex, _, _ = _gpu_bins(g, seq, offs, k, m, 16)
+    assert _rows(ex) == _rows(oracle.partition(seq, offs, k, m, 16))
+    got, _ = _gpu_count(g, seq, offs, k, m, 16, 1)
+    assert_same_rows(got, oracle.count(seq, offs, k, min_count=1))
+
+
 # ---- phase two -------------------------------------------------------------------------
 
 # the first and last k of every (key words, stored chunks) pair from k = 8 to the paper's 479:
