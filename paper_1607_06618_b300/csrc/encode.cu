@@ -8,6 +8,7 @@
 // tile, scans the tile sums, then writes every tile's records from its own offset.
 #include <algorithm>
 
+#include "../../include/gerbil.h"
 #include "common.cuh"
 #include "kernels.h"
 
@@ -75,72 +76,105 @@ __global__ void __launch_bounds__(1024) encode_scan_kernel(unsigned long long* _
   if (threadIdx.x == 0) *total = carry;
 }
 
-// Eight bits of the 2k-bit key (W words, word 0 most significant) whose lowest bit sits at
-// bit position t (t >= -6; bits below position 0 read as 0).
-template <int W>
-__device__ __forceinline__ uint32_t key_byte(const unsigned long long key[W], int t) {
-  if (t < 0) return (uint32_t)(key[W - 1] << (-t)) & 0xFFu;
-  const int wi = W - 1 - (t >> 6), off = t & 63;
-  unsigned long long v = 0;
-#pragma unroll
-  for (int j = 0; j < W; ++j)
-    if (j == wi) v = key[j] >> off;
-  if (off > 56) {
-#pragma unroll
-    for (int j = 0; j < W; ++j)
-      if (j == wi - 1) v |= key[j] << (64 - off);
-  }
-  return (uint32_t)v & 0xFFu;
-}
+// Record writer.  A CTA takes one tile of ENC_TILE rows, a warp 32 consecutive rows (a chunk,
+// one row per lane) at a time.  The lanes write their records into the warp's shared buffer,
+// placed so that buffer and output agree modulo 16 bytes; the warp then copies the chunk's
+// bytes out with 16-byte stores, and byte stores for the partial 16 bytes at either end (the
+// neighbouring chunks own the other bytes there).  Chunk offsets within the tile come from a
+// per-chunk count of long-count rows (ballot) and one scan over the tile's chunks.
+constexpr int ENC_CHUNKS = ENC_TILE / 32;
+constexpr int ENC_WARPS = ENC_THREADS / 32;
+constexpr int ENC_MAX_REC = (GERBIL_MAX_K + 3) / 4 + 5;       // longest record
+constexpr int ENC_BUF = (32 * ENC_MAX_REC + 16 + 15) / 16 * 16;  // per warp, 16-byte multiple
 
 template <int W>
 __global__ void __launch_bounds__(ENC_THREADS) encode_write_kernel(EncodeParams P) {
-  const unsigned long long t = blockIdx.x;
-  const unsigned long long r0 = t * ENC_TILE + (unsigned long long)threadIdx.x * ENC_ROWS;
-  const int KB = (P.k + 3) >> 2;
-  uint32_t c[ENC_ROWS];
-  uint32_t mine = 0;
-#pragma unroll
-  for (int j = 0; j < ENC_ROWS; ++j) {
-    c[j] = (r0 + j < P.n) ? __ldg(P.counts + r0 + j) : 0u;
-    mine += (r0 + j < P.n && c[j] >= 255u) ? 1u : 0u;
-  }
-  // long-count rows of this tile before this thread's rows
+  __shared__ uint32_t s_long[ENC_CHUNKS];  // long-count rows per chunk, then their prefix
+  __shared__ __align__(16) uint8_t s_buf[ENC_WARPS][ENC_BUF];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  uint32_t incl = mine;
-  for (int o = 1; o < 32; o <<= 1) {
-    const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-    if (lane >= o) incl += y;
-  }
-  __shared__ uint32_t s[ENC_THREADS / 32];
-  if (lane == 31) s[warp] = incl;
-  __syncthreads();
-  uint32_t before = incl - mine;
-  for (int w = 0; w < warp; ++w) before += s[w];
-  unsigned long long off = P.base + r0 * (unsigned long long)(KB + 1) +
-                           4ull * (P.tile_long[t] + before);
-#pragma unroll 1
-  for (int j = 0; j < ENC_ROWS; ++j) {
-    const unsigned long long r = r0 + j;
-    if (r >= P.n) break;
-    uint8_t* o = P.out + off;
-    if (c[j] < 255u) {
-      o[0] = (uint8_t)c[j];
-      o += 1;
-    } else {
-      o[0] = 0xFFu;
-      o[1] = (uint8_t)(c[j] >> 24);
-      o[2] = (uint8_t)(c[j] >> 16);
-      o[3] = (uint8_t)(c[j] >> 8);
-      o[4] = (uint8_t)c[j];
-      o += 5;
-    }
-    unsigned long long key[W];
+  const unsigned long long t = blockIdx.x;
+  const unsigned long long row0 = t * ENC_TILE;
+  const int k = P.k;
+  const int KB = (k + 3) >> 2;
+  constexpr int CPW = ENC_CHUNKS / ENC_WARPS;  // chunks per warp: warp w takes w, w + 8, ...
+  uint32_t cnt[CPW], lng[CPW];
 #pragma unroll
-    for (int q = 0; q < W; ++q) key[q] = __ldg(P.keys + r * W + q);
-    // byte b holds bases 4b..4b+3: key bits 2k-8b-1 down to 2k-8b-8
-    for (int b = 0; b < KB; ++b) o[b] = (uint8_t)key_byte<W>(key, 2 * P.k - 8 * b - 8);
-    off += (c[j] < 255u ? 1u : 5u) + (unsigned)KB;
+  for (int i = 0; i < CPW; ++i) {
+    const unsigned long long r = row0 + (unsigned long long)(warp + ENC_WARPS * i) * 32 + lane;
+    cnt[i] = r < P.n ? __ldg(P.counts + r) : 0u;
+    lng[i] = __ballot_sync(0xFFFFFFFFu, r < P.n && cnt[i] >= 255u);
+    if (lane == 0) s_long[warp + ENC_WARPS * i] = __popc(lng[i]);
+  }
+  __syncthreads();
+  if (warp == 0) {  // exclusive prefix over the tile's chunks, two per lane
+    const uint32_t a = s_long[2 * lane], b = s_long[2 * lane + 1];
+    uint32_t incl = a + b;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    const uint32_t ex = incl - a - b;
+    __syncwarp();
+    s_long[2 * lane] = ex;
+    s_long[2 * lane + 1] = ex + a;
+  }
+  __syncthreads();
+  const unsigned long long tile_off =
+      P.base + row0 * (unsigned long long)(KB + 1) + 4ull * P.tile_long[t];
+  const int s = 8 * KB - 2 * k;  // left shift that ends the key on a byte boundary (0..6)
+  const int skip = 8 * W - KB;   // leading zero bytes of the shifted W-word key
+  uint8_t* buf = s_buf[warp];
+#pragma unroll
+  for (int i = 0; i < CPW; ++i) {  // unrolled: cnt and lng stay in registers
+    const int c = warp + ENC_WARPS * i;
+    const unsigned long long r = row0 + (unsigned long long)c * 32 + lane;
+    if (row0 + (unsigned long long)c * 32 >= P.n) break;  // the same for the whole warp
+    const int nrows = (int)min(32ull, P.n - (row0 + (unsigned long long)c * 32));
+    const unsigned long long g0 = tile_off + (unsigned long long)c * 32 * (KB + 1) + 4ull * s_long[c];
+    const int a0 = (int)(((uintptr_t)P.out + g0) & 15);  // the buffer's byte a0 goes to out + g0
+    const int bytes = nrows * (KB + 1) + 4 * __popc(lng[i]);
+    if (lane < nrows) {
+      uint8_t* o = buf + a0 + lane * (KB + 1) + 4 * __popc(lng[i] & ((1u << lane) - 1u));
+      const uint32_t cv = cnt[i];
+      if (cv < 255u) {
+        *o++ = (uint8_t)cv;
+      } else {
+        o[0] = 0xFFu;
+        o[1] = (uint8_t)(cv >> 24);
+        o[2] = (uint8_t)(cv >> 16);
+        o[3] = (uint8_t)(cv >> 8);
+        o[4] = (uint8_t)cv;
+        o += 5;
+      }
+      unsigned long long key[W];
+#pragma unroll
+      for (int q = 0; q < W; ++q) key[q] = __ldg(P.keys + r * W + q);
+      if (s) {
+#pragma unroll
+        for (int q = 0; q < W; ++q)
+          key[q] = (key[q] << s) | (q + 1 < W ? key[q + 1] >> (64 - s) : 0ull);
+      }
+      // big-endian bytes of the shifted key, the first `skip` (zero) bytes left out
+#pragma unroll
+      for (int q = 0; q < W; ++q)
+#pragma unroll
+        for (int y = 0; y < 8; ++y) {
+          const int B = 8 * q + y - skip;
+          if (B >= 0) o[B] = (uint8_t)(key[q] >> (56 - 8 * y));
+        }
+    }
+    __syncwarp();
+    // copy buf[a0, a0 + bytes) to out[g0, g0 + bytes)
+    uint8_t* dst = P.out + (g0 - (unsigned long long)a0);  // 16-byte aligned
+    const int e = a0 + bytes;
+    const int h1 = min(16, e);  // head: bytes a0 .. 15 of the first 16
+    if (lane >= a0 && lane < h1) dst[lane] = buf[lane];
+    const int t0 = max(16, e & ~15);  // tail: the last partial 16, past the head
+    if (lane < 16 && t0 + lane < e) dst[t0 + lane] = buf[t0 + lane];
+    for (int x = 16 + 16 * lane; x + 16 <= e; x += 512)
+      *reinterpret_cast<uint4*>(dst + x) = *reinterpret_cast<const uint4*>(buf + x);
+    __syncwarp();
   }
 }
 

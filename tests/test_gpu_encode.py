@@ -77,3 +77,37 @@ def test_records_of_a_grouped_result_and_of_an_empty_one(g):
     assert len(res) == 0 and res.encode_records(k).size == 0
     res.free()
     bins.free()
+
+
+@pytest.mark.parametrize("k", [320, 479])
+def test_records_of_wide_keys_at_any_output_alignment(g, k):
+    """The longest records (k up to 479, counts of five bytes) and device output that starts
+    at every offset modulo 16: the writer stages each 32-row chunk in shared memory and copies
+    it out in 16-byte stores, with byte stores at the chunk's ends."""
+    import torch
+    gerbil, ctx = g
+    gen = synth.genome(1500, 7204 + k)
+    tiled, toffs = synth.tiled_reads(gen, 600, 1)
+    rnd, roffs = synth.random_small(60, k, k + 300, p_n=0.0, seed=7205)
+    parts = [(tiled, toffs)] * 3 + [(rnd, roffs)]  # up to 3 x 122 = 366 copies at k = 479
+    seq = np.concatenate([p[0] for p in parts])
+    offs = [np.uint64(0)]
+    for s_, o_ in parts:
+        offs.extend((o_[1:] + offs[-1]).tolist())
+    offs = np.asarray(offs, dtype=np.uint64)
+    bins = ctx.partition(seq, offs, k, 11, 4)
+    res = ctx.count_batch(bins, None, k, 1)
+    keys, counts = res.to_host()
+    assert counts.max() >= 255 and counts.min() < 255
+    want = _want(keys, counts, k)
+    assert res.encode_records(k).tobytes() == want
+    buf = torch.full((len(want) + 64,), 0xAB, dtype=torch.uint8, device="cuda")
+    for shift in (1, 3, 8, 15):
+        buf.fill_(0xAB)
+        nb = gerbil.gerbil_encode_records(res.handle, k, buf.data_ptr() + shift, len(want), 1)
+        host = buf.cpu().numpy()
+        assert nb == len(want)
+        assert host[shift:shift + nb].tobytes() == want
+        assert (host[:shift] == 0xAB).all() and (host[shift + nb:] == 0xAB).all()
+    res.free()
+    bins.free()
