@@ -112,7 +112,9 @@ constexpr int SEG = 8;  // consecutive m-mers per thread in the key pass
 #define GERBIL_SUPER_TILE 3072
 #endif
 #ifndef GERBIL_SUPER_MINB
-#define GERBIL_SUPER_MINB 7  // resident CTAs per SM the registers are held to (shared memory allows 7)
+// resident CTAs per SM the registers are held to: 6 (39 registers, no spills); shared memory
+// allows 7, at which the kernel spills 16 bytes and ran 0.5% slower on k = 65 and k = 99
+#define GERBIL_SUPER_MINB 6
 #endif
 constexpr int SUPER_TILE = GERBIL_SUPER_TILE;  // window starts per CTA
 constexpr int SUPER_WORDS = SUPER_TILE / 32 + 1;  // mask words holding a CTA's windows 0..tile
