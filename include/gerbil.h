@@ -370,8 +370,8 @@ void gerbil_counts_free(gerbil_counts* counts);
  * first base in the two high bits of the first byte; the unused low bits of the last byte, which
  * App. C leaves undefined, are written as 0).  k must be the k the result was counted with.
  * *nbytes receives the size of all records.  out == NULL only computes the size; otherwise out
- * (cap bytes, device memory when out_on_device != 0, else host memory) receives the records.
- * The work runs on the stream of the context that owns the result and synchronizes it; scratch
+ * (cap bytes, device memory when out_on_device != 0, else host memory; any byte alignment)
+ * receives the records.  The work runs on the stream of the context that owns the result and synchronizes it; scratch
  * comes from that context.  A host buffer with room for rows * (ceil(k/4) + 5) bytes (every
  * count in its 5-byte form) lets a one-part result skip the size pass before the records are
  * written: one stream synchronisation instead of two.  Errors: E_INVAL (k of another key width,
