@@ -257,18 +257,19 @@ int gerbil_forget_ratio(gerbil_ctx* ctx);
  * of k-mers placed at the first probe and the largest number of probes any k-mer needed).
  * enable != 0 clears and starts the histograms: every later insert of this context's counts
  * (two-grid and waves forms; fused 1 does not record) records, once placed, the number of
- * slots it read and the number of distinct
- * 128-byte lines those slots lie in (this build probes linearly, one slot per read, so
- * consecutive probes share lines).  While on, counts run a separate build of the insert kernel
- * that adds two global atomics per k-mer; the normal build carries no recording code.
- * enable == 0 stops and frees.  Errors: E_INVAL, E_CUDA. */
+ * slots it read and the number of distinct 128-byte lines those slots lie in under linear
+ * probing (one slot per read, so consecutive probes share lines), or of windows under the
+ * windowed double hashing of probe_scheme 1.  While on, counts run a separate instantiation
+ * of the insert kernel that adds two global atomics per k-mer; the normal one carries no
+ * recording code.  enable == 0 stops and frees.  Errors: E_INVAL, E_CUDA. */
 #define GERBIL_PROBE_BUCKETS 34
 int gerbil_probe_stats(gerbil_ctx* ctx, int enable);
 
-/* Reads the probe histograms of Sec. 3.3's comparison (GERBIL_PROBE_BUCKETS entries each): entry i < 32 counts k-mers placed
- * after reading i+1 slots (slots[]) or touching i+1 lines (lines[]), entry 32 more than 32,
- * entry 33 k-mers sent to the overflow area (theta probes without room).  Synchronizes the
- * context's stream.  Errors: E_INVAL, E_STATE (statistics off), E_CUDA. */
+/* Reads the probe histograms of Sec. 3.3's comparison (GERBIL_PROBE_BUCKETS entries each):
+ * entry i < 32 counts k-mers placed after reading i+1 slots (slots[]) or touching i+1 lines
+ * (lines[]), entry 32 more than 32, entry 33 k-mers sent to the overflow area (theta probes
+ * without room).  Synchronizes the context's stream.  Errors: E_INVAL, E_STATE (statistics
+ * off), E_CUDA. */
 int gerbil_get_probe_stats(const gerbil_ctx* ctx, uint64_t* slots, uint64_t* lines);
 
 /* Destroys the context and releases its scratch memory (not the caller's stream).  Bins and
@@ -336,9 +337,10 @@ int gerbil_count(gerbil_ctx* ctx, const gerbil_bins* bins, int bin, int k, uint3
 
 /* Phase two for many bins at once (Sec. 2.3 Phase Two over several temporary files; bins are
  * independent, Sec. 2.1): the bins listed in bin_list (host array of nb distinct bin indices;
- * NULL = all bins, nb ignored) are counted together and their rows returned in one result.  Because bins partition the k-mers, the rows are the union of the per-bin
- * results.  With opts->persistent (default) one persistent kernel pops tiles of all bins
- * from a device work queue.  Errors: as gerbil_count. */
+ * NULL = all bins, nb ignored) are counted together and their rows returned in one result.
+ * Because bins partition the k-mers, the rows are the union of the per-bin results.  With
+ * opts->persistent (default) one persistent kernel pops tiles of all bins from a device work
+ * queue.  Errors: as gerbil_count. */
 int gerbil_count_batch(gerbil_ctx* ctx, const gerbil_bins* bins, const int32_t* bin_list,
                        int nb, int k, uint32_t min_count, const gerbil_opts* opts,
                        gerbil_counts** out);
@@ -371,11 +373,12 @@ void gerbil_counts_free(gerbil_counts* counts);
  * App. C leaves undefined, are written as 0).  k must be the k the result was counted with.
  * *nbytes receives the size of all records.  out == NULL only computes the size; otherwise out
  * (cap bytes, device memory when out_on_device != 0, else host memory; any byte alignment)
- * receives the records.  The work runs on the stream of the context that owns the result and synchronizes it; scratch
- * comes from that context.  A host buffer with room for rows * (ceil(k/4) + 5) bytes (every
- * count in its 5-byte form) lets a one-part result skip the size pass before the records are
- * written: one stream synchronisation instead of two.  Errors: E_INVAL (k of another key width,
- * cap too small -- *nbytes is still set), E_NOMEM, E_CUDA. */
+ * receives the records.  The work runs on the stream of the context that owns the result and
+ * synchronizes it; scratch comes from that context.  A host buffer with room for
+ * rows * (ceil(k/4) + 5) bytes (every count in its 5-byte form) lets a one-part result skip
+ * the size pass before the records are written: one stream synchronisation instead of two.
+ * Errors: E_INVAL (k of another key width, cap too small -- *nbytes is still set), E_NOMEM,
+ * E_CUDA. */
 int gerbil_encode_records(const gerbil_counts* counts, int k, void* out, uint64_t cap,
                           int out_on_device, uint64_t* nbytes);
 
